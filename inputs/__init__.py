@@ -1,0 +1,111 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This package holds none of the method's arithmetic: it only makes the files that
+both sides read.  The byte stream is xorshift64 (Marsaglia 2003, shifts 13/7/17),
+state = seed, each step emitting the new state as 8 little-endian bytes; a file of
+`size` bytes is the first `size` bytes of that stream.  The fast writer is
+`xorshift_gen.c` (multi-threaded, GF(2) jump-ahead); `xorshift64_bytes` is the
+plain Python definition used to pin it on small sizes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xorshift_gen.c")
+_LIB = os.path.join(_HERE, "_xorshift_gen.so")
+_MASK = (1 << 64) - 1
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the generator with gcc into inputs/_xorshift_gen.so (host code only)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.xs_state_after.restype = ctypes.c_uint64
+            lib.xs_state_after.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.xs_fill.restype = ctypes.c_int
+            lib.xs_fill.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+            lib.xs_write_file.restype = ctypes.c_int
+            lib.xs_write_file.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def xorshift64_step(x: int) -> int:
+    """One step of Marsaglia's xorshift64 with triple (13, 7, 17)."""
+    x ^= (x << 13) & _MASK
+    x ^= x >> 7
+    x ^= (x << 17) & _MASK
+    return x
+
+
+def xorshift64_words(seed: int, n: int, start_word: int = 0) -> list[int]:
+    """Output words start_word .. start_word+n-1 (word j = state after j+1 steps). Slow."""
+    if seed == 0:
+        raise ValueError("xorshift64 seed must be non-zero")
+    x = seed
+    for _ in range(start_word):
+        x = xorshift64_step(x)
+    out = []
+    for _ in range(n):
+        x = xorshift64_step(x)
+        out.append(x)
+    return out
+
+
+def xorshift64_bytes(seed: int, size: int) -> bytes:
+    """The first `size` bytes of the stream, by the plain definition (small sizes only)."""
+    words = xorshift64_words(seed, (size + 7) // 8)
+    return b"".join(w.to_bytes(8, "little") for w in words)[:size]
+
+
+def state_after(seed: int, k: int) -> int:
+    """xorshift64 state after k steps, by the C jump-ahead."""
+    return int(_load().xs_state_after(seed, k))
+
+
+def fill(seed: int, byte_off: int, n: int) -> bytes:
+    """Stream bytes [byte_off, byte_off+n) via the C generator."""
+    buf = ctypes.create_string_buffer(max(n, 1))
+    rc = _load().xs_fill(buf, seed, byte_off, n)
+    if rc != 0:
+        raise OSError(-rc, os.strerror(-rc))
+    return buf.raw[:n]
+
+
+def write_file(path: str, seed: int, size: int, threads: int | None = None) -> str:
+    """Write `size` stream bytes for `seed` to `path` (multi-threaded)."""
+    threads = threads or min(32, os.cpu_count() or 1)
+    rc = _load().xs_write_file(path.encode(), seed, size, threads)
+    if rc != 0:
+        raise OSError(-rc, "xs_write_file(%s): %s" % (path, os.strerror(-rc)))
+    return path
+
+
+def ensure_file(path: str, seed: int, size: int, threads: int | None = None) -> str:
+    """Write the file unless one of the right size with a matching head and tail exists."""
+    if os.path.exists(path) and os.path.getsize(path) == size:
+        k = min(size, 4096)
+        with open(path, "rb") as f:
+            head = f.read(k)
+            f.seek(size - k)
+            tail = f.read(k)
+        if head == fill(seed, 0, k) and tail == fill(seed, size - k, k):
+            return path
+    return write_file(path, seed, size, threads)

@@ -1,0 +1,69 @@
+"""Seeded input generator: pinned to Marsaglia's definition, independent of the method."""
+import os
+
+import pytest
+
+import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "xorshift64_seed1.txt")
+
+
+def _golden():
+    vals = {}
+    for line in open(GOLD):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = v
+    return vals
+
+
+def test_first_word_by_hand():
+    g = _golden()
+    assert inputs.xorshift64_words(1, 1)[0] == int(g["word0"], 16)
+    assert inputs.xorshift64_bytes(1, 8).hex() == g["bytes0_7"]
+    assert inputs.fill(1, 0, 8).hex() == g["bytes0_7"]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 0x9E3779B97F4A7C15])
+@pytest.mark.parametrize("k", [0, 1, 2, 63, 64, 1000, 4097])
+def test_jump_ahead_matches_stepping(seed, k):
+    x = seed
+    for _ in range(k):
+        x = inputs.xorshift64_step(x)
+    assert inputs.state_after(seed, k) == x
+
+
+def test_jump_ahead_is_linear():
+    # xorshift is linear over GF(2): M^k (a ^ b) = M^k a ^ M^k b
+    a, b, k = 0x1234567, 0xABCDEF0123, 12345
+    assert inputs.state_after(a ^ b, k) == inputs.state_after(a, k) ^ inputs.state_after(b, k)
+
+
+@pytest.mark.parametrize("off,n", [(0, 1), (0, 17), (3, 29), (8, 8), (1001, 513)])
+def test_fill_matches_definition(off, n):
+    assert inputs.fill(5, off, n) == inputs.xorshift64_bytes(5, off + n)[off:]
+
+
+@pytest.mark.parametrize("size", [0, 1, 7, 8, 9, 4095, 4096, 4097, (3 << 20) + 17])
+@pytest.mark.parametrize("threads", [1, 3])
+def test_write_file(tmp_path, size, threads):
+    p = str(tmp_path / "f.bin")
+    inputs.write_file(p, 11, size, threads)
+    data = open(p, "rb").read()
+    assert len(data) == size
+    head = min(size, 256)
+    assert data[:head] == inputs.xorshift64_bytes(11, head)
+    if size > 300:
+        assert data[-100:] == inputs.fill(11, size - 100, 100)
+
+
+def test_thread_count_independent(tmp_path):
+    a, b = str(tmp_path / "a"), str(tmp_path / "b")
+    inputs.write_file(a, 3, (5 << 20) + 3, 1)
+    inputs.write_file(b, 3, (5 << 20) + 3, 7)
+    assert open(a, "rb").read() == open(b, "rb").read()
+
+
+def test_seed_zero_rejected(tmp_path):
+    with pytest.raises(OSError):
+        inputs.write_file(str(tmp_path / "z"), 0, 10)

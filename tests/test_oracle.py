@@ -1,0 +1,401 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: expected values come from the
+generator's definition (bytes), brute-force loops, closed forms, hand-derived
+traces in tests/golden (with their derivation), and invariants.
+"""
+import os
+import random
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import plain, policy
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+P = 4096
+
+
+def _file(tmp_path, name, seed, size):
+    p = str(tmp_path / name)
+    inputs.write_file(p, seed, size, 2)
+    return p
+
+
+# ---------------------------------------------------------------- plain definition
+@pytest.mark.parametrize("size", [0, 1, P - 1, P, P + 1, 3 * P + 17])
+def test_gread_plain_matches_generator(tmp_path, size):
+    path = _file(tmp_path, "f", 21, size)
+    ref = inputs.xorshift64_bytes(21, size)
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        offs = sorted({0, 1, P - 1, P, P + 1, size - 1, size, size + 1, 2 * P + 5})
+        lens = [0, 1, 15, P, P + 1, 3 * P, 10 * P]
+        for off in offs:
+            if off < 0:
+                continue
+            for ln in lens:
+                n, data = plain.gread_plain(fd, size, off, ln)
+                want = ref[off:off + ln]
+                assert n == len(want) == max(0, min(ln, size - off))
+                assert data == want
+    finally:
+        os.close(fd)
+
+
+def test_gread_plain_rejects_negative(tmp_path):
+    path = _file(tmp_path, "f", 2, 100)
+    fd = os.open(path, os.O_RDONLY)
+    assert plain.gread_plain(fd, 100, -1, 4)[0] == -22
+    assert plain.gread_plain(fd, 100, 0, -4)[0] == -22
+    os.close(fd)
+
+
+def _sum_loop(data):
+    s = 0
+    for b in data:
+        s += b
+    return s % (1 << 64)
+
+
+def _hash_loop(data, off):
+    h = 0
+    for i, b in enumerate(data):
+        h += b * (off + i + 1)
+    return h % (1 << 64)
+
+
+@pytest.mark.parametrize("off", [0, 1, 4096, (1 << 40) + 3])
+def test_checksums_brute_force(off):
+    rng = random.Random(off)
+    data = bytes(rng.randrange(256) for _ in range(3001))
+    assert plain.byte_sum(data) == _sum_loop(data)
+    assert plain.pos_hash(data, off) == _hash_loop(data, off)
+
+
+@pytest.mark.parametrize("c,n,off", [(1, 10, 0), (255, 4096, 0), (7, 1000, 123456), (200, 1 << 20, 1 << 33)])
+def test_checksums_closed_form(c, n, off):
+    data = bytes([c]) * n
+    assert plain.byte_sum(data) == (c * n) % (1 << 64)
+    # sum_{i<n} c*(off+i+1) = c*(n*off + n(n+1)/2)
+    assert plain.pos_hash(data, off) == (c * (n * off + n * (n + 1) // 2)) % (1 << 64)
+
+
+def test_hash_wraps_mod_2_64():
+    off = (1 << 64) - 10
+    data = bytes([255]) * 64
+    assert plain.pos_hash(data, off) == _hash_loop(data, off)
+
+
+def test_hash_detects_swapped_pages():
+    # hash(a+b) - hash(b+a) = len(a) * (sum(b) - sum(a)) for equal lengths
+    a, b = bytes([1]) * 4096, bytes([2]) * 4096
+    assert plain.byte_sum(a + b) == plain.byte_sum(b + a)
+    assert plain.pos_hash(a + b, 0) != plain.pos_hash(b + a, 0)
+
+
+def test_scan_plain_strides(tmp_path):
+    size = 5 * 8192 + 100
+    path = _file(tmp_path, "s", 9, size)
+    ref = inputs.xorshift64_bytes(9, size)
+    counts, sums, hashes = plain.scan_plain(path, 8192)
+    assert len(counts) == 6
+    for s in range(6):
+        chunk = ref[s * 8192:(s + 1) * 8192]
+        assert counts[s] == len(chunk)
+        assert sums[s] == _sum_loop(chunk)
+        assert hashes[s] == _hash_loop(chunk, s * 8192)
+
+
+def test_stride_owner():
+    assert plain.stride_owner(0, 64) == (0, 0)
+    assert plain.stride_owner(65, 64) == (1, 1)
+    assert plain.stride_count(0, 10) == 0 and plain.stride_count(10, 10) == 1 and plain.stride_count(11, 10) == 2
+
+
+# ---------------------------------------------------------------- policy: data
+def _random_trace(rng, size, n, streams, max_len):
+    out = []
+    for _ in range(n):
+        off = rng.randrange(size + 2 * P)
+        ln = rng.randrange(max_len + 1)
+        out.append((rng.randrange(streams), 0, off, ln))
+    return out
+
+
+@pytest.mark.parametrize("mode", ["readahead", "ondemand"])
+@pytest.mark.parametrize("frames,ra_cap,reserve,async_ra,max_rpc", [
+    (64, 8, 0, True, 64), (5, 8, 2, True, 64), (3, 1, 0, False, 64), (8, 64, 1, True, 3), (2, 4, 0, True, 64)])
+def test_policy_delivers_plain_bytes(tmp_path, mode, frames, ra_cap, reserve, async_ra, max_rpc):
+    size = 23 * P + 1234
+    path = _file(tmp_path, "p", 31, size)
+    ref = inputs.xorshift64_bytes(31, size)
+    rng = random.Random(frames * 131 + ra_cap)
+    sim = policy.PageCacheSim(P, frames, mode, ra_cap, reserve, async_ra, max_rpc_pages=max_rpc)
+    sim.open(0, path)
+    seq = [(0, 0, k * 3000, 3000) for k in range(size // 3000 + 2)]
+    for stream, fid, off, ln in seq + _random_trace(rng, size, 300, 4, 2 * P + 5):
+        n, data = sim.gread(stream, fid, off, ln)
+        want = ref[off:off + ln] if off < size else b""
+        assert n == len(want)
+        assert data == want
+    sim.close_all()
+
+
+def test_policy_rejects_bad_fid_and_args(tmp_path):
+    path = _file(tmp_path, "b", 1, 100)
+    sim = policy.PageCacheSim(P, 4)
+    sim.open(0, path)
+    assert sim.gread(0, 3, 0, 10)[0] == -9
+    assert sim.gread(0, 0, -1, 10)[0] == -22
+    assert sim.gread(0, 0, 100, 10) == (0, b"")
+    assert sim.gread(0, 0, 0, 0) == (0, b"")
+    sim.close_all()
+
+
+# ---------------------------------------------------------------- policy: readahead rule
+def _parse(name):
+    params, rows = {}, []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        parts = line.split()
+        if parts[0] == "params":
+            for kv in parts[1:]:
+                k, v = kv.split("=")
+                params[k] = v
+        else:
+            rows.append(parts)
+    return params, rows
+
+
+def test_worked_example_first_window(tmp_path):
+    params, rows = _parse("readahead_worked_example.txt")
+    page = int([r for r in rows if r[0] == "page_size"][0][1])
+    off, ln = map(int, [r for r in rows if r[0] == "read"][0][1:])
+    lo, n = map(int, [r for r in rows if r[0] == "expect_first_request"][0][1:])
+    path = _file(tmp_path, "w", 5, 64 * page)
+    sim = policy.PageCacheSim(page, 64, ra_cap=64, reserve=0)
+    sim.open(0, path)
+    sim.gread(0, 0, off, ln)
+    assert sim.rpc_log[0][1:3] == (lo, n)          # 4 KB read -> 16 KB fetched
+    assert sim.rpc_log[0][1] * page == 0 and sim.rpc_log[0][2] * page == 16384
+    sim.close_all()
+
+
+def _windows(tmp_path, ra_cap, async_ra, pages=400, max_rpc=256):
+    path = _file(tmp_path, "r%d%d%d" % (ra_cap, async_ra, max_rpc), 6, pages * P)
+    sim = policy.PageCacheSim(P, pages + 1, ra_cap=ra_cap, reserve=0, async_ra=async_ra,
+                              max_rpc_pages=max_rpc)
+    sim.open(0, path)
+    for q in range(pages):
+        sim.gread(0, 0, q * P, P)
+    sim.close_all()
+    return sim
+
+
+def test_window_doubles_async(tmp_path):
+    # initial 4x (Section 3.1), then asynchronous windows doubling to Wmax (Section 2.3)
+    sim = _windows(tmp_path, 64, True)
+    sizes = [n for (_, _, n, _) in sim.rpc_log]
+    assert sizes[:8] == [4, 8, 16, 32, 64, 64, 64, 64]
+    kinds = [k for (_, _, _, k) in sim.rpc_log]
+    assert kinds[0] == policy.SYNC_RA and set(kinds[1:]) == {policy.ASYNC_RA}
+    starts = [lo for (_, lo, _, _) in sim.rpc_log]
+    assert starts[:6] == [0, 4, 12, 28, 60, 124]
+    assert sum(sizes) == 400 and sim.stats.misses == 1
+
+
+def test_window_cap_one(tmp_path):
+    sim = _windows(tmp_path, 1, True, pages=20)
+    assert [n for (_, _, n, _) in sim.rpc_log] == [2] + [1] * 18
+
+
+def test_window_cap_eight(tmp_path):
+    sim = _windows(tmp_path, 8, True, pages=60)
+    assert [n for (_, _, n, _) in sim.rpc_log][:5] == [4, 8, 8, 8, 8]
+
+
+def test_window_doubles_sync_only(tmp_path):
+    # async off (Section 4.1 synchronous prefetcher): each miss doubles the
+    # previous window up to d + Wmax = 65
+    sim = _windows(tmp_path, 64, False)
+    sizes = [n for (_, _, n, _) in sim.rpc_log]
+    assert sizes[:8] == [4, 8, 16, 32, 64, 65, 65, 65]
+    assert all(k == policy.SYNC_RA for (_, _, _, k) in sim.rpc_log[:8])
+    # and a request never exceeds the slot's page capacity
+    sim = _windows(tmp_path, 64, False, max_rpc=64)
+    assert [n for (_, _, n, _) in sim.rpc_log][:7] == [4, 8, 16, 32, 64, 64, 64]
+
+
+def test_not_sequential_fetches_demand_run_only(tmp_path):
+    path = _file(tmp_path, "n", 8, 64 * P)
+    sim = policy.PageCacheSim(P, 64, ra_cap=8, reserve=0)
+    sim.open(0, path)
+    sim.gread(0, 0, 10 * P + 5, 2 * P)          # pages 10..12, page 9 absent
+    assert sim.rpc_log == [(0, 10, 3, policy.DEMAND)]
+    sim.gread(0, 0, 13 * P, P)                  # previous gread of this stream ended at page 13
+    assert sim.rpc_log[1] == (0, 13, min(1 + 8, max(4, 2 * 0)), policy.SYNC_RA)
+    sim.close_all()
+
+
+def test_present_predecessor_is_sequential(tmp_path):
+    path = _file(tmp_path, "q", 8, 64 * P)
+    sim = policy.PageCacheSim(P, 64, ra_cap=8, reserve=0, async_ra=False)
+    sim.open(0, path)
+    sim.gread(0, 0, 0, P)                       # [0,4) window 4
+    sim.gread(1, 0, 4 * P, P)                   # other stream; page 3 present, Tprev 4 -> T = min(9, 8)
+    assert sim.rpc_log[1] == (0, 4, 8, policy.SYNC_RA)
+    sim.close_all()
+
+
+def test_window_cut_at_eof_and_present_page(tmp_path):
+    path = _file(tmp_path, "e", 8, 10 * P + 7)
+    sim = policy.PageCacheSim(P, 64, ra_cap=64, reserve=0)
+    sim.open(0, path)
+    sim.gread(0, 0, 5 * P, P)                   # not sequential: [5,6)
+    sim.gread(1, 0, 0, P)                       # p=0: T=4 but page 5 present: [0,4) ... cut at 5? no: 4 < 5
+    sim.gread(2, 0, 4 * P, 1)                   # p=4 mark -> not a miss; hit
+    assert sim.rpc_log[0] == (0, 5, 1, policy.DEMAND)
+    assert sim.rpc_log[1] == (0, 0, 4, policy.SYNC_RA)
+    # page 4 missing: sequential (3 present), Tprev 4 -> T 8, cut at present page 5
+    assert sim.rpc_log[2] == (0, 4, 1, policy.DEMAND)
+    sim.gread(3, 0, 6 * P, 5 * P)               # pages 6..10 (10 is the 7-byte tail), cut at EOF
+    assert sim.rpc_log[3][1:3] == (6, 5)
+    sim.close_all()
+
+
+def test_max_rpc_pages_caps_requests(tmp_path):
+    path = _file(tmp_path, "m", 8, 40 * P)
+    sim = policy.PageCacheSim(P, 64, ra_cap=64, reserve=0, max_rpc_pages=3)
+    sim.open(0, path)
+    sim.gread(0, 0, 0, 10 * P)
+    assert all(n <= 3 for (_, _, n, _) in sim.rpc_log)
+    sim.close_all()
+
+
+# ---------------------------------------------------------------- policy: hand-derived traces
+def _kind(name):
+    return {"DEMAND": policy.DEMAND, "SYNC_RA": policy.SYNC_RA, "ASYNC_RA": policy.ASYNC_RA}[name]
+
+
+def test_golden_stream_small_cache(tmp_path):
+    params, rows = _parse("policy_stream_small_cache.txt")
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(tmp_path, "g1", int(params["seed"]), npg * page)
+    sim = policy.PageCacheSim(page, int(params["frames"]), ra_cap=int(params["ra_cap"]),
+                              reserve=int(params["reserve"]), async_ra=params["async_ra"] == "1")
+    sim.open(0, path)
+    reads = [int(x) for x in [r for r in rows if r[0] == "reads"][0][1:]]
+    for q in reads:
+        assert sim.gread(0, 0, q * page, page)[0] == page
+    want_rpc = [(0, int(r[1]), int(r[2]), _kind(r[3])) for r in rows if r[0] == "rpc"]
+    want_ev = [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert sim.rpc_log == want_rpc
+    assert sim.evict_log == want_ev
+    assert all(v == 1 for v in sim.stats.fetch_count.values()) and len(sim.stats.fetch_count) == npg
+    sim.close_all()
+
+
+def test_golden_ondemand_fallback(tmp_path):
+    params, rows = _parse("policy_ondemand_fallback.txt")
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(tmp_path, "g2", int(params["seed"]), npg * page)
+    sim = policy.PageCacheSim(page, int(params["frames"]), params["mode"], reserve=0)
+    sim.open(0, path)
+    ref = inputs.xorshift64_bytes(int(params["seed"]), npg * page)
+    for r in rows:
+        if r[0] == "gread":
+            s, off, ln = int(r[1]), int(r[2]), int(r[3])
+            n, data = sim.gread(s, 0, off, ln)
+            assert data == ref[off:off + ln]
+    want_rpc = [(0, int(r[1]), int(r[2]), _kind(r[3])) for r in rows if r[0] == "rpc"]
+    want_ev = [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert sim.rpc_log == want_rpc
+    assert sim.evict_log == want_ev
+    unc = int([r for r in rows if r[0] == "unconsumed_evictions"][0][1])
+    assert sim.stats.unconsumed_evictions == unc
+    sim.close_all()
+
+
+# ---------------------------------------------------------------- policy: invariants
+def test_fits_each_page_fetched_once(tmp_path):
+    # config-1 shape scaled down: file fits the cache -> no eviction, no refetch
+    size = 64 * P
+    path = _file(tmp_path, "c1", 1, size)
+    sim, res = policy.run_scan(path, P, 128, 4 * P, 4, ra_cap=8)
+    assert sim.stats.evictions == 0
+    assert sorted(sim.stats.fetch_count) == [(0, q) for q in range(64)]
+    assert set(sim.stats.fetch_count.values()) == {1}
+    c, s, h = plain.scan_plain(path, 4 * P)
+    assert [r[0] for r in res] == c and [r[1] for r in res] == s and [r[2] for r in res] == h
+
+
+def test_ondemand_one_page_per_request(tmp_path):
+    size = 50 * P + 3
+    path = _file(tmp_path, "od", 2, size)
+    sim, res = policy.run_scan(path, P, 128, 3 * P, 5, mode="ondemand")
+    assert all(n == 1 and k == policy.DEMAND for (_, _, n, k) in sim.rpc_log)
+    assert sim.stats.rpcs == 51
+
+
+def test_big_file_streams_without_refetch(tmp_path):
+    # config-2 shape scaled down: file 8x the cache, disjoint strides per stream
+    size = 256 * P
+    path = _file(tmp_path, "c2", 2, size)
+    blocks, stride = 4, 2 * P
+    sim, res = policy.run_scan(path, P, 32, stride, blocks, ra_cap=8)
+    assert set(sim.stats.fetch_count.values()) == {1} and len(sim.stats.fetch_count) == 256
+    assert sim.stats.unconsumed_evictions == 0
+    assert sim.stats.evictions == 256 - 32
+    c, s, h = plain.scan_plain(path, stride)
+    assert [r[1] for r in res] == s and [r[2] for r in res] == h
+
+
+def test_random_and_rdwr_disable_readahead(tmp_path):
+    path = _file(tmp_path, "rr", 3, 32 * P)
+    for kwargs in ({"advice": policy.ADV_RANDOM}, {"readonly": False}):
+        sim = policy.PageCacheSim(P, 64, ra_cap=8, reserve=0)
+        sim.open(0, path, **kwargs)
+        for q in range(8):
+            sim.gread(0, 0, q * P, P)
+        assert sim.rpc_log == [(0, q, 1, policy.DEMAND) for q in range(8)]
+        sim.close_all()
+
+
+def test_short_host_read_gives_eio(tmp_path):
+    path = _file(tmp_path, "sh", 3, 16 * P)
+
+    def short_read(fd, off, n):
+        return os.pread(fd, n // 2, off)
+
+    sim = policy.PageCacheSim(P, 16, ra_cap=3, reserve=0, read_fn=short_read)
+    sim.open(0, path)
+    n, _ = sim.gread(0, 0, 0, P)       # [0,4) requested; only pages 0,1 arrive
+    assert n == P
+    assert sim.gread(0, 0, 2 * P, P)[0] == -policy.EIO
+    sim.close_all()
+
+
+def test_eviction_never_takes_unconsumed_while_fifo_nonempty(tmp_path):
+    # random multi-stream trace on a tiny cache: every unconsumed eviction
+    # happens when no free frame and no consumed frame existed
+    size = 40 * P
+    path = _file(tmp_path, "iv", 4, size)
+    rng = random.Random(4)
+    sim = policy.PageCacheSim(P, 6, ra_cap=4, reserve=1)
+    sim.open(0, path)
+    orig = sim._evict
+
+    def checked(f, new_key):
+        fr = sim.frames[f]
+        if fr.key is not None and fr.consumed < fr.valid:
+            assert sim.next_unused == sim.F and not sim.fifo
+        orig(f, new_key)
+
+    sim._evict = checked
+    for stream, fid, off, ln in _random_trace(rng, size, 400, 3, 3 * P):
+        sim.gread(stream, fid, off, ln)
+    sim.close_all()
