@@ -1,0 +1,349 @@
+"""Benchmark of the GPU file-read path (one JSON line on stdout, rank 0).
+
+Workload (default): the file-larger-than-cache stride scan -- an 8 GiB seeded
+xorshift64 file, 1 GiB GPU page cache, 512 KiB pages, 296 threadblocks (2 per
+SM of a 148-SM part; the GB300 has 152), each streaming 1 MiB strides
+round-robin and computing a uint64 byte sum + position hash per stride; warm
+host page cache.  A step is one whole scan of the file from an empty GPU page
+cache.  The file (8 GiB) is far larger than L2, so no L2 flush is needed
+between steps.
+
+Reported beside the readahead path, in the same run: the on-demand path (one
+page per request), the CPU-I/O baseline (host pread threads + cudaMemcpyAsync +
+the same checksum kernel), the host-link probes that bound the path (pinned
+H2D copy and multi-thread pread), and the CPU oracle on a bounded sample.
+
+`--impl reference` times the CPU oracle itself (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
+
+WORKLOADS = {
+    # name: (file bytes, seed, page, cache, blocks, stride)
+    "cfg2_8GiB_file_1GiB_cache": (8 * GiB, 2, 512 * KiB, 1 * GiB, 296, MiB),
+    "cfg1_64MiB_file_128MiB_cache": (64 * MiB, 1, 256 * KiB, 128 * MiB, 64, MiB),
+}
+DEFAULT_WORKLOAD = "cfg2_8GiB_file_1GiB_cache"
+METRIC = "sequential gread GB/s (readahead vs on-demand vs CPU-I/O) + % link roofline; p50/p99 latency"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ensure_input(path, seed, size):
+    import inputs
+    t0 = time.time()
+    inputs.ensure_file(path, seed, size)
+    # warm host page cache: read it once
+    with open(path, "rb", buffering=0) as f:
+        while f.read(64 * MiB):
+            pass
+    return time.time() - t0
+
+
+def data_dir():
+    for d in (os.environ.get("GFS_BENCH_DIR"), "/dev/shm", tempfile.gettempdir()):
+        if d and os.path.isdir(d) and os.access(d, os.W_OK):
+            return d
+    return tempfile.gettempdir()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- reference arm (CPU oracle)
+def oracle_sample(path, page, frames, blocks, stride, budget_s, mode="readahead"):
+    """Run the oracle over the canonical trace until budget_s; returns (bytes, seconds, strides)."""
+    from oracle import plain, policy
+    reserve = policy.default_reserve(blocks, stride, page)
+    sim = policy.PageCacheSim(page, frames, mode, 8, reserve, True)
+    sim.open(0, path)
+    size = sim.files[0].size
+    done = nbytes = 0
+    t0 = time.perf_counter()
+    for stream, fid, off, ln in policy.canonical_scan_trace(size, stride, blocks, stride):
+        n, data = sim.gread(stream, fid, off, ln)
+        plain.byte_sum(data)
+        plain.pos_hash(data, off)
+        nbytes += max(n, 0)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    sim.close_all()
+    return nbytes, dt, done
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    size, seed, page, cache, blocks, stride = WORKLOADS[args.workload]
+    path = os.path.join(data_dir(), "gfs_bench_s%d_%d.bin" % (seed, size))
+    ensure_input(path, seed, size)
+    budget = args.ref_step_seconds
+    for _ in range(args.warmup):
+        oracle_sample(path, page, cache // page, blocks, stride, budget / 4)
+    tot_b = tot_t = 0.0
+    strides = 0
+    for _ in range(args.steps):
+        b, t, n = oracle_sample(path, page, cache // page, blocks, stride, budget)
+        tot_b += b
+        tot_t += t
+        strides += n
+    gbps = tot_b / tot_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbps, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_t / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "file_bytes": size, "page_bytes": page, "cache_bytes": cache,
+                   "blocks": blocks, "stride_bytes": stride, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": round(gbps, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "first %d strides of the canonical trace per step (%.0f s budget)" % (
+                             strides // max(args.steps, 1), budget)},
+        "e2e": {"value": round(gbps, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- the GPU path
+def run_gfs(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2109_05366_gb300 import gfs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    size, seed, page, cache, blocks, stride = WORKLOADS[args.workload]
+    if args.blocks:
+        blocks = args.blocks
+    # weak scaling: every rank scans its own file (seed + rank), no data-path collective
+    path = os.path.join(data_dir(), "gfs_bench_s%d_%d.bin" % (seed + rank, size))
+    gen_s = ensure_input(path, seed + rank, size)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    nstr = (size + stride - 1) // stride
+    out = tuple(torch.empty(nstr, dtype=torch.int64, device=dev) for _ in range(3))
+    peaks = measured_peaks()
+    res = {}
+
+    def timed_scans(ctx, fid, steps, warmup, fused=False):
+        ev = []
+        for i in range(warmup + steps):
+            ctx.reset_cache(stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            ctx.scan(fid, stride, blocks=blocks, threads=args.threads, fused=fused, out=out, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                ev.append(e0.elapsed_time(e1) / 1e3)
+        return ev
+
+    cfg = dict(cache_bytes=cache, page_size=page, host_threads=args.host_threads, ra_cap_pages=args.ra_cap,
+               rpc_slots=args.rpc_slots, staging_bytes=args.staging_mib * MiB, max_rpc_pages=64)
+    with gfs.Context(mode=gfs.MODE_READAHEAD, **cfg) as ctx:
+        fid = ctx.open(path)
+        # correctness of the timed configuration on sampled strides (full check in tests)
+        with ClockSampler(local) as clk:
+            if world > 1:
+                dist.barrier()
+            times = timed_scans(ctx, fid, args.steps, args.warmup, fused=args.fused)
+        st = ctx.stats(stream)
+        cnt = out[0].cpu().numpy()
+        assert (cnt[:-1] == stride).all() and cnt[-1] == size - (nstr - 1) * stride, "scan returned short counts"
+        # e2e: the C-ABI call with host result buffers, wall clock, cache reset outside
+        e2e_t = []
+        for _ in range(max(1, min(args.steps, 3))):
+            ctx.reset_cache(stream)
+            t0 = time.perf_counter()
+            ctx.scan_host(fid, stride, blocks=blocks, threads=args.threads, fused=args.fused, stream=stream)
+            e2e_t.append(time.perf_counter() - t0)
+    if world > 1:
+        tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = tt.item()
+    else:
+        total = sum(times)
+    value = world * args.steps * size / total / 1e9
+    res["readahead"] = value
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        with gfs.Context(mode=gfs.MODE_ONDEMAND, **cfg) as ctx:
+            fid = ctx.open(path)
+            od = timed_scans(ctx, fid, 1, 1)
+        extra["ondemand_gbps"] = round(size / (sum(od) / len(od)) / 1e9, 2)
+        d_file = torch.empty(size, dtype=torch.uint8, device=dev)
+        cpu_t = []
+        for i in range(3):
+            cpu_t.append(gfs.cpuio_scan(path, stride, stride, args.host_threads, 8 * MiB, d_file, out, stream))
+        extra["cpuio_gbps"] = round(size / min(cpu_t[1:]) / 1e9, 2)
+        extra["cpuio_threads"] = args.host_threads
+        one = gfs.cpuio_scan(path, stride, stride, 1, size, d_file, out, stream)
+        extra["cpuio_naive_1thread_gbps"] = round(size / one / 1e9, 2)
+        del d_file
+        h2d = gfs.probe_h2d(GiB, 16 * MiB, 3)
+        h2d_page = gfs.probe_h2d(GiB, page, 3)
+        prd = gfs.probe_pread(path, 16, 4 * MiB, 2)
+        extra["link_probe"] = {"h2d_pinned_16MiB_gbps": round(h2d, 1), "h2d_pinned_page_gbps": round(h2d_page, 1),
+                               "pread_16thr_gbps": round(prd, 1)}
+        binding = min(h2d, prd)
+    else:
+        binding = None
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    clocks = clk.summary()
+    nbytes_hbm = 4 * size  # frame write (DMA) + frame read + user write + user read
+    kt = sum(times) / len(times)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * kt, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded xorshift64 file, warm host page cache)",
+        "config": {"workload": args.workload, "file_bytes": size, "page_bytes": page, "cache_bytes": cache,
+                   "blocks": blocks, "threads": args.threads, "stride_bytes": stride, "ra_cap_pages": args.ra_cap,
+                   "host_threads": args.host_threads, "rpc_slots": args.rpc_slots, "fused": bool(args.fused),
+                   "l2": "inputs larger than L2 (8 GiB file); no flush", "parallelism": "replicas" if world > 1 else "1gpu"},
+        "clocks": clocks,
+        "e2e": {"value": round(size / (sum(e2e_t) / len(e2e_t)) / 1e9, 3), "unit": "GB/s",
+                "h2d_bytes_per_step": size, "d2h_bytes_per_step": nstr * 24},
+        "gpu_launches": args.steps,
+        "stats_last_step": {k: st[k] for k in ("rpcs", "pages_fetched", "hits", "misses", "coalesced_waits",
+                                               "ra_pages_sync", "ra_pages_async", "evictions",
+                                               "unconsumed_evictions", "timeouts", "eio")},
+        "input_gen_s": round(gen_s, 1),
+    }
+    if binding:
+        line["roofline"] = {"bound": "link", "achieved": round(value / world, 2), "peak": round(binding, 1),
+                            "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": None,
+                            "peak_source": "measured in this run: min(pinned H2D copy, 16-thread pread)"}
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        line["hbm_roofline"] = {"bound": "hbm", "achieved": round(nbytes_hbm / kt / 1e9, 1), "peak": hbm,
+                                "unit": "GB/s", "frac": round(nbytes_hbm / kt / 1e9 / hbm, 4),
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    line.update(extra)
+    if not args.quick and not args.no_cpu_baseline:
+        size_, seed_, page_, cache_, blocks_, stride_ = WORKLOADS[args.workload]
+        b, t, n = oracle_sample(path, page_, cache_ // page_, blocks_, stride_, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": "first %d strides (%d MiB) of the canonical trace, %.1f s" % (
+                                    n, b // MiB, t)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gfs", "reference"], default="gfs")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--blocks", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--host-threads", type=int, default=16)
+    ap.add_argument("--ra-cap", type=int, default=8)
+    ap.add_argument("--rpc-slots", type=int, default=128)
+    ap.add_argument("--staging-mib", type=int, default=4)
+    ap.add_argument("--fused", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gfs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,232 @@
+/*
+ * gfs.h -- C ABI of the GB300 GPU file-read path: a GPU-resident page cache fed
+ * by a GPU-side readahead prefetcher, with streaming replacement for files larger
+ * than the cache, served by host I/O threads over a request ring.
+ *
+ * Method: "A readahead prefetcher for GPU file system layer" (Dimitsas and
+ * Silberstein).  Section 2.2 defines the read path (GPUfs): every thread of a
+ * threadblock calls a POSIX-like read together; the request is split into pages
+ * of the GPU page cache; hits are copied to the user buffer, misses go to the CPU
+ * over a shared request queue, the CPU preads the file and sends the data to the
+ * GPU.  Section 4.1 adds the readahead prefetcher (one request of PAGE_SIZE +
+ * PREFETCH_SIZE on a miss; CPU delivers several pages from one pread; read-only
+ * files only; an fadvise-style hint turns it off).  Section 5.1 adds the
+ * least-recently-allocated replacement for files larger than the cache.
+ *
+ * Conventions for every call:
+ *   - Return 0 (or a count >= 0) on success and a negative errno on failure
+ *     (-EINVAL bad argument, -EBADF bad file id, -ENOMEM allocation failed,
+ *     -EIO host read failed, -ENODEV no CUDA device, -ETIMEDOUT a device wait
+ *     gave up).  No call aborts the process.
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL is the
+ *     legacy default stream.  Launch calls are asynchronous on that stream.
+ *   - Pointers named d_* are device pointers (cudaMalloc or equivalent) owned by
+ *     the caller; h_* pointers are host memory owned by the caller.
+ *   - A gfs_ctx is owned by the library from gfs_init to gfs_shutdown; it is
+ *     not safe to call gfs_* on one context from several host threads at once.
+ */
+#ifndef GFS_H_
+#define GFS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GFS_ABI_VERSION 1
+
+/* Cache policy modes. */
+#define GFS_MODE_READAHEAD 0 /* Section 4.1 prefetcher + Section 2.3 window growth */
+#define GFS_MODE_ONDEMAND 1  /* original GPUfs (Section 2.2): one page per request */
+
+/* Open flags (Section 4.4, "Page cache coherency": readahead for read-only opens only). */
+#define GFS_RDONLY 0
+#define GFS_RDWR 2 /* accepted for the hint semantics only; the path never writes */
+
+/* fadvise hints (Section 4.4: the user may turn the prefetcher off). */
+#define GFS_ADV_NORMAL 0
+#define GFS_ADV_SEQUENTIAL 1
+#define GFS_ADV_RANDOM 2
+
+/* How a served request reaches the cache frames. */
+#define GFS_XFER_DMA 0  /* host: pread -> pinned staging -> cudaMemcpyAsync -> stream write of the frame state */
+#define GFS_XFER_PULL 1 /* host: pread -> pinned staging; GPU copies staging -> frames over the host link */
+
+/* Request kinds in the RPC trace. */
+#define GFS_KIND_DEMAND 0
+#define GFS_KIND_SYNC_RA 1
+#define GFS_KIND_ASYNC_RA 2
+
+typedef struct gfs_ctx gfs_ctx;
+
+/* Configuration.  gfs_config_default() fills every field; change what you need. */
+typedef struct gfs_config {
+  uint64_t cache_bytes;    /* GPU page cache size (frames = cache_bytes / page_size) */
+  uint64_t timeout_ns;     /* deadline of every device-side wait (default 10 s) */
+  uint32_t page_size;      /* bytes per page, power of two, 4 KiB .. 64 MiB */
+  uint32_t mode;           /* GFS_MODE_* */
+  uint32_t ra_cap_pages;   /* Wmax: readahead pages beyond the demand run (Section 4.1 PREFETCH_SIZE / page) */
+  uint32_t async_ra;       /* 1: asynchronous readahead at the readahead mark (Section 2.3); 0: synchronous only (Section 4.1) */
+  uint32_t reserve_frames; /* frames readahead must leave for demand misses; 0 = B * ceil(len/P) + 1 per launch */
+  uint32_t rpc_slots;      /* request ring slots (Section 2.2 request queue; 128 in GPUfs) */
+  uint32_t max_rpc_pages;  /* pages per request at most (1 .. 256) */
+  uint32_t host_threads;   /* host I/O threads (Section 2.2; 4 in GPUfs) */
+  uint32_t staging_bytes;  /* pinned staging per host thread and buffer (rounded up to whole pages) */
+  uint32_t max_streams;    /* distinct gread stream ids (threadblocks) tracked for sequential detection */
+  uint32_t max_files;      /* open files at once (<= 255) */
+  uint32_t trace_capacity; /* entries kept in the RPC and eviction traces (0 = off) */
+  uint32_t xfer;           /* GFS_XFER_* */
+  uint32_t debug_counts;   /* 1: keep per-page fetch counts for file id 0 */
+  int32_t device;          /* CUDA device ordinal */
+  uint32_t reserved[7];
+} gfs_config;
+
+typedef struct gfs_stat {
+  uint64_t size;      /* file size in bytes */
+  uint32_t page_size; /* cache page size */
+  uint32_t flags;     /* open flags */
+  uint32_t advice;    /* current fadvise hint */
+  uint32_t reserved;
+} gfs_stat;
+
+/* Counters since the last gfs_reset_cache (device side and host side). */
+typedef struct gfs_stats {
+  uint64_t greads, hits, misses, coalesced_waits;
+  uint64_t rpcs, pages_fetched, bytes_fetched, ra_pages_sync, ra_pages_async;
+  uint64_t evictions, unconsumed_evictions, retries;
+  uint64_t timeouts, eio, enomem;
+  uint64_t host_requests, host_preads, host_bytes, host_copies, host_errors;
+  uint64_t trace_rpc_count, trace_evict_count;
+  uint64_t reserved[8];
+} gfs_stats;
+
+/* One entry of the RPC trace: a request as the GPU issued it. */
+typedef struct gfs_rpc_rec {
+  uint32_t fid, kind, npages, reserved;
+  uint64_t page_lo;
+} gfs_rpc_rec;
+
+/* One entry of the eviction trace. */
+typedef struct gfs_evict_rec {
+  uint32_t frame, old_fid, new_fid, reserved;
+  uint64_t old_page, new_page;
+} gfs_evict_rec;
+
+/* Arguments of the stride scan (Section 6.1 microbenchmark): block b of
+ * `blocks` greads strides b, b+blocks, ...; stride s covers
+ * [s*stride, s*stride + read_len) clipped at EOF. */
+typedef struct gfs_scan_args {
+  uint64_t stride;    /* bytes between stride starts */
+  uint64_t read_len;  /* bytes per gread (usually == stride) */
+  uint32_t blocks;    /* threadblocks (gread streams) */
+  uint32_t threads;   /* threads per block: 128, 256 or 512 */
+  uint32_t serialize; /* 1: one gread at a time in stride order, each waiting for its requests (exact policy traces) */
+  uint32_t fused;     /* 1: checksum while copying out of the cache (no user-buffer re-read) */
+  uint32_t reserved[4];
+} gfs_scan_args;
+
+/* Fill *cfg with defaults: 1 GiB cache, 512 KiB pages, readahead, Wmax 8,
+ * async readahead on, 128 slots, 64 pages per request, 16 host threads,
+ * 4 MiB staging, 4096 streams, 16 files, no trace, DMA transfer, device 0. */
+int gfs_config_default(gfs_config* cfg);
+
+/* Create a context: allocates the cache frames and metadata in device memory,
+ * the request ring (mapped pinned host memory) and pinned staging, and starts
+ * the host I/O threads.  *out is set only on success. */
+int gfs_init(const gfs_config* cfg, gfs_ctx** out);
+
+/* Stop the I/O threads and free everything.  No kernel using the context may
+ * still be running.  Accepts NULL. */
+int gfs_shutdown(gfs_ctx* ctx);
+
+/* Open `path` read-only; *fid (0 .. max_files-1) names it on host and device.
+ * Readahead applies only with GFS_RDONLY (Section 4.4). */
+int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid);
+
+/* Close a file id; its cached pages stay until evicted or reset. */
+int gfs_close(gfs_ctx* ctx, int fid);
+
+/* Set the access hint of a file (Section 4.4): GFS_ADV_RANDOM turns readahead off. */
+int gfs_fadvise(gfs_ctx* ctx, int fid, int advice);
+
+/* File size and cache page size. */
+int gfs_fstat(gfs_ctx* ctx, int fid, gfs_stat* st);
+
+/* Host-side fault injection for tests (never a device fault): every
+ * eio_every-th pread fails with EIO, every short_every-th returns half of what
+ * was asked, every pread first sleeps delay_us.  0 disables each. */
+int gfs_set_faults(gfs_ctx* ctx, uint32_t eio_every, uint32_t short_every, uint32_t delay_us);
+
+/* Drop every cached page, clear the counters, traces and stream history.
+ * Enqueued on `stream`; the ring keeps running.  Waits for requests in flight. */
+int gfs_reset_cache(gfs_ctx* ctx, void* stream);
+
+/* Read the counters (synchronises `stream`). */
+int gfs_get_stats(gfs_ctx* ctx, gfs_stats* out, void* stream);
+
+/* Copy up to `cap` trace entries to host arrays (either may be NULL);
+ * *n_rpc / *n_evict receive the totals recorded (may exceed cap). */
+int gfs_get_trace(gfs_ctx* ctx, gfs_rpc_rec* h_rpc, gfs_evict_rec* h_evict, uint32_t cap,
+                  uint64_t* n_rpc, uint64_t* n_evict, void* stream);
+
+/* Per-page fetch counts of file id 0 (debug_counts=1); copies min(cap, pages). */
+int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* stream);
+
+/* The stride scan: launches `args->blocks` threadblocks that gread their strides
+ * through the page cache and write, per stride s, d_count[s] (bytes delivered or
+ * -errno), d_sum[s] = sum of the bytes mod 2^64 and d_hash[s] = sum of
+ * byte * (file offset + 1) mod 2^64.  Arrays hold ceil(size/stride) entries. */
+int gfs_scan(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d_count,
+             uint64_t* d_sum, uint64_t* d_hash, void* stream);
+
+/* Same as gfs_scan with host output arrays: the device results are copied back
+ * (through a pinned buffer the context keeps) and `stream` is synchronised
+ * before return.
+ * While a kernel that calls gread is running, other host threads of the
+ * process must not issue blocking CUDA calls that take the driver lock (for
+ * example a device-to-pageable-host cudaMemcpy): the host I/O threads need the
+ * driver to complete the requests the kernel waits for (GFS_XFER_DMA). */
+int gfs_scan_host(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* h_count,
+                  uint64_t* h_sum, uint64_t* h_hash, void* stream);
+
+/* n independent greads: request i reads [d_off[i], d_off[i]+d_len[i]) into
+ * d_buf + d_dst[i] and writes its return value to d_ret[i]; `blocks`
+ * threadblocks take requests i = b, b+blocks, ...; gread stream id = block
+ * index. */
+int gfs_read_many(gfs_ctx* ctx, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                  const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks,
+                  uint32_t threads, void* stream);
+
+/* CPU-I/O baseline (Section 6.2 comparison): `threads` host threads pread the
+ * file in `chunk` pieces into pinned buffers and cudaMemcpyAsync them into
+ * d_file (>= size bytes, caller-owned); then the same per-stride checksum
+ * kernel runs.  threads == 1 and chunk >= size is the whole-file variant.
+ * *seconds receives the wall time from first pread to results ready. */
+int gfs_cpuio_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t threads,
+                   uint64_t chunk, uint8_t* d_file, int64_t* d_count, uint64_t* d_sum,
+                   uint64_t* d_hash, void* stream, double* seconds);
+
+/* Host-link probes for the roofline: pinned host->device copy GB/s with
+ * `chunk`-byte copies over `bytes`, and multi-thread pread GB/s of a file. */
+int gfs_probe_h2d(uint64_t bytes, uint64_t chunk, int reps, double* gbps);
+int gfs_probe_pread(const char* path, uint32_t threads, uint64_t chunk, int reps, double* gbps);
+
+/* Self-test of the request ring and the host I/O service without a GPU: a host
+ * thread plays the device client (same slot protocol), the service preads the
+ * file into host frames; returns 0 when every page matches pread. */
+int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests,
+                      uint32_t max_pages, uint32_t threads, uint32_t slots, uint64_t seed,
+                      uint64_t* h_served);
+
+/* Library ABI version (GFS_ABI_VERSION). */
+int gfs_abi_version(void);
+
+/* Human-readable text for a negative return value. */
+const char* gfs_strerror(int err);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFS_H_ */

@@ -1,0 +1,841 @@
+// Device runtime of the GPU file-read path (sm_103a).
+//
+// gread() is threadblock-collective (Section 2.2: every thread of a threadblock
+// calls the read together).  Warp 0 runs the page-cache control for one page at a
+// time; then all threads copy the page slice to the user buffer.
+//
+//   page table      lock-free warp-cooperative lookup in 32-slot buckets of
+//                   (key << 24 | frame); inserts and removals take a per-bucket
+//                   lock bit so one key is never mapped twice.
+//   frames          per-frame state word (EMPTY/FILLING/READY/ERROR/RECLAIM), pin
+//                   count, consumed bytes, recorded readahead window, readahead
+//                   mark, allocation sequence.
+//   miss coalescing the warp that installs a page as FILLING requests it; every
+//                   other reader pins the frame and waits on its state word.
+//   readahead       Sections 2.3 / 4.1: sequential test, window growth
+//                   min(d + Wmax, max(4d, 2 Tprev)), mark for asynchronous
+//                   readahead, cut at EOF / present page / reserve.
+//   replacement     Section 5.1: never-used frames, then the consumed FIFO (pages
+//                   read once, in consumption order), then for demand misses only
+//                   the least-recently-allocated unconsumed frame.
+//   request ring    Vyukov slots in mapped pinned memory, system-scope release /
+//                   acquire; any host thread serves any slot.
+//
+// Every wait has a %globaltimer deadline; on expiry the call returns -ETIMEDOUT.
+// Nothing traps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gfs_internal.h"
+
+namespace gfs {
+namespace dev {
+
+constexpr int kEIO = 5, kEBADF = 9, kEAGAIN = 11, kENOMEM = 12, kEINVAL = 22, kETIMEDOUT = 110;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acq(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_rlx(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_acq64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_rel64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Mapped pinned host memory (request ring): system scope.
+__device__ __forceinline__ unsigned long long ld_acq_sys64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_sys64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_sys32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_sys64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int bcast(int v) { return __shfl_sync(kFull, v, 0); }
+__device__ __forceinline__ unsigned long long bcast64(unsigned long long v) { return __shfl_sync(kFull, v, 0); }
+
+__device__ __forceinline__ void stat_add(const DevHandle& g, int i, unsigned long long v) {
+  if (v) atomicAdd(&g.ctrl->stat[i], v);
+}
+
+// SplitMix64 finaliser (Steele, Lea, Flood 2014) as the bucket hash.
+__device__ __forceinline__ uint32_t bucket_of(unsigned long long key, uint32_t nb) {
+  unsigned long long z = key + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return (uint32_t)z & (nb - 1);
+}
+
+__device__ __forceinline__ uint32_t expected_valid(const DevHandle& g, const FileDev& fi, unsigned long long page) {
+  unsigned long long base = page << g.page_shift;
+  unsigned long long rem = fi.size - base;
+  return rem < g.page_size ? (uint32_t)rem : g.page_size;
+}
+
+// ---------------------------------------------------------------- page table
+// Warp-cooperative lookup: each lane reads one slot of the bucket (256 B).
+__device__ int tab_lookup(const DevHandle& g, unsigned long long key) {
+  const int lane = lane_id();
+  uint32_t b = bucket_of(key, g.nbuckets);
+  for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {
+    unsigned long long e = ld_rlx64(&g.tab[(size_t)b * BUCKET + lane]);
+    bool hit = e != ENTRY_EMPTY && (e >> FRAME_BITS) == key;
+    unsigned m = __ballot_sync(kFull, hit);
+    if (m) {
+      unsigned long long w = __shfl_sync(kFull, e, __ffs(m) - 1);
+      return (int)(w & MAX_FRAMES);
+    }
+    int ovf = 0;
+    if (lane == 0) ovf = (int)ld_rlx(&g.tovf[b]);
+    if (!bcast(ovf)) return -1;
+    b = (b + 1) & (g.nbuckets - 1);
+  }
+  return -1;
+}
+
+__device__ bool bucket_lock(const DevHandle& g, uint32_t b, unsigned long long deadline) {
+  // lane 0 only
+  while (atomicCAS(&g.tlock[b], 0u, 1u) != 0u) {
+    if (now_ns() > deadline) return false;
+    __nanosleep(32);
+  }
+  __threadfence();
+  return true;
+}
+__device__ void bucket_unlock(const DevHandle& g, uint32_t b) {
+  __threadfence();
+  atomicExch(&g.tlock[b], 0u);
+}
+
+// Map key -> f unless key is already mapped.  Returns the frame now mapped for
+// the key (f if this call inserted it), -ETIMEDOUT, or -ENOMEM (table full).
+__device__ int tab_insert(const DevHandle& g, unsigned long long key, uint32_t f, unsigned long long deadline) {
+  const int lane = lane_id();
+  const uint32_t home = bucket_of(key, g.nbuckets);
+  int ok = 0;
+  if (lane == 0) ok = bucket_lock(g, home, deadline);
+  if (!bcast(ok)) return -kETIMEDOUT;
+  int result = -kENOMEM;
+  uint32_t b = home;
+  for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {  // already present?
+    unsigned long long e = ld_rlx64(&g.tab[(size_t)b * BUCKET + lane]);
+    unsigned m = __ballot_sync(kFull, e != ENTRY_EMPTY && (e >> FRAME_BITS) == key);
+    if (m) {
+      result = (int)(__shfl_sync(kFull, e, __ffs(m) - 1) & MAX_FRAMES);
+      break;
+    }
+    int ovf = 0;
+    if (lane == 0) ovf = (int)ld_rlx(&g.tovf[b]);
+    if (!bcast(ovf)) break;
+    b = (b + 1) & (g.nbuckets - 1);
+  }
+  if (result < 0) {
+    const unsigned long long entry = (key << FRAME_BITS) | f;
+    b = home;
+    for (uint32_t probe = 0; probe < g.nbuckets && result < 0; ++probe) {
+      unsigned long long* slot = &g.tab[(size_t)b * BUCKET + lane];
+      unsigned em = __ballot_sync(kFull, ld_rlx64(slot) == ENTRY_EMPTY);
+      while (em) {
+        int src = __ffs(em) - 1;
+        unsigned long long old = 0;
+        if (lane == src) old = atomicCAS(slot, ENTRY_EMPTY, entry);
+        old = __shfl_sync(kFull, old, src);
+        if (old == ENTRY_EMPTY) { result = (int)f; break; }
+        em &= ~(1u << src);
+      }
+      if (result < 0) {  // bucket full: later lookups must continue past it
+        if (lane == 0) { atomicExch(&g.tovf[b], 1u); __threadfence(); }
+        __syncwarp();
+        b = (b + 1) & (g.nbuckets - 1);
+      }
+    }
+  }
+  __syncwarp();
+  if (lane == 0) bucket_unlock(g, home);
+  __syncwarp();
+  return result;
+}
+
+// Remove the mapping key -> f if present.
+__device__ void tab_remove(const DevHandle& g, unsigned long long key, uint32_t f, unsigned long long deadline) {
+  const int lane = lane_id();
+  const uint32_t home = bucket_of(key, g.nbuckets);
+  int ok = 0;
+  if (lane == 0) ok = bucket_lock(g, home, deadline);
+  ok = bcast(ok);
+  const unsigned long long entry = (key << FRAME_BITS) | f;
+  uint32_t b = home;
+  for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {
+    unsigned long long* slot = &g.tab[(size_t)b * BUCKET + lane];
+    unsigned m = __ballot_sync(kFull, ld_rlx64(slot) == entry);
+    if (m) {
+      if (lane == __ffs(m) - 1) atomicCAS(slot, entry, ENTRY_EMPTY);
+      break;
+    }
+    int ovf = 0;
+    if (lane == 0) ovf = (int)ld_rlx(&g.tovf[b]);
+    if (!bcast(ovf)) break;
+    b = (b + 1) & (g.nbuckets - 1);
+  }
+  __syncwarp();
+  if (lane == 0 && ok) bucket_unlock(g, home);
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- consumed FIFO
+// Bounded MPMC queue (Vyukov) over fifo_cap cells; each frame is in it at most once.
+__device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
+  unsigned long long t = atomicAdd(&g.ctrl->fifo_tail.v, 1ull);
+  unsigned long long* c = &g.fifo[t % g.fifo_cap];
+  while ((ld_acq64(c) >> FRAME_BITS) != t) {
+    if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return false; }
+    __nanosleep(32);
+  }
+  st_rel64(c, ((t + 1) << FRAME_BITS) | f);
+  return true;
+}
+
+// Returns a frame, -1 when empty, -ETIMEDOUT.
+__device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
+  for (;;) {
+    unsigned long long h = ld_acq64(&g.ctrl->fifo_head.v);
+    unsigned long long t = ld_acq64(&g.ctrl->fifo_tail.v);
+    if (h >= t) return -1;
+    if (atomicCAS(&g.ctrl->fifo_head.v, h, h + 1) != h) continue;
+    unsigned long long* c = &g.fifo[h % g.fifo_cap];
+    unsigned long long v;
+    while (((v = ld_acq64(c)) >> FRAME_BITS) != h + 1) {
+      if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return -kETIMEDOUT; }
+      __nanosleep(32);
+    }
+    st_rel64(c, ((h + g.fifo_cap) << FRAME_BITS) | MAX_FRAMES);
+    return (int)(v & MAX_FRAMES);
+  }
+}
+
+// ---------------------------------------------------------------- frames
+// Pin frame f for key.  Returns its state, or -1 if the mapping went stale.
+__device__ int frame_pin(const DevHandle& g, int f, unsigned long long key) {  // one thread
+  atomicAdd(&g.fpins[f], 1u);
+  __threadfence();
+  uint32_t st = ld_acq(&g.fstate[f]);
+  if (st == FR_RECLAIM || st == FR_EMPTY || ld_rlx64(&g.fkey[f]) != key) {
+    atomicSub(&g.fpins[f], 1u);
+    return -1;
+  }
+  return (int)st;
+}
+
+__device__ void frame_unpin(const DevHandle& g, int f) {  // one thread
+  __threadfence();
+  atomicSub(&g.fpins[f], 1u);
+}
+
+// Claim frame f for eviction.  from_fifo: only a still-consumed READY frame or a
+// returned (EMPTY, keyless) frame qualifies.  Returns 1 claimed, 0 pinned (try
+// later), -1 not a victim (stale entry).
+__device__ int frame_claim(const DevHandle& g, int f, bool from_fifo) {  // one thread
+  uint32_t st = ld_acq(&g.fstate[f]);
+  if (from_fifo) {
+    if (st == FR_READY) {
+      if (ld_rlx(&g.fconsumed[f]) < ld_rlx(&g.fvalid[f])) return -1;
+    } else if (!(st == FR_EMPTY && ld_rlx64(&g.fkey[f]) == KEY_NONE)) {
+      return -1;
+    }
+  } else if (st != FR_READY && st != FR_ERROR) {
+    return -1;
+  }
+  if (atomicCAS(&g.fstate[f], st, (uint32_t)FR_RECLAIM) != st) return -1;
+  __threadfence();
+  if (ld_rlx(&g.fpins[f]) != 0u) {
+    st_rel(&g.fstate[f], st);
+    return 0;
+  }
+  return 1;
+}
+
+// Unmap a claimed frame's old page and record the eviction.
+__device__ void evict_key(const DevHandle& g, int f, unsigned long long new_key, unsigned long long deadline) {
+  const int lane = lane_id();
+  unsigned long long old = 0;
+  uint32_t consumed = 0, valid = 0;
+  if (lane == 0) {
+    old = ld_rlx64(&g.fkey[f]);
+    consumed = ld_rlx(&g.fconsumed[f]);
+    valid = ld_rlx(&g.fvalid[f]);
+  }
+  old = bcast64(old);
+  if (old == KEY_NONE) return;
+  tab_remove(g, old, (uint32_t)f, deadline);
+  if (lane == 0) {
+    st_rlx64(&g.fkey[f], KEY_NONE);
+    stat_add(g, ST_EVICT, 1);
+    if (consumed < valid || valid == 0) stat_add(g, ST_EVICT_UNCONSUMED, 1);
+    if (g.trace_cap) {
+      unsigned long long i = atomicAdd(&g.ctrl->trace_evict_n.v, 1ull);
+      if (i < g.trace_cap) {
+        gfs_evict_rec r;
+        r.frame = (uint32_t)f;
+        r.old_fid = key_fid(old);
+        r.new_fid = key_fid(new_key);
+        r.reserved = 0;
+        r.old_page = key_page(old);
+        r.new_page = key_page(new_key);
+        g.trace_evict[i] = r;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Readahead may only use free / consumed frames above the reserve (victim classes 1, 2).
+__device__ bool ra_allowed(const DevHandle& g) {  // one thread
+  unsigned long long used = ld_rlx64(&g.ctrl->next_unused.v);
+  unsigned long long never = used >= g.n_frames ? 0 : g.n_frames - used;
+  unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
+  unsigned long long consumed = t > h ? t - h : 0;
+  return never + consumed > g.reserve;
+}
+
+// Victim selection (Section 5.1 restated; classes 1-3).  Returns a frame owned
+// by the caller with its old mapping removed, -1 if none (readahead), or a
+// negative errno.
+__device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long long seq0, unsigned long long new_key,
+                          unsigned long long deadline) {
+  const int lane = lane_id();
+  int r = 0;
+  if (for_ra) {
+    if (lane == 0) r = ra_allowed(g) ? 1 : 0;
+    if (!bcast(r)) return -1;
+  }
+  // (1) never-used frames, lowest index first
+  int f = -1;
+  if (lane == 0 && ld_rlx64(&g.ctrl->next_unused.v) < g.n_frames) {
+    unsigned long long u = atomicAdd(&g.ctrl->next_unused.v, 1ull);
+    if (u < g.n_frames) f = (int)u;
+  }
+  f = bcast(f);
+  if (f >= 0) return f;
+  // (2) consumed FIFO, oldest first; a pinned entry goes back to the tail
+  for (uint32_t it = 0; it <= g.fifo_cap; ++it) {
+    int c = -1, claimed = -1;
+    if (lane == 0) {
+      c = fifo_pop(g, deadline);
+      if (c >= 0) {
+        claimed = frame_claim(g, c, true);
+        if (claimed == 0) fifo_push(g, (uint32_t)c, deadline);
+      }
+    }
+    c = bcast(c);
+    claimed = bcast(claimed);
+    if (c == -1) break;
+    if (c < 0) return c;
+    if (claimed == 1) {
+      evict_key(g, c, new_key, deadline);
+      return c;
+    }
+  }
+  if (for_ra) return -1;
+  // (3) demand only: the least recently allocated unconsumed frame not
+  //     allocated during this gread
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    unsigned long long best = ~0ull;
+    int bf = -1;
+    for (uint32_t i = lane; i < g.n_frames; i += 32) {
+      uint32_t st = ld_rlx(&g.fstate[i]);
+      if (st != FR_READY && st != FR_ERROR) continue;
+      if (ld_rlx(&g.fpins[i]) != 0u) continue;
+      unsigned long long a = ld_rlx64(&g.faseq[i]);
+      if (a >= seq0) continue;
+      if (st == FR_READY && ld_rlx(&g.fconsumed[i]) >= ld_rlx(&g.fvalid[i])) continue;  // belongs to the FIFO
+      if (a < best) { best = a; bf = (int)i; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      unsigned long long ob = __shfl_xor_sync(kFull, best, o);
+      int of = __shfl_xor_sync(kFull, bf, o);
+      if (ob < best || (ob == best && of >= 0 && (bf < 0 || of < bf))) { best = ob; bf = of; }
+    }
+    if (bf < 0) return -kENOMEM;
+    int claimed = 0;
+    if (lane == 0) claimed = frame_claim(g, bf, false);
+    if (bcast(claimed) == 1) {
+      evict_key(g, bf, new_key, deadline);
+      return bf;
+    }
+  }
+  return -kEAGAIN;
+}
+
+// Give a frame that lost an insert race back as a keyless FIFO entry.
+__device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned long long deadline) {  // one thread
+  if (pinned) atomicSub(&g.fpins[f], 1u);
+  st_rlx64(&g.fkey[f], KEY_NONE);
+  st_rel(&g.fstate[f], FR_EMPTY);
+  fifo_push(g, (uint32_t)f, deadline);
+}
+
+// ---------------------------------------------------------------- request ring
+__device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
+                          const uint32_t* s_frames, unsigned long long deadline) {
+  const int lane = lane_id();
+  unsigned long long t = 0;
+  int ok = 1;
+  if (lane == 0) {
+    t = atomicAdd(&g.ctrl->ring_tail.v, 1ull);
+    RingSlot* s = (RingSlot*)(g.ring + (size_t)(t % g.rpc_slots) * g.slot_stride);
+    while (ld_acq_sys64(&s->seq) != t) {
+      if (now_ns() > deadline) { ok = 0; break; }
+      __nanosleep(64);
+    }
+  }
+  t = bcast64(t);
+  if (!bcast(ok)) {
+    if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
+    return -kETIMEDOUT;
+  }
+  RingSlot* s = (RingSlot*)(g.ring + (size_t)(t % g.rpc_slots) * g.slot_stride);
+  for (uint32_t i = lane; i < n; i += 32) st_sys32(&s->frames[i], s_frames[i]);
+  if (lane == 0) {
+    st_sys32(&s->fid, fid);
+    st_sys32(&s->npages, n);
+    st_sys64(&s->page_lo, page_lo);
+    st_sys32(&s->kind, kind);
+    st_sys32(&s->op, 1u);
+    st_sys64(&s->issue_ns, now_ns());
+  }
+  __syncwarp();
+  __threadfence_system();
+  __syncwarp();
+  if (lane == 0) {
+    st_rel_sys64(&s->seq, t + 1);
+    stat_add(g, ST_RPCS, 1);
+    if (g.trace_cap) {
+      unsigned long long i = atomicAdd(&g.ctrl->trace_rpc_n.v, 1ull);
+      if (i < g.trace_cap) {
+        gfs_rpc_rec r;
+        r.fid = fid;
+        r.kind = kind;
+        r.npages = n;
+        r.reserved = 0;
+        r.page_lo = page_lo;
+        g.trace_rpc[i] = r;
+      }
+    }
+  }
+  __syncwarp();
+  return 0;
+}
+
+// Allocate and install frames for [p, p + want): the first `demand` pages are
+// demand pages, the rest readahead.  Cut at EOF, at the first present page and
+// when no readahead victim is allowed.  Frames go to s_frames; the first is
+// pinned when pin_first.  Returns the page count, -EAGAIN when page p was
+// inserted by someone else meanwhile, or a negative errno.
+__device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t want,
+                             uint32_t demand, bool pin_first, unsigned long long seq0, unsigned long long deadline,
+                             uint32_t* s_frames) {
+  const int lane = lane_id();
+  if (want > g.max_rpc_pages) want = g.max_rpc_pages;
+  uint32_t n = 0;
+  for (uint32_t i = 0; i < want; ++i) {
+    const unsigned long long q = p + i;
+    if (q >= fi.npages) break;
+    const unsigned long long key = make_key(fid, q);
+    if (i > 0 && tab_lookup(g, key) >= 0) break;
+    const bool is_ra = i >= demand;
+    int f = take_frame(g, is_ra, seq0, key, deadline);
+    while (f < 0 && !is_ra && i == 0) {  // the first demand page waits for a victim
+      if (now_ns() > deadline) {
+        if (lane == 0) stat_add(g, ST_ENOMEM, 1);
+        return -kENOMEM;
+      }
+      __nanosleep(256);
+      f = take_frame(g, false, seq0, key, deadline);
+    }
+    if (f < 0) break;
+    const bool pin = pin_first && i == 0;
+    if (lane == 0) {  // install: metadata first, then FILLING, then the table entry
+      st_rlx64(&g.fkey[f], key);
+      st_rlx(&g.fconsumed[f], 0u);
+      st_rlx(&g.fwindow[f], 0u);
+      st_rlx(&g.fmark[f], 0u);
+      st_rlx(&g.fvalid[f], expected_valid(g, fi, q));
+      st_rlx64(&g.faseq[f], atomicAdd(&g.ctrl->alloc_counter.v, 1ull));
+      __threadfence();
+      if (pin) atomicAdd(&g.fpins[f], 1u);
+      st_rel(&g.fstate[f], FR_FILLING);
+    }
+    __syncwarp();
+    int r = tab_insert(g, key, (uint32_t)f, deadline);
+    if (r != f) {
+      if (lane == 0) frame_return(g, f, pin, deadline);
+      __syncwarp();
+      if (i == 0) return r < 0 ? r : -kEAGAIN;
+      break;
+    }
+    if (lane == 0) {
+      s_frames[n] = (uint32_t)f;
+      if (g.fetch_count && fid == 0 && q < g.debug_pages) atomicAdd(&g.fetch_count[q], 1u);
+    }
+    __syncwarp();
+    ++n;
+  }
+  return (int)n;
+}
+
+// Finish a request: record windows and the readahead mark, send it, count it.
+__device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t n,
+                              uint32_t demand, uint32_t window, uint32_t kind, unsigned long long mark_end,
+                              int mark_idx, const uint32_t* s_frames, unsigned long long deadline) {
+  const int lane = lane_id();
+  for (uint32_t i = lane; i < n; i += 32) st_rlx(&g.fwindow[s_frames[i]], window);
+  if (lane == 0) {
+    if (mark_idx >= 0) st_rlx(&g.fmark[s_frames[mark_idx]], (uint32_t)(mark_end + 1));
+    unsigned long long bytes = 0;
+    for (uint32_t i = 0; i < n; ++i) bytes += expected_valid(g, fi, p + i);
+    stat_add(g, ST_PAGES, n);
+    stat_add(g, ST_BYTES, bytes);
+    if (kind == GFS_KIND_SYNC_RA) stat_add(g, ST_RA_SYNC, n - demand);
+    if (kind == GFS_KIND_ASYNC_RA) stat_add(g, ST_RA_ASYNC, n);
+    __threadfence();
+  }
+  __syncwarp();
+  return rpc_submit(g, fid, p, n, kind, s_frames, deadline);
+}
+
+// R4: asynchronous readahead of [end, end + min(Wmax, 2T)) from a readahead mark.
+__device__ void async_readahead(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long end, uint32_t t,
+                                unsigned long long seq0, unsigned long long deadline, uint32_t* s_frames) {
+  if (end >= fi.npages) return;
+  if (tab_lookup(g, make_key(fid, end)) >= 0) return;
+  uint32_t want = 2 * t < g.ra_cap ? 2 * t : g.ra_cap;
+  if (want == 0) return;
+  int n = request_range(g, fid, fi, end, want, 0, false, seq0, deadline, s_frames);
+  if (n <= 0) return;
+  finish_request(g, fid, fi, end, (uint32_t)n, 0, (uint32_t)n, GFS_KIND_ASYNC_RA, end + (uint32_t)n, 0, s_frames,
+                 deadline);
+}
+
+// R1-R3: a miss on page p (p1 = last page of the gread).  Returns the pinned,
+// FILLING frame of page p, -EAGAIN to look p up again, or a negative errno.
+__device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
+                           unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
+                           uint32_t* s_frames) {
+  const int lane = lane_id();
+  if (lane == 0) stat_add(g, ST_MISSES, 1);
+  const bool ra = g.mode == GFS_MODE_READAHEAD && fi.ra;
+  uint32_t d = 1, T = 1;
+  bool seq = false;
+  if (ra) {
+    while (p + d <= p1 && d < g.max_rpc_pages && tab_lookup(g, make_key(fid, p + d)) < 0) ++d;  // R2
+    int prev = -1;
+    seq = p == 0;                                                                              // R3
+    if (!seq) {
+      prev = tab_lookup(g, make_key(fid, p - 1));
+      seq = prev >= 0;
+    }
+    if (!seq && stream >= 0 && (uint32_t)stream < g.max_streams) {
+      unsigned long long le = 0;
+      if (lane == 0) le = ld_rlx64(&g.last_end[(size_t)stream * g.max_files + fid]);
+      seq = bcast64(le) == p + 1;  // stored as end page + 1
+    }
+    if (!seq) {
+      T = d;
+    } else {
+      uint32_t tprev = 0;
+      if (prev >= 0 && lane == 0) tprev = ld_rlx(&g.fwindow[prev]);
+      tprev = (uint32_t)bcast((int)tprev);
+      uint32_t grow = 4 * d > 2 * tprev ? 4 * d : 2 * tprev;
+      T = d + g.ra_cap < grow ? d + g.ra_cap : grow;
+    }
+    if (T > g.max_rpc_pages) T = g.max_rpc_pages;
+    if (d > T) d = T;
+  }
+  int n = request_range(g, fid, fi, p, T, d, true, seq0, deadline, s_frames);
+  if (n < 0) return n;
+  const uint32_t kind = (uint32_t)n > d ? GFS_KIND_SYNC_RA : GFS_KIND_DEMAND;
+  const uint32_t window = (ra && seq) ? (uint32_t)n : 0u;
+  const int mark_idx = (uint32_t)n > d ? (int)d : -1;
+  int f0 = 0;
+  if (lane == 0) f0 = (int)s_frames[0];
+  f0 = bcast(f0);
+  int r = finish_request(g, fid, fi, p, (uint32_t)n, d, window, kind, p + (uint32_t)n, mark_idx, s_frames, deadline);
+  if (r < 0) {
+    if (lane == 0) frame_unpin(g, f0);
+    return r;
+  }
+  return f0;
+}
+
+// Wait until frame f leaves FILLING.  Returns the state or -ETIMEDOUT.
+__device__ int wait_filled(const DevHandle& g, int f, unsigned long long deadline) {  // one thread
+  uint32_t st;
+  unsigned ns = 64;
+  while ((st = ld_acq(&g.fstate[f])) == FR_FILLING) {
+    if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return -kETIMEDOUT; }
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  return (int)st;
+}
+
+// Make page p resident and pinned for the caller (warp 0).  Returns its frame or -errno.
+__device__ int acquire_page(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
+                            unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
+                            uint32_t* s_frames) {
+  const int lane = lane_id();
+  const unsigned long long key = make_key(fid, p);
+  for (;;) {
+    int late = 0;
+    if (lane == 0) late = now_ns() > deadline;
+    if (bcast(late)) {
+      if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
+      return -kETIMEDOUT;
+    }
+    int f = tab_lookup(g, key);
+    if (f >= 0) {
+      int st = -1;
+      if (lane == 0) {
+        st = frame_pin(g, f, key);
+        if (st >= 0) {
+          stat_add(g, ST_HITS, 1);
+          if (st == FR_FILLING) {
+            stat_add(g, ST_COALESCED, 1);
+            st = wait_filled(g, f, deadline);
+          }
+          if (st != FR_READY) frame_unpin(g, f);
+        } else {
+          stat_add(g, ST_RETRIES, 1);
+        }
+      }
+      st = bcast(st);
+      if (st == -1) continue;
+      if (st == FR_ERROR) {
+        if (lane == 0) stat_add(g, ST_EIO, 1);
+        return -kEIO;
+      }
+      if (st < 0) return st;
+      if (st != FR_READY) continue;
+      if (g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra) {  // R4
+        uint32_t m = 0, w = 0;
+        if (lane == 0) {
+          m = atomicExch(&g.fmark[f], 0u);
+          w = ld_rlx(&g.fwindow[f]);
+        }
+        m = (uint32_t)bcast((int)m);
+        w = (uint32_t)bcast((int)w);
+        if (m) async_readahead(g, fid, fi, (unsigned long long)m - 1, w, seq0, deadline, s_frames);
+      }
+      return f;
+    }
+    int r = handle_miss(g, stream, fid, fi, p, p1, seq0, deadline, s_frames);
+    if (r == -kEAGAIN) {
+      if (lane == 0) stat_add(g, ST_RETRIES, 1);
+      continue;
+    }
+    if (r < 0) return r;
+    int st = 0;
+    if (lane == 0) {
+      st = wait_filled(g, r, deadline);
+      if (st != FR_READY) frame_unpin(g, r);
+      if (st == FR_ERROR) stat_add(g, ST_EIO, 1);
+    }
+    st = bcast(st);
+    if (st == FR_ERROR) return -kEIO;
+    if (st < 0) return st;
+    if (st != FR_READY) return -kEIO;
+    return r;
+  }
+}
+
+// R5: account the delivered bytes, unpin, and queue the frame once fully consumed.
+__device__ void release_page(const DevHandle& g, int f, uint32_t nbytes, unsigned long long deadline) {  // one thread
+  uint32_t c = atomicAdd(&g.fconsumed[f], nbytes);
+  uint32_t v = ld_rlx(&g.fvalid[f]);
+  bool push = c < v && c + nbytes >= v;
+  frame_unpin(g, f);
+  if (push) fifo_push(g, (uint32_t)f, deadline);
+}
+
+// ---------------------------------------------------------------- copy-out
+// Checksum accumulators of the stride-scan consumer (per thread).
+struct Sums {
+  unsigned long long sum, hash;
+};
+
+// Add 16 bytes starting at absolute file offset `o` to the checksums:
+// sum += sum of bytes, hash += sum of byte_j * (o + j + 1).
+__device__ __forceinline__ void sums_add16(Sums& s, uint4 v, unsigned long long o) {
+  uint32_t s16 = __dp4a(v.x, 0x01010101u, 0u);
+  s16 = __dp4a(v.y, 0x01010101u, s16);
+  s16 = __dp4a(v.z, 0x01010101u, s16);
+  s16 = __dp4a(v.w, 0x01010101u, s16);
+  uint32_t w16 = __dp4a(v.x, 0x03020100u, 0u);
+  w16 = __dp4a(v.y, 0x07060504u, w16);
+  w16 = __dp4a(v.z, 0x0b0a0908u, w16);
+  w16 = __dp4a(v.w, 0x0f0e0d0cu, w16);
+  s.sum += s16;
+  s.hash += (o + 1) * (unsigned long long)s16 + w16;
+}
+__device__ __forceinline__ void sums_add1(Sums& s, uint8_t b, unsigned long long o) {
+  s.sum += b;
+  s.hash += (o + 1) * (unsigned long long)b;
+}
+
+// Copy n bytes of a cache frame (src) to the user buffer (dst).  Frame data is
+// read through L2 (ld.global.cg): frames are rewritten by the copy engine, so
+// L1 may hold an older page.  With FUSED the checksums of the copied bytes are
+// accumulated on the way (src_off = file offset of src[0]).
+template <bool FUSED>
+__device__ __forceinline__ void copy_out(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n,
+                                         unsigned long long src_off, Sums& acc) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t phase_s = (uint32_t)((uintptr_t)src & 15), phase_d = (uint32_t)((uintptr_t)dst & 15);
+  if (phase_s == phase_d) {
+    uint32_t head = (16 - phase_s) & 15;
+    if (head > n) head = n;
+    for (uint32_t i = tid; i < head; i += nt) {
+      uint8_t b = __ldcg(src + i);
+      dst[i] = b;
+      if (FUSED) sums_add1(acc, b, src_off + i);
+    }
+    const uint32_t n16 = (n - head) >> 4;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    uint32_t i = tid;
+    for (; i + 3 * nt < n16; i += 4 * nt) {
+      uint4 a = __ldcg(s4 + i), b = __ldcg(s4 + i + nt), c = __ldcg(s4 + i + 2 * nt), d = __ldcg(s4 + i + 3 * nt);
+      d4[i] = a;
+      d4[i + nt] = b;
+      d4[i + 2 * nt] = c;
+      d4[i + 3 * nt] = d;
+      if (FUSED) {
+        const unsigned long long o = src_off + head + 16ull * i;
+        sums_add16(acc, a, o);
+        sums_add16(acc, b, o + 16ull * nt);
+        sums_add16(acc, c, o + 32ull * nt);
+        sums_add16(acc, d, o + 48ull * nt);
+      }
+    }
+    for (; i < n16; i += nt) {
+      uint4 a = __ldcg(s4 + i);
+      d4[i] = a;
+      if (FUSED) sums_add16(acc, a, src_off + head + 16ull * i);
+    }
+    for (uint32_t j = head + 16 * n16 + tid; j < n; j += nt) {
+      uint8_t b = __ldcg(src + j);
+      dst[j] = b;
+      if (FUSED) sums_add1(acc, b, src_off + j);
+    }
+  } else {
+    for (uint32_t j = tid; j < n; j += nt) {
+      uint8_t b = __ldcg(src + j);
+      dst[j] = b;
+      if (FUSED) sums_add1(acc, b, src_off + j);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- gread
+// Threadblock-collective read of [off, off + len) of file `fid` into buf.
+// Every thread of the block must call it with the same arguments.  `stream`
+// identifies the reader for sequential detection (the threadblock).  Returns
+// the byte count (short at EOF, 0 at or past EOF) or a negative errno.
+template <bool FUSED>
+__device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigned long long off,
+                                unsigned long long len, uint8_t* buf, Sums& acc) {
+  __shared__ int s_frame;
+  __shared__ unsigned long long s_seq0;
+  __shared__ uint32_t s_frames[MAX_RPC_PAGES];
+  const uint32_t tid = threadIdx.x;
+  if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
+  const FileDev fi = g.files[fid];
+  if (!fi.open) return -kEBADF;
+  if (tid == 0) stat_add(g, ST_GREADS, 1);
+  if (off >= fi.size || len == 0) return 0;
+  const unsigned long long end = (len > fi.size - off) ? fi.size : off + len;
+  const unsigned long long p0 = off >> g.page_shift, p1 = (end - 1) >> g.page_shift;
+  if (tid == 0) s_seq0 = ld_rlx64(&g.ctrl->alloc_counter.v);
+  __syncthreads();
+  const unsigned long long seq0 = s_seq0;
+  const unsigned long long deadline = now_ns() + g.timeout_ns;
+  long long err = 0;
+  for (unsigned long long p = p0; p <= p1; ++p) {
+    if (tid < 32) {
+      int r = acquire_page(g, stream, (uint32_t)fid, fi, p, p1, seq0, deadline, s_frames);
+      if (tid == 0) s_frame = r;
+    }
+    __syncthreads();
+    const int f = s_frame;
+    if (f < 0) {
+      err = f;
+      break;
+    }
+    const unsigned long long base = p << g.page_shift;
+    const unsigned long long lo = (off > base ? off : base) - base;
+    const unsigned long long hi = (end < base + g.page_size ? end : base + g.page_size) - base;
+    copy_out<FUSED>(g.frames + ((size_t)f << g.page_shift) + lo, buf + (base + lo - off), (uint32_t)(hi - lo),
+                    base + lo, acc);
+    __syncthreads();
+    if (tid == 0) release_page(g, f, (uint32_t)(hi - lo), deadline);
+  }
+  if (tid == 0 && stream >= 0 && (uint32_t)stream < g.max_streams)
+    st_rlx64(&g.last_end[(size_t)stream * g.max_files + fid], p1 + 2);  // end page + 1
+  __syncthreads();
+  return err ? err : (long long)(end - off);
+}
+
+__device__ __forceinline__ long long gread(const DevHandle& g, int stream, int fid, unsigned long long off,
+                                           unsigned long long len, void* buf) {
+  Sums unused{0, 0};
+  return gread_impl<false>(g, stream, fid, off, len, (uint8_t*)buf, unused);
+}
+
+// File size of an open fid, or -EBADF.
+__device__ __forceinline__ long long gfstat_size(const DevHandle& g, int fid) {
+  if (fid < 0 || (uint32_t)fid >= g.max_files || !g.files[fid].open) return -kEBADF;
+  return (long long)g.files[fid].size;
+}
+
+}  // namespace dev
+}  // namespace gfs

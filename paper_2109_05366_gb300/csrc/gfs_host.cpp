@@ -1,0 +1,959 @@
+// Host runtime and C ABI of the GPU file-read path (see include/gfs.h).
+#include "gfs_host.h"
+
+#include <cuda.h>
+#include <errno.h>
+#include <fcntl.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gfs_service.h"
+
+using namespace gfs;
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return 0;
+  if (e == cudaErrorMemoryAllocation) return -ENOMEM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return -ENODEV;
+  return -EINVAL;
+}
+#define CK(x)                           \
+  do {                                  \
+    int rc_ = cuda_err(x);              \
+    if (rc_) return rc_;                \
+  } while (0)
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+uint64_t next_pow2(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+uint32_t log2u(uint64_t v) {
+  uint32_t s = 0;
+  while ((1ull << s) < v) ++s;
+  return s;
+}
+
+// Stream memory operations from the driver (the frame state is written on the
+// I/O thread's stream right after the copies of the frame).
+typedef CUresult (*BatchMemOpFn)(CUstream, unsigned int, CUstreamBatchMemOpParams*, unsigned int);
+typedef CUresult (*WriteValue32Fn)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+BatchMemOpFn g_batch = nullptr;
+WriteValue32Fn g_write32 = nullptr;
+
+int load_driver_fns() {
+  if (g_batch || g_write32) return 0;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuStreamBatchMemOp", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_batch = (BatchMemOpFn)fn;
+  fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_write32 = (WriteValue32Fn)fn;
+  return (g_batch || g_write32) ? 0 : -ENOSYS;
+}
+
+// GFS_XFER_DMA sink: copy engine into the frames, then a stream write of each
+// frame state (the write is ordered after the copies on the same stream and
+// carries a memory barrier, so a GPU reader that sees READY sees the data).
+class DmaSink : public Sink {
+ public:
+  DmaSink(int device, uint8_t* d_frames, uint32_t* d_state, uint32_t page_shift, size_t staging_bytes)
+      : device_(device), d_frames_(d_frames), d_state_(d_state), page_shift_(page_shift), bytes_(staging_bytes) {}
+  int init() {
+    CK(cudaSetDevice(device_));
+    CK(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaHostAlloc((void**)&stg_[k], bytes_, cudaHostAllocDefault));
+      CK(cudaEventCreateWithFlags(&ev_[k], cudaEventDisableTiming));
+    }
+    ops_.reserve(MAX_RPC_PAGES);
+    return 0;
+  }
+  ~DmaSink() override {
+    cudaSetDevice(device_);
+    if (stream_) cudaStreamSynchronize(stream_);
+    for (int k = 0; k < 2; ++k) {
+      if (stg_[k]) cudaFreeHost(stg_[k]);
+      if (ev_[k]) cudaEventDestroy(ev_[k]);
+    }
+    if (stream_) cudaStreamDestroy(stream_);
+  }
+  void thread_init() override { cudaSetDevice(device_); }
+  uint8_t* staging(int k) override { return stg_[k]; }
+  void wait_staging(int k) override {
+    if (pending_[k]) cudaEventSynchronize(ev_[k]);
+    pending_[k] = false;
+  }
+  int copy(uint32_t frame, const uint8_t* src, size_t bytes) override {
+    return cuda_err(cudaMemcpyAsync(d_frames_ + ((size_t)frame << page_shift_), src, bytes, cudaMemcpyHostToDevice,
+                                    stream_));
+  }
+  int set_state(uint32_t frame, uint32_t state) override {
+    CUstreamBatchMemOpParams p;
+    memset(&p, 0, sizeof(p));
+    p.writeValue.operation = CU_STREAM_MEM_OP_WRITE_VALUE_32;
+    p.writeValue.address = (CUdeviceptr)(d_state_ + frame);
+    p.writeValue.value = state;
+    p.writeValue.flags = CU_STREAM_WRITE_VALUE_DEFAULT;
+    ops_.push_back(p);
+    return 0;
+  }
+  int end_chunk(int k) override {
+    int rc = flush();
+    cudaEventRecord(ev_[k], stream_);
+    pending_[k] = true;
+    // Submit now: the driver may hold queued work until the stream is touched
+    // again, and a GPU reader may be waiting on exactly these state writes.
+    cudaStreamQuery(stream_);
+    return rc;
+  }
+  void drain() override {
+    if (stream_) cudaStreamSynchronize(stream_);
+    pending_[0] = pending_[1] = false;
+  }
+
+ private:
+  int flush() {
+    int rc = 0;
+    if (ops_.empty()) return 0;
+    if (g_batch) {
+      for (size_t i = 0; i < ops_.size(); i += 128) {
+        unsigned cnt = (unsigned)std::min<size_t>(128, ops_.size() - i);
+        if (g_batch((CUstream)stream_, cnt, ops_.data() + i, 0) != CUDA_SUCCESS) rc = -EIO;
+      }
+    } else {
+      for (auto& p : ops_)
+        if (g_write32((CUstream)stream_, p.writeValue.address, p.writeValue.value, 0) != CUDA_SUCCESS) rc = -EIO;
+    }
+    ops_.clear();
+    return rc;
+  }
+  int device_;
+  uint8_t* d_frames_;
+  uint32_t* d_state_;
+  uint32_t page_shift_;
+  size_t bytes_;
+  cudaStream_t stream_ = nullptr;
+  uint8_t* stg_[2] = {nullptr, nullptr};
+  cudaEvent_t ev_[2] = {nullptr, nullptr};
+  bool pending_[2] = {false, false};
+  std::vector<CUstreamBatchMemOpParams> ops_;
+};
+
+// Host-memory sink for the CPU self-test of the ring and service.
+class HostSink : public Sink {
+ public:
+  HostSink(uint8_t* frames, uint32_t* states, uint32_t page_shift, size_t staging_bytes)
+      : frames_(frames), states_(states), shift_(page_shift) {
+    buf_[0].resize(staging_bytes);
+    buf_[1].resize(staging_bytes);
+  }
+  uint8_t* staging(int k) override { return buf_[k].data(); }
+  void wait_staging(int) override {}
+  int copy(uint32_t frame, const uint8_t* src, size_t bytes) override {
+    memcpy(frames_ + ((size_t)frame << shift_), src, bytes);
+    return 0;
+  }
+  int set_state(uint32_t frame, uint32_t state) override {
+    __atomic_store_n(&states_[frame], state, __ATOMIC_RELEASE);
+    return 0;
+  }
+  int end_chunk(int) override { return 0; }
+  void drain() override {}
+
+ private:
+  uint8_t* frames_;
+  uint32_t* states_;
+  uint32_t shift_;
+  std::vector<uint8_t> buf_[2];
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
+  if (fid >= ctx->files.size()) return false;
+  const HostFile& f = ctx->files[fid];
+  if (!f.open) return false;
+  out->fd = f.fd;
+  out->size = f.size;
+  return true;
+}
+
+int push_file(gfs_ctx* ctx, int fid) {
+  const HostFile& hf = ctx->files[fid];
+  FileDev fd{};
+  fd.size = hf.size;
+  fd.npages = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  fd.open = hf.open ? 1u : 0u;
+  fd.ra = (hf.open && (hf.flags & 3) == GFS_RDONLY && hf.advice != GFS_ADV_RANDOM) ? 1u : 0u;
+  CK(cudaMemcpy(ctx->dev.files + fid, &fd, sizeof(fd), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gfs_abi_version(void) { return GFS_ABI_VERSION; }
+
+const char* gfs_strerror(int err) {
+  switch (-err) {
+    case 0: return "success";
+    case EINVAL: return "invalid argument";
+    case EBADF: return "bad file id";
+    case ENOMEM: return "out of memory (or no victim frame)";
+    case EIO: return "host read failed";
+    case ENODEV: return "no CUDA device";
+    case ETIMEDOUT: return "device wait timed out";
+    case ENOSYS: return "stream memory operations unavailable";
+    case EMFILE: return "too many open files";
+    case EAGAIN: return "resource temporarily unavailable";
+    default: return strerror(-err);
+  }
+}
+
+int gfs_config_default(gfs_config* c) {
+  if (!c) return -EINVAL;
+  memset(c, 0, sizeof(*c));
+  c->cache_bytes = 1ull << 30;
+  c->timeout_ns = 10ull * 1000 * 1000 * 1000;
+  c->page_size = 512u << 10;
+  c->mode = GFS_MODE_READAHEAD;
+  c->ra_cap_pages = 8;
+  c->async_ra = 1;
+  c->reserve_frames = 0;
+  c->rpc_slots = 128;
+  c->max_rpc_pages = 64;
+  c->host_threads = 16;
+  c->staging_bytes = 4u << 20;
+  c->max_streams = 4096;
+  c->max_files = 16;
+  c->trace_capacity = 0;
+  c->xfer = GFS_XFER_DMA;
+  c->debug_counts = 0;
+  c->device = 0;
+  return 0;
+}
+
+int gfs_shutdown(gfs_ctx* ctx) {
+  if (!ctx) return 0;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->io) {
+    ctx->io->stop();
+    delete ctx->io;
+    ctx->io = nullptr;
+  }
+  cudaDeviceSynchronize();
+  for (auto& f : ctx->files)
+    if (f.fd >= 0) close(f.fd);
+  if (ctx->d_arena) cudaFree(ctx->d_arena);
+  if (ctx->d_frames) cudaFree(ctx->d_frames);
+  if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
+  if (ctx->d_out) cudaFree(ctx->d_out);
+  if (ctx->h_out) cudaFreeHost(ctx->h_out);
+  if (ctx->dev.fetch_count) cudaFree(ctx->dev.fetch_count);
+  if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+  delete ctx;
+  return 0;
+}
+
+int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
+  if (!cfg_in || !out) return -EINVAL;
+  const gfs_config c = *cfg_in;
+  if (!is_pow2(c.page_size) || c.page_size < 4096 || c.page_size > (64u << 20)) return -EINVAL;
+  if (c.cache_bytes < c.page_size) return -EINVAL;
+  if (c.mode > GFS_MODE_ONDEMAND || c.xfer != GFS_XFER_DMA) return -EINVAL;
+  if (c.rpc_slots < 1 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
+  if (c.host_threads < 1 || c.host_threads > 256 || c.max_files < 1 || c.max_files > MAX_FILES) return -EINVAL;
+  if (c.max_streams < 1 || c.timeout_ns == 0) return -EINVAL;
+  const uint64_t F64 = c.cache_bytes / c.page_size;
+  if (F64 > MAX_FRAMES) return -EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return -ENODEV;
+  if (c.device < 0 || c.device >= ndev) return -EINVAL;
+  int rc = load_driver_fns();
+  if (rc) return rc;
+  CK(cudaSetDevice(c.device));
+
+  gfs_ctx* ctx = new (std::nothrow) gfs_ctx();
+  if (!ctx) return -ENOMEM;
+  ctx->cfg = c;
+  DevHandle& g = ctx->dev;
+  const uint32_t F = (uint32_t)F64;
+  g.timeout_ns = c.timeout_ns;
+  g.cache_bytes = (uint64_t)F * c.page_size;
+  g.page_size = c.page_size;
+  g.page_shift = log2u(c.page_size);
+  g.n_frames = F;
+  g.mode = c.mode;
+  g.ra_cap = c.ra_cap_pages;
+  g.async_ra = c.async_ra ? 1 : 0;
+  g.max_rpc_pages = c.max_rpc_pages;
+  g.reserve = c.reserve_frames;
+  g.nbuckets = (uint32_t)std::max<uint64_t>(4, next_pow2(((uint64_t)F * 4 + BUCKET - 1) / BUCKET));
+  g.max_streams = c.max_streams;
+  g.max_files = c.max_files;
+  g.trace_cap = c.trace_capacity;
+  g.rpc_slots = c.rpc_slots;
+  g.slot_stride = slot_stride(c.max_rpc_pages);
+  g.fifo_cap = F;
+
+  // device arena
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_fkey = take((size_t)F * 8), o_fstate = take((size_t)F * 4), o_fpins = take((size_t)F * 4),
+               o_fcons = take((size_t)F * 4), o_fvalid = take((size_t)F * 4), o_fwin = take((size_t)F * 4),
+               o_fmark = take((size_t)F * 4), o_faseq = take((size_t)F * 8),
+               o_tab = take((size_t)g.nbuckets * BUCKET * 8), o_tlock = take((size_t)g.nbuckets * 4),
+               o_tovf = take((size_t)g.nbuckets * 4), o_fifo = take((size_t)F * 8), o_ctrl = take(sizeof(Ctrl)),
+               o_files = take((size_t)c.max_files * sizeof(FileDev)),
+               o_last = take((size_t)c.max_streams * c.max_files * 8),
+               o_trpc = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_rpc_rec)),
+               o_tev = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_evict_rec));
+  ctx->arena_bytes = off;
+  rc = cuda_err(cudaMalloc(&ctx->d_arena, off));
+  if (!rc) rc = cuda_err(cudaMemset(ctx->d_arena, 0, off));
+  if (!rc) rc = cuda_err(cudaMalloc((void**)&ctx->d_frames, (size_t)F << g.page_shift));
+  if (rc) {
+    gfs_shutdown(ctx);
+    return rc;
+  }
+  uint8_t* a = (uint8_t*)ctx->d_arena;
+  g.frames = ctx->d_frames;
+  g.fkey = (unsigned long long*)(a + o_fkey);
+  g.fstate = (uint32_t*)(a + o_fstate);
+  g.fpins = (uint32_t*)(a + o_fpins);
+  g.fconsumed = (uint32_t*)(a + o_fcons);
+  g.fvalid = (uint32_t*)(a + o_fvalid);
+  g.fwindow = (uint32_t*)(a + o_fwin);
+  g.fmark = (uint32_t*)(a + o_fmark);
+  g.faseq = (unsigned long long*)(a + o_faseq);
+  g.tab = (unsigned long long*)(a + o_tab);
+  g.tlock = (uint32_t*)(a + o_tlock);
+  g.tovf = (uint32_t*)(a + o_tovf);
+  g.fifo = (unsigned long long*)(a + o_fifo);
+  g.ctrl = (Ctrl*)(a + o_ctrl);
+  g.files = (FileDev*)(a + o_files);
+  g.last_end = (unsigned long long*)(a + o_last);
+  g.trace_rpc = (gfs_rpc_rec*)(a + o_trpc);
+  g.trace_evict = (gfs_evict_rec*)(a + o_tev);
+  g.fetch_count = nullptr;
+  g.debug_pages = 0;
+
+  // request ring in mapped pinned memory
+  const size_t ring_bytes = (size_t)c.rpc_slots * g.slot_stride;
+  rc = cuda_err(cudaHostAlloc((void**)&ctx->h_ring, ring_bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  if (rc) {
+    gfs_shutdown(ctx);
+    return rc;
+  }
+  memset(ctx->h_ring, 0, ring_bytes);
+  for (uint32_t i = 0; i < c.rpc_slots; ++i) ((RingSlot*)(ctx->h_ring + (size_t)i * g.slot_stride))->seq = i;
+  void* d_ring = nullptr;
+  rc = cuda_err(cudaHostGetDevicePointer(&d_ring, ctx->h_ring, 0));
+  if (rc) {
+    gfs_shutdown(ctx);
+    return rc;
+  }
+  g.ring = (uint8_t*)d_ring;
+
+  ctx->files.resize(c.max_files);
+  rc = launch_reset(g, 0);
+  if (!rc) rc = cuda_err(cudaDeviceSynchronize());
+  if (rc) {
+    gfs_shutdown(ctx);
+    return rc;
+  }
+
+  ServiceConfig sc;
+  sc.ring = ctx->h_ring;
+  sc.slots = c.rpc_slots;
+  sc.slot_stride = g.slot_stride;
+  sc.page_size = c.page_size;
+  sc.page_shift = g.page_shift;
+  sc.staging_pages = std::max<uint32_t>(1, c.staging_bytes / c.page_size);
+  sc.threads = c.host_threads;
+  sc.n_frames = F;
+  const size_t stg = (size_t)sc.staging_pages * c.page_size;
+  ctx->io = new IoService(
+      sc,
+      [ctx, stg](int) -> Sink* {
+        DmaSink* s = new (std::nothrow) DmaSink(ctx->cfg.device, ctx->d_frames, ctx->dev.fstate, ctx->dev.page_shift, stg);
+        if (s && s->init() != 0) {
+          delete s;
+          return nullptr;
+        }
+        return s;
+      },
+      [ctx](uint32_t fid, FileView* fv) { return file_lookup(ctx, fid, fv); });
+  rc = ctx->io->start();
+  if (rc) {
+    gfs_shutdown(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return 0;
+}
+
+int gfs_set_faults(gfs_ctx* ctx, uint32_t eio_every, uint32_t short_every, uint32_t delay_us) {
+  if (!ctx || !ctx->io) return -EINVAL;
+  ctx->io->set_faults(eio_every, short_every, delay_us);
+  return 0;
+}
+
+int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
+  if (!ctx || !path || !fid) return -EINVAL;
+  if ((flags & 3) != GFS_RDONLY && (flags & 3) != GFS_RDWR) return -EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  int slot = -1;
+  for (size_t i = 0; i < ctx->files.size(); ++i)
+    if (!ctx->files[i].open) {
+      slot = (int)i;
+      break;
+    }
+  if (slot < 0) return -EMFILE;
+  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return -errno;
+  struct stat st;
+  if (fstat(fd, &st) != 0) {
+    int e = errno;
+    close(fd);
+    return -e;
+  }
+  HostFile& hf = ctx->files[slot];
+  hf.fd = fd;
+  hf.size = (uint64_t)st.st_size;
+  hf.flags = flags;
+  hf.advice = GFS_ADV_NORMAL;
+  hf.open = true;
+  hf.path = path;
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (slot == 0 && ctx->cfg.debug_counts) {
+    const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+    if (ctx->dev.fetch_count) cudaFree(ctx->dev.fetch_count);
+    ctx->dev.fetch_count = nullptr;
+    ctx->dev.debug_pages = 0;
+    if (np) {
+      CK(cudaMalloc((void**)&ctx->dev.fetch_count, np * 4));
+      CK(cudaMemset(ctx->dev.fetch_count, 0, np * 4));
+      ctx->dev.debug_pages = (uint32_t)std::min<uint64_t>(np, 0xffffffffull);
+    }
+  }
+  int rc = push_file(ctx, slot);
+  if (rc) {
+    close(fd);
+    hf = HostFile();
+    return rc;
+  }
+  *fid = slot;
+  return 0;
+}
+
+int gfs_close(gfs_ctx* ctx, int fid) {
+  if (!ctx || fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  HostFile& hf = ctx->files[fid];
+  hf.open = false;
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = push_file(ctx, fid);
+  close(hf.fd);
+  hf = HostFile();
+  return rc;
+}
+
+int gfs_fadvise(gfs_ctx* ctx, int fid, int advice) {
+  if (!ctx || fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
+  if (advice < GFS_ADV_NORMAL || advice > GFS_ADV_RANDOM) return -EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->files[fid].advice = advice;
+  CK(cudaSetDevice(ctx->cfg.device));
+  return push_file(ctx, fid);
+}
+
+int gfs_fstat(gfs_ctx* ctx, int fid, gfs_stat* st) {
+  if (!ctx || !st) return -EINVAL;
+  if (fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
+  memset(st, 0, sizeof(*st));
+  st->size = ctx->files[fid].size;
+  st->page_size = ctx->cfg.page_size;
+  st->flags = (uint32_t)ctx->files[fid].flags;
+  st->advice = (uint32_t)ctx->files[fid].advice;
+  return 0;
+}
+
+int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
+  if (!ctx) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(s));
+  unsigned long long tail = 0;
+  CK(cudaMemcpy(&tail, &ctx->dev.ctrl->ring_tail.v, 8, cudaMemcpyDeviceToHost));
+  const double t0 = now_s();
+  while (ctx->io->served() < tail) {
+    if (now_s() - t0 > (double)ctx->cfg.timeout_ns * 1e-9 + 5.0) return -ETIMEDOUT;
+    usleep(50);
+  }
+  ctx->io->drain_sinks();
+  ctx->io->stats.requests = 0;
+  ctx->io->stats.preads = 0;
+  ctx->io->stats.bytes = 0;
+  ctx->io->stats.copies = 0;
+  ctx->io->stats.errors = 0;
+  if (ctx->dev.fetch_count) CK(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, s));
+  int rc = launch_reset(ctx->dev, s);
+  if (rc) return rc;
+  return cuda_err(cudaStreamSynchronize(s));
+}
+
+int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
+  if (!ctx || !o) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned long long st[ST_COUNT];
+  unsigned long long tr[2];
+  CK(cudaMemcpy(st, ctx->dev.ctrl->stat, sizeof(st), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&tr[0], &ctx->dev.ctrl->trace_rpc_n.v, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&tr[1], &ctx->dev.ctrl->trace_evict_n.v, 8, cudaMemcpyDeviceToHost));
+  memset(o, 0, sizeof(*o));
+  o->greads = st[ST_GREADS];
+  o->hits = st[ST_HITS];
+  o->misses = st[ST_MISSES];
+  o->coalesced_waits = st[ST_COALESCED];
+  o->rpcs = st[ST_RPCS];
+  o->pages_fetched = st[ST_PAGES];
+  o->bytes_fetched = st[ST_BYTES];
+  o->ra_pages_sync = st[ST_RA_SYNC];
+  o->ra_pages_async = st[ST_RA_ASYNC];
+  o->evictions = st[ST_EVICT];
+  o->unconsumed_evictions = st[ST_EVICT_UNCONSUMED];
+  o->retries = st[ST_RETRIES];
+  o->timeouts = st[ST_TIMEOUTS];
+  o->eio = st[ST_EIO];
+  o->enomem = st[ST_ENOMEM];
+  o->host_requests = ctx->io->stats.requests.load();
+  o->host_preads = ctx->io->stats.preads.load();
+  o->host_bytes = ctx->io->stats.bytes.load();
+  o->host_copies = ctx->io->stats.copies.load();
+  o->host_errors = ctx->io->stats.errors.load();
+  o->trace_rpc_count = tr[0];
+  o->trace_evict_count = tr[1];
+  return 0;
+}
+
+int gfs_get_trace(gfs_ctx* ctx, gfs_rpc_rec* h_rpc, gfs_evict_rec* h_evict, uint32_t cap, uint64_t* n_rpc,
+                  uint64_t* n_evict, void* stream) {
+  if (!ctx) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned long long nr = 0, ne = 0;
+  CK(cudaMemcpy(&nr, &ctx->dev.ctrl->trace_rpc_n.v, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&ne, &ctx->dev.ctrl->trace_evict_n.v, 8, cudaMemcpyDeviceToHost));
+  const uint64_t kr = std::min<uint64_t>({nr, (uint64_t)cap, (uint64_t)ctx->dev.trace_cap});
+  const uint64_t ke = std::min<uint64_t>({ne, (uint64_t)cap, (uint64_t)ctx->dev.trace_cap});
+  if (h_rpc && kr) CK(cudaMemcpy(h_rpc, ctx->dev.trace_rpc, kr * sizeof(gfs_rpc_rec), cudaMemcpyDeviceToHost));
+  if (h_evict && ke) CK(cudaMemcpy(h_evict, ctx->dev.trace_evict, ke * sizeof(gfs_evict_rec), cudaMemcpyDeviceToHost));
+  if (n_rpc) *n_rpc = nr;
+  if (n_evict) *n_evict = ne;
+  return 0;
+}
+
+int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* stream) {
+  if (!ctx || !h_counts) return -EINVAL;
+  if (!ctx->dev.fetch_count) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  const uint64_t n = std::min<uint64_t>(cap, ctx->dev.debug_pages);
+  CK(cudaMemcpy(h_counts, ctx->dev.fetch_count, n * 4, cudaMemcpyDeviceToHost));
+  return 0;
+}
+
+static int scan_prepare(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint64_t* nstrides, uint64_t* buf_stride,
+                        DevHandle* g) {
+  if (!ctx || !a) return -EINVAL;
+  if (fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
+  if (a->stride == 0 || a->read_len == 0 || a->blocks == 0) return -EINVAL;
+  if (a->threads != 128 && a->threads != 256 && a->threads != 512) return -EINVAL;
+  const uint64_t size = ctx->files[fid].size;
+  *nstrides = size ? (size + a->stride - 1) / a->stride : 0;
+  *buf_stride = align_up(a->read_len, 256);
+  CK(cudaSetDevice(ctx->cfg.device));
+  const size_t need = (size_t)a->blocks * *buf_stride;
+  if (need > ctx->scan_buf_bytes) {
+    if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
+    ctx->d_scan_buf = nullptr;
+    ctx->scan_buf_bytes = 0;
+    CK(cudaMalloc((void**)&ctx->d_scan_buf, need));
+    ctx->scan_buf_bytes = need;
+  }
+  *g = ctx->dev;
+  const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  g->reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
+                                       : (uint32_t)std::min<uint64_t>(0xffffffffull, a->blocks * pages_per_read + 1);
+  if (a->serialize) {
+    int maxb = 0;
+    int rc = scan_max_resident_blocks(a->threads, a->fused != 0, ctx->cfg.device, &maxb);
+    if (rc) return rc;
+    if ((int)a->blocks > maxb) return -EINVAL;  // every block must be resident to take its turn
+  }
+  return 0;
+}
+
+int gfs_scan(gfs_ctx* ctx, int fid, const gfs_scan_args* a, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash,
+             void* stream) {
+  uint64_t ns = 0, bs = 0;
+  DevHandle g;
+  int rc = scan_prepare(ctx, fid, a, &ns, &bs, &g);
+  if (rc) return rc;
+  if (ns == 0) return 0;
+  if (!d_count || !d_sum || !d_hash) return -EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a->serialize) CK(cudaMemsetAsync(&g.ctrl->ticket.v, 0, 8, s));
+  return launch_scan(g, fid, *a, ns, ctx->d_scan_buf, bs, d_count, d_sum, d_hash, s);
+}
+
+int gfs_scan_host(gfs_ctx* ctx, int fid, const gfs_scan_args* a, int64_t* h_count, uint64_t* h_sum, uint64_t* h_hash,
+                  void* stream) {
+  uint64_t ns = 0, bs = 0;
+  DevHandle g;
+  int rc = scan_prepare(ctx, fid, a, &ns, &bs, &g);
+  if (rc) return rc;
+  if (ns == 0) return 0;
+  if (!h_count || !h_sum || !h_hash) return -EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Result buffers are allocated before the launch and the copy back goes to
+  // pinned memory: a pageable device-to-host copy issued while the kernel runs
+  // blocks in the driver, and so would the I/O threads' submissions the kernel
+  // is waiting for.
+  const size_t need = (size_t)ns * 24;
+  if (need > ctx->out_bytes) {
+    if (ctx->d_out) cudaFree(ctx->d_out);
+    if (ctx->h_out) cudaFreeHost(ctx->h_out);
+    ctx->d_out = ctx->h_out = nullptr;
+    ctx->out_bytes = 0;
+    CK(cudaMalloc((void**)&ctx->d_out, need));
+    CK(cudaHostAlloc((void**)&ctx->h_out, need, cudaHostAllocDefault));
+    ctx->out_bytes = need;
+  }
+  int64_t* dc = (int64_t*)ctx->d_out;
+  uint64_t* dsum = (uint64_t*)(ctx->d_out + ns * 8);
+  uint64_t* dh = (uint64_t*)(ctx->d_out + ns * 16);
+  if (a->serialize) CK(cudaMemsetAsync(&g.ctrl->ticket.v, 0, 8, s));
+  rc = launch_scan(g, fid, *a, ns, ctx->d_scan_buf, bs, dc, dsum, dh, s);
+  if (!rc) rc = cuda_err(cudaMemcpyAsync(ctx->h_out, ctx->d_out, need, cudaMemcpyDeviceToHost, s));
+  int rc2 = cuda_err(cudaStreamSynchronize(s));
+  if (!rc && !rc2) {
+    memcpy(h_count, ctx->h_out, ns * 8);
+    memcpy(h_sum, ctx->h_out + ns * 8, ns * 8);
+    memcpy(h_hash, ctx->h_out + ns * 16, ns * 8);
+  }
+  return rc ? rc : rc2;
+}
+
+int gfs_read_many(gfs_ctx* ctx, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len, const uint64_t* d_dst,
+                  uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads, void* stream) {
+  if (!ctx) return -EINVAL;
+  if (fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
+  if (n == 0) return 0;
+  if (!d_off || !d_len || !d_dst || !d_buf || !d_ret || blocks == 0) return -EINVAL;
+  if (threads != 128 && threads != 256 && threads != 512) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  DevHandle g = ctx->dev;
+  g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames : blocks + 1;
+  return launch_read_many(g, fid, n, d_off, d_len, d_dst, d_buf, d_ret, blocks, threads, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- CPU-I/O baseline
+int gfs_cpuio_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t threads, uint64_t chunk,
+                   uint8_t* d_file, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, void* stream,
+                   double* seconds) {
+  if (!path || !d_file || !d_count || !d_sum || !d_hash || stride == 0 || read_len == 0 || threads == 0 ||
+      chunk == 0 || threads > 256)
+    return -EINVAL;
+  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return -errno;
+  struct stat st;
+  if (fstat(fd, &st) != 0) {
+    int e = errno;
+    close(fd);
+    return -e;
+  }
+  const uint64_t size = (uint64_t)st.st_size;
+  chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(size, 1));
+  struct Worker {
+    cudaStream_t s = nullptr;
+    uint8_t* buf[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int err = 0;
+  };
+  std::vector<Worker> w(threads);
+  int rc = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (auto& x : w) {
+    if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking));
+    for (int k = 0; k < 2 && !rc; ++k) {
+      rc = cuda_err(cudaHostAlloc((void**)&x.buf[k], chunk, cudaHostAllocDefault));
+      if (!rc) rc = cuda_err(cudaEventCreateWithFlags(&x.ev[k], cudaEventDisableTiming));
+    }
+  }
+  double t0 = now_s(), t1 = t0;
+  if (!rc) {
+    std::atomic<uint64_t> next{0};
+    std::vector<std::thread> th;
+    for (uint32_t t = 0; t < threads; ++t)
+      th.emplace_back([&, t] {
+        cudaSetDevice(dev);
+        Worker& x = w[t];
+        bool pend[2] = {false, false};
+        int k = 0;
+        for (;;) {
+          const uint64_t o = next.fetch_add(chunk);
+          if (o >= size) break;
+          const size_t nb = (size_t)std::min<uint64_t>(chunk, size - o);
+          if (pend[k]) cudaEventSynchronize(x.ev[k]);
+          size_t got = 0;
+          while (got < nb) {
+            ssize_t r = pread(fd, x.buf[k] + got, nb - got, (off_t)(o + got));
+            if (r < 0 && errno == EINTR) continue;
+            if (r <= 0) {
+              x.err = -EIO;
+              break;
+            }
+            got += (size_t)r;
+          }
+          if (x.err) break;
+          if (cudaMemcpyAsync(d_file + o, x.buf[k], nb, cudaMemcpyHostToDevice, x.s) != cudaSuccess) {
+            x.err = -EIO;
+            break;
+          }
+          cudaEventRecord(x.ev[k], x.s);
+          pend[k] = true;
+          k ^= 1;
+        }
+        cudaStreamSynchronize(x.s);
+      });
+    for (auto& t : th) t.join();
+    for (auto& x : w)
+      if (x.err) rc = x.err;
+    if (!rc) rc = launch_checksum(d_file, size, stride, read_len, d_count, d_sum, d_hash, (cudaStream_t)stream);
+    if (!rc) rc = cuda_err(cudaStreamSynchronize((cudaStream_t)stream));
+    t1 = now_s();
+  }
+  for (auto& x : w) {
+    for (int k = 0; k < 2; ++k) {
+      if (x.buf[k]) cudaFreeHost(x.buf[k]);
+      if (x.ev[k]) cudaEventDestroy(x.ev[k]);
+    }
+    if (x.s) cudaStreamDestroy(x.s);
+  }
+  close(fd);
+  if (seconds) *seconds = t1 - t0;
+  return rc;
+}
+
+// ---------------------------------------------------------------- link probes
+int gfs_probe_h2d(uint64_t bytes, uint64_t chunk, int reps, double* gbps) {
+  if (!gbps || bytes == 0 || chunk == 0 || reps < 1) return -EINVAL;
+  uint8_t* h = nullptr;
+  uint8_t* d = nullptr;
+  cudaStream_t s = nullptr;
+  int rc = cuda_err(cudaHostAlloc((void**)&h, bytes, cudaHostAllocDefault));
+  if (!rc) rc = cuda_err(cudaMalloc((void**)&d, bytes));
+  if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  double best = 0;
+  if (!rc) {
+    memset(h, 1, bytes);
+    for (int r = 0; r <= reps && !rc; ++r) {
+      const double t0 = now_s();
+      for (uint64_t o = 0; o < bytes; o += chunk)
+        cudaMemcpyAsync(d + o, h + o, std::min<uint64_t>(chunk, bytes - o), cudaMemcpyHostToDevice, s);
+      rc = cuda_err(cudaStreamSynchronize(s));
+      const double bw = bytes / (now_s() - t0) / 1e9;
+      if (r > 0 && bw > best) best = bw;  // r == 0 is a warm-up
+    }
+  }
+  if (s) cudaStreamDestroy(s);
+  if (d) cudaFree(d);
+  if (h) cudaFreeHost(h);
+  *gbps = best;
+  return rc;
+}
+
+int gfs_probe_pread(const char* path, uint32_t threads, uint64_t chunk, int reps, double* gbps) {
+  if (!path || !gbps || threads == 0 || threads > 256 || chunk == 0 || reps < 1) return -EINVAL;
+  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return -errno;
+  struct stat st;
+  fstat(fd, &st);
+  const uint64_t size = (uint64_t)st.st_size;
+  std::vector<uint8_t*> bufs(threads, nullptr);
+  int rc = 0;
+  for (auto& b : bufs)
+    if (!rc) rc = cuda_err(cudaHostAlloc((void**)&b, chunk, cudaHostAllocDefault));
+  double best = 0;
+  for (int r = 0; r < reps && !rc; ++r) {
+    std::atomic<uint64_t> next{0};
+    const double t0 = now_s();
+    std::vector<std::thread> th;
+    for (uint32_t t = 0; t < threads; ++t)
+      th.emplace_back([&, t] {
+        for (;;) {
+          const uint64_t o = next.fetch_add(chunk);
+          if (o >= size) break;
+          if (pread(fd, bufs[t], (size_t)std::min<uint64_t>(chunk, size - o), (off_t)o) < 0) break;
+        }
+      });
+    for (auto& x : th) x.join();
+    const double bw = size / (now_s() - t0) / 1e9;
+    if (bw > best) best = bw;
+  }
+  for (auto& b : bufs)
+    if (b) cudaFreeHost(b);
+  close(fd);
+  *gbps = best;
+  return rc;
+}
+
+// ---------------------------------------------------------------- CPU self-test
+int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests, uint32_t max_pages,
+                      uint32_t threads, uint32_t slots, uint64_t seed, uint64_t* h_served) {
+  if (!path || !is_pow2(page_size) || page_size < 16 || frames == 0 || max_pages == 0 ||
+      max_pages > MAX_RPC_PAGES || threads == 0 || threads > 64 || slots == 0 || seed == 0)
+    return -EINVAL;
+  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return -errno;
+  struct stat st;
+  fstat(fd, &st);
+  const uint64_t size = (uint64_t)st.st_size;
+  const uint64_t npages = (size + page_size - 1) / page_size;
+  const uint32_t shift = log2u(page_size);
+  const uint32_t stride = slot_stride(max_pages);
+  std::vector<uint8_t> ring((size_t)slots * stride + 64);
+  uint8_t* rb = (uint8_t*)(((uintptr_t)ring.data() + 63) & ~(uintptr_t)63);
+  for (uint32_t i = 0; i < slots; ++i) ((RingSlot*)(rb + (size_t)i * stride))->seq = i;
+  std::vector<uint8_t> fr((size_t)frames << shift);
+  std::vector<uint32_t> state(frames, FR_EMPTY);
+  ServiceConfig sc;
+  sc.ring = rb;
+  sc.slots = slots;
+  sc.slot_stride = stride;
+  sc.page_size = page_size;
+  sc.page_shift = shift;
+  sc.staging_pages = std::max<uint32_t>(1, (uint32_t)std::min<uint64_t>(4, max_pages));
+  sc.threads = threads;
+  sc.n_frames = frames;
+  const size_t stg = (size_t)sc.staging_pages * page_size;
+  IoService io(
+      sc, [&](int) -> Sink* { return new HostSink(fr.data(), state.data(), shift, stg); },
+      [&](uint32_t fid, FileView* fv) {
+        if (fid != 0) return false;
+        fv->fd = fd;
+        fv->size = size;
+        return true;
+      });
+  int rc = io.start();
+  if (rc) {
+    close(fd);
+    return rc;
+  }
+  // Emulated device client: batches of requests over disjoint frame runs.
+  uint64_t x = seed, ticket = 0, bad = 0;
+  std::vector<uint8_t> want((size_t)max_pages << shift);
+  auto rnd = [&]() {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    return x;
+  };
+  struct Pending {
+    uint64_t page_lo;
+    uint32_t n, frame0;
+  };
+  uint32_t done = 0;
+  const uint32_t batch_max = std::max<uint32_t>(1, std::min<uint32_t>(slots, frames / max_pages));
+  while (done < requests && !bad && npages) {
+    std::vector<Pending> batch;
+    uint32_t next_frame = 0;
+    while (batch.size() < batch_max && done + batch.size() < requests) {
+      Pending p;
+      p.page_lo = rnd() % (npages + 1);  // one past the end exercises EOF
+      p.n = 1 + (uint32_t)(rnd() % max_pages);
+      p.frame0 = next_frame;
+      if (next_frame + p.n > frames) break;
+      next_frame += p.n;
+      for (uint32_t i = 0; i < p.n; ++i) __atomic_store_n(&state[p.frame0 + i], (uint32_t)FR_FILLING, __ATOMIC_RELAXED);
+      RingSlot* s = (RingSlot*)(rb + (size_t)(ticket % slots) * stride);
+      const double t0 = now_s();
+      while (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != ticket)
+        if (now_s() - t0 > 10) {
+          bad = 1;
+          break;
+        }
+      if (bad) break;
+      s->fid = 0;
+      s->npages = p.n;
+      s->page_lo = p.page_lo;
+      s->kind = GFS_KIND_DEMAND;
+      s->op = 1;
+      for (uint32_t i = 0; i < p.n; ++i) s->frames[i] = p.frame0 + i;
+      __atomic_store_n(&s->seq, ticket + 1, __ATOMIC_RELEASE);
+      ++ticket;
+      batch.push_back(p);
+    }
+    for (const Pending& p : batch) {
+      for (uint32_t i = 0; i < p.n && !bad; ++i) {
+        const double t0 = now_s();
+        uint32_t sv;
+        while ((sv = __atomic_load_n(&state[p.frame0 + i], __ATOMIC_ACQUIRE)) == FR_FILLING)
+          if (now_s() - t0 > 10) {
+            bad = 2;
+            break;
+          }
+        if (bad) break;
+        const uint64_t page = p.page_lo + i;
+        const uint64_t base = page << shift;
+        const bool expect_ok = page < npages;
+        if ((sv == FR_READY) != expect_ok) {
+          bad = 3;
+          break;
+        }
+        if (expect_ok) {
+          const size_t nb = (size_t)std::min<uint64_t>(page_size, size - base);
+          if (pread(fd, want.data(), nb, (off_t)base) != (ssize_t)nb) {
+            bad = 4;
+            break;
+          }
+          if (memcmp(want.data(), fr.data() + ((size_t)(p.frame0 + i) << shift), nb) != 0) bad = 5;
+        }
+      }
+    }
+    done += (uint32_t)batch.size();
+    if (batch.empty()) break;
+  }
+  io.stop();
+  close(fd);
+  if (h_served) *h_served = io.stats.requests.load();
+  return bad ? -(int)(1000 + bad) : 0;
+}
+
+}  // extern "C"

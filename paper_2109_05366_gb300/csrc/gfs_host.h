@@ -1,0 +1,61 @@
+// Host-side context of the GPU file-read path (shared by gfs_host.cpp and gfs_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gfs_internal.h"
+
+struct gfs_faults_cfg {
+  uint32_t eio_every = 0;    // every Nth pread fails with EIO (0 = never)
+  uint32_t short_every = 0;  // every Nth pread returns half of what was asked
+  uint32_t delay_us = 0;     // sleep before every pread
+};
+
+namespace gfs {
+
+struct HostFile {
+  int fd = -1;
+  uint64_t size = 0;
+  int flags = 0;
+  int advice = GFS_ADV_NORMAL;
+  bool open = false;
+  std::string path;
+};
+
+class IoService;
+
+// Entry points of the device code, implemented in gfs_kernels.cu.
+int launch_reset(const DevHandle& g, cudaStream_t s);
+int launch_scan(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
+                uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
+int launch_read_many(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                     const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
+                     cudaStream_t s);
+int launch_checksum(const uint8_t* d_file, uint64_t size, uint64_t stride, uint64_t read_len, int64_t* d_count,
+                    uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
+int scan_max_resident_blocks(uint32_t threads, bool fused, int device, int* out);
+
+}  // namespace gfs
+
+struct gfs_ctx {
+  gfs_config cfg{};
+  gfs::DevHandle dev{};
+  void* d_arena = nullptr;
+  uint8_t* d_frames = nullptr;
+  size_t arena_bytes = 0;
+  uint8_t* h_ring = nullptr;  // mapped pinned
+  std::vector<gfs::HostFile> files;
+  gfs::IoService* io = nullptr;
+  uint8_t* d_scan_buf = nullptr;  // per-block gread buffers of gfs_scan
+  size_t scan_buf_bytes = 0;
+  uint8_t* d_out = nullptr;        // gfs_scan_host results: device side
+  uint8_t* h_out = nullptr;        // and a pinned host copy
+  size_t out_bytes = 0;
+  std::mutex mu;
+};

@@ -1,0 +1,126 @@
+// Layouts shared by the host runtime and the device code of the GPU file-read path.
+//
+// Everything the GPU touches lives in two places:
+//   * one device arena (cudaMalloc): cache frames, per-frame metadata, the page
+//     table, the consumed FIFO, control counters, traces;
+//   * the request ring in mapped pinned host memory, written by the GPU and
+//     served by the host I/O threads (Section 2.2 "shared CPU-GPU request queue").
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/gfs.h"
+
+#if defined(__CUDACC__)
+#define GFS_HD __host__ __device__
+#else
+#define GFS_HD
+#endif
+
+namespace gfs {
+
+// Frame states.  RECLAIM = claimed by an evictor, not yet reinstalled.
+enum : uint32_t { FR_EMPTY = 0, FR_FILLING = 1, FR_READY = 2, FR_ERROR = 3, FR_RECLAIM = 4 };
+
+constexpr uint64_t KEY_NONE = ~0ull;
+constexpr uint64_t ENTRY_EMPTY = ~0ull;
+constexpr uint32_t FRAME_BITS = 24;               // frame index bits in a table entry
+constexpr uint32_t MAX_FRAMES = (1u << FRAME_BITS) - 1;
+constexpr uint32_t MAX_FILES = 255;               // fid 255 reserved (all-ones entry)
+constexpr uint32_t BUCKET = 32;                   // slots per bucket = one warp
+constexpr uint32_t MAX_RPC_PAGES = 256;
+
+// Page key: (fid, page), 8 + 32 bits.
+GFS_HD inline uint64_t make_key(uint32_t fid, uint64_t page) { return ((uint64_t)fid << 32) | (page & 0xffffffffull); }
+GFS_HD inline uint32_t key_fid(uint64_t key) { return (uint32_t)(key >> 32); }
+GFS_HD inline uint64_t key_page(uint64_t key) { return key & 0xffffffffull; }
+
+// Statistic slots in the device counter block (order = gfs_stats fields).
+enum : int {
+  ST_GREADS = 0, ST_HITS, ST_MISSES, ST_COALESCED, ST_RPCS, ST_PAGES, ST_BYTES, ST_RA_SYNC, ST_RA_ASYNC,
+  ST_EVICT, ST_EVICT_UNCONSUMED, ST_RETRIES, ST_TIMEOUTS, ST_EIO, ST_ENOMEM, ST_COUNT
+};
+
+// Control counters in device memory (one 128-byte line per hot counter).
+struct alignas(128) Line { unsigned long long v; unsigned long long pad[15]; };
+struct Ctrl {
+  Line next_unused;    // never-used frames handed out (victim class 1)
+  Line alloc_counter;  // allocation sequence
+  Line fifo_head;      // consumed FIFO pop position
+  Line fifo_tail;      // consumed FIFO push position
+  Line ring_tail;      // request ring: next ticket the GPU takes
+  Line ticket;         // serialized mode: next stride allowed to gread
+  Line trace_rpc_n;
+  Line trace_evict_n;
+  unsigned long long stat[ST_COUNT];
+};
+
+// Per-file device state.
+struct FileDev {
+  unsigned long long size;
+  unsigned long long npages;
+  uint32_t open;     // 1 if the fid is open
+  uint32_t ra;       // readahead enabled (read-only, not ADV_RANDOM)
+  uint32_t pad[2];
+};
+
+// One request-ring slot in mapped pinned memory (64-byte header + frame list).
+// Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; the GPU
+// producer with ticket t waits for seq == t, fills the slot and publishes
+// seq = t + 1; the host consumer with ticket h waits for seq == h + 1, copies the
+// request out and frees the slot with seq = h + R.
+struct RingSlot {
+  unsigned long long seq;
+  uint32_t fid;
+  uint32_t npages;
+  unsigned long long page_lo;
+  uint32_t kind;
+  uint32_t op;
+  unsigned long long issue_ns;
+  uint32_t pad[6];
+  uint32_t frames[1];  // npages entries follow (slot stride covers max_rpc_pages)
+};
+static_assert(sizeof(unsigned long long) == 8, "u64");
+
+GFS_HD inline uint32_t slot_stride(uint32_t max_pages) {
+  uint32_t b = 64 + 4 * max_pages;
+  return (b + 63) & ~63u;
+}
+
+// Handle passed by value to every kernel.  Plain data only.
+struct DevHandle {
+  // configuration
+  unsigned long long timeout_ns;
+  unsigned long long cache_bytes;
+  uint32_t page_size, page_shift, n_frames, mode;
+  uint32_t ra_cap, async_ra, max_rpc_pages, reserve;
+  uint32_t nbuckets, max_streams, max_files, trace_cap;
+  uint32_t rpc_slots, slot_stride, fifo_cap, debug_pages;
+  // cache frames and per-frame metadata (structure of arrays)
+  uint8_t* frames;
+  unsigned long long* fkey;
+  uint32_t* fstate;
+  uint32_t* fpins;
+  uint32_t* fconsumed;
+  uint32_t* fvalid;
+  uint32_t* fwindow;
+  uint32_t* fmark;            // readahead mark: end page + 1, 0 = none
+  unsigned long long* faseq;  // allocation sequence
+  // page table: nbuckets * 32 entries of (key << 24 | frame); per-bucket lock and overflow flag
+  unsigned long long* tab;
+  uint32_t* tlock;
+  uint32_t* tovf;
+  // consumed FIFO cells: (position << 24 | frame)
+  unsigned long long* fifo;
+  Ctrl* ctrl;
+  FileDev* files;
+  unsigned long long* last_end;  // per stream: (fid << 32 | end page), ~0 = none
+  // request ring (device view of mapped pinned memory)
+  uint8_t* ring;
+  // traces
+  gfs_rpc_rec* trace_rpc;
+  gfs_evict_rec* trace_evict;
+  uint32_t* fetch_count;  // per page of fid 0
+};
+
+}  // namespace gfs

@@ -1,0 +1,220 @@
+// Kernels of the GPU file-read path: the stride scan (Section 6.1 microbenchmark
+// shape: block b greads strides b, b+B, ... and checksums each), independent
+// greads, cache reset, and the checksum kernel of the CPU-I/O baseline.
+#include <cuda_runtime.h>
+
+#include "gfs_device.cuh"
+#include "gfs_host.h"
+
+namespace gfs {
+
+using dev::Sums;
+
+// Block-wide sum of two u64 values; result valid in thread 0.
+__device__ __forceinline__ void block_reduce2(unsigned long long& a, unsigned long long& b) {
+  __shared__ unsigned long long ra[32], rb[32];
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(dev::kFull, a, o);
+    b += __shfl_xor_sync(dev::kFull, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) {
+    ra[w] = a;
+    rb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < nw ? ra[l] : 0ull;
+    b = l < nw ? rb[l] : 0ull;
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(dev::kFull, a, o);
+      b += __shfl_xor_sync(dev::kFull, b, o);
+    }
+  }
+}
+
+// Checksums of n bytes at p (file offset `off` of p[0]); p is 16-byte aligned.
+__device__ __forceinline__ void checksum_range(const uint8_t* __restrict__ p, unsigned long long n,
+                                               unsigned long long off, Sums& acc) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  const unsigned long long n16 = n >> 4;
+  const uint4* p4 = reinterpret_cast<const uint4*>(p);
+  unsigned long long i = tid;
+  for (; i + 3 * nt < n16; i += 4 * nt) {
+    uint4 a = p4[i], b = p4[i + nt], c = p4[i + 2 * nt], d = p4[i + 3 * nt];
+    dev::sums_add16(acc, a, off + 16 * i);
+    dev::sums_add16(acc, b, off + 16 * (i + nt));
+    dev::sums_add16(acc, c, off + 16 * (i + 2 * nt));
+    dev::sums_add16(acc, d, off + 16 * (i + 3 * nt));
+  }
+  for (; i < n16; i += nt) dev::sums_add16(acc, p4[i], off + 16 * i);
+  for (unsigned long long j = 16 * n16 + tid; j < n; j += nt) dev::sums_add1(acc, p[j], off + j);
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(512) k_scan(DevHandle g, int fid, unsigned long long stride,
+                                               unsigned long long read_len, unsigned long long nstrides, int serialize,
+                                               uint8_t* bufs, unsigned long long buf_stride, long long* cnt,
+                                               unsigned long long* sum, unsigned long long* hash) {
+  const uint32_t b = blockIdx.x, tid = threadIdx.x;
+  uint8_t* buf = bufs + (size_t)b * buf_stride;
+  for (unsigned long long s = b; s < nstrides; s += gridDim.x) {
+    const unsigned long long off = s * stride;
+    if (serialize) {  // one gread at a time, in stride order
+      if (tid == 0) {
+        const unsigned long long dl = dev::now_ns() + g.timeout_ns;
+        while (dev::ld_acq64(&g.ctrl->ticket.v) != s) {
+          if (dev::now_ns() > dl) {
+            dev::stat_add(g, ST_TIMEOUTS, 1);
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __syncthreads();
+    }
+    Sums acc{0ull, 0ull};
+    long long r = dev::gread_impl<FUSED>(g, (int)b, fid, off, read_len, buf, acc);
+    if (serialize) {  // wait until every request of this gread has been served
+      const unsigned long long dl = dev::now_ns() + g.timeout_ns;
+      for (uint32_t f = tid; f < g.n_frames; f += blockDim.x)
+        while (dev::ld_acq(&g.fstate[f]) == FR_FILLING && dev::now_ns() < dl) __nanosleep(256);
+      __syncthreads();
+      if (tid == 0) dev::st_rel64(&g.ctrl->ticket.v, s + 1);
+    }
+    if (!FUSED && r > 0) checksum_range(buf, (unsigned long long)r, off, acc);
+    block_reduce2(acc.sum, acc.hash);
+    if (tid == 0) {
+      cnt[s] = r;
+      sum[s] = r > 0 ? acc.sum : 0ull;
+      hash[s] = r > 0 ? acc.hash : 0ull;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_t n, const uint64_t* off,
+                                                    const uint64_t* len, const uint64_t* dst, uint8_t* buf,
+                                                    long long* ret) {
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    long long r = dev::gread(g, (int)blockIdx.x, fid, off[i], len[i], buf + dst[i]);
+    if (threadIdx.x == 0) ret[i] = r;
+    __syncthreads();
+  }
+}
+
+__global__ void k_reset(DevHandle g) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+  for (size_t f = tid; f < g.n_frames; f += nt) {
+    g.fkey[f] = KEY_NONE;
+    g.fstate[f] = FR_EMPTY;
+    g.fpins[f] = 0;
+    g.fconsumed[f] = 0;
+    g.fvalid[f] = 0;
+    g.fwindow[f] = 0;
+    g.fmark[f] = 0;
+    g.faseq[f] = ~0ull;
+  }
+  const size_t nslots = (size_t)g.nbuckets * BUCKET;
+  for (size_t i = tid; i < nslots; i += nt) g.tab[i] = ENTRY_EMPTY;
+  for (size_t i = tid; i < g.nbuckets; i += nt) {
+    g.tlock[i] = 0;
+    g.tovf[i] = 0;
+  }
+  for (size_t i = tid; i < g.fifo_cap; i += nt) g.fifo[i] = ((unsigned long long)i << FRAME_BITS) | MAX_FRAMES;
+  const size_t nle = (size_t)g.max_streams * g.max_files;
+  for (size_t i = tid; i < nle; i += nt) g.last_end[i] = 0;
+  if (g.fetch_count)
+    for (size_t i = tid; i < g.debug_pages; i += nt) g.fetch_count[i] = 0;
+  if (tid == 0) {
+    g.ctrl->next_unused.v = 0;
+    g.ctrl->alloc_counter.v = 0;
+    g.ctrl->fifo_head.v = 0;
+    g.ctrl->fifo_tail.v = 0;
+    g.ctrl->ticket.v = 0;
+    g.ctrl->trace_rpc_n.v = 0;
+    g.ctrl->trace_evict_n.v = 0;
+    for (int i = 0; i < ST_COUNT; ++i) g.ctrl->stat[i] = 0;
+    // ring_tail is left alone: the ring keeps its position across resets
+  }
+}
+
+// CPU-I/O baseline consumer: per-stride checksums of a file already in device memory.
+__global__ void __launch_bounds__(512) k_checksum(const uint8_t* file, unsigned long long size,
+                                                  unsigned long long stride, unsigned long long read_len,
+                                                  unsigned long long nstrides, long long* cnt,
+                                                  unsigned long long* sum, unsigned long long* hash) {
+  for (unsigned long long s = blockIdx.x; s < nstrides; s += gridDim.x) {
+    const unsigned long long off = s * stride;
+    const unsigned long long n = off >= size ? 0 : (read_len < size - off ? read_len : size - off);
+    Sums acc{0ull, 0ull};
+    if ((off & 15) == 0) {
+      checksum_range(file + off, n, off, acc);
+    } else {
+      for (unsigned long long j = threadIdx.x; j < n; j += blockDim.x) dev::sums_add1(acc, file[off + j], off + j);
+    }
+    block_reduce2(acc.sum, acc.hash);
+    if (threadIdx.x == 0) {
+      cnt[s] = (long long)n;
+      sum[s] = acc.sum;
+      hash[s] = acc.hash;
+    }
+    __syncthreads();
+  }
+}
+
+static int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return 0;
+  if (e == cudaErrorMemoryAllocation) return -12;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return -19;
+  return -22;
+}
+
+int launch_reset(const DevHandle& g, cudaStream_t s) {
+  k_reset<<<304, 512, 0, s>>>(g);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_scan(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
+                uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s) {
+  if (a.fused)
+    k_scan<true><<<a.blocks, a.threads, 0, s>>>(g, fid, a.stride, a.read_len, nstrides, (int)a.serialize, bufs,
+                                                buf_stride, (long long*)d_count, (unsigned long long*)d_sum,
+                                                (unsigned long long*)d_hash);
+  else
+    k_scan<false><<<a.blocks, a.threads, 0, s>>>(g, fid, a.stride, a.read_len, nstrides, (int)a.serialize, bufs,
+                                                 buf_stride, (long long*)d_count, (unsigned long long*)d_sum,
+                                                 (unsigned long long*)d_hash);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_read_many(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                     const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
+                     cudaStream_t s) {
+  k_read_many<<<blocks, threads, 0, s>>>(g, fid, n, d_off, d_len, d_dst, d_buf, (long long*)d_ret);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_checksum(const uint8_t* d_file, uint64_t size, uint64_t stride, uint64_t read_len, int64_t* d_count,
+                    uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s) {
+  unsigned long long ns = size ? (size + stride - 1) / stride : 0;
+  if (ns == 0) return 0;
+  unsigned grid = ns < 152ull * 8 ? (unsigned)ns : 152u * 8;
+  k_checksum<<<grid, 512, 0, s>>>(d_file, size, stride, read_len, ns, (long long*)d_count,
+                                   (unsigned long long*)d_sum, (unsigned long long*)d_hash);
+  return cuda_err(cudaGetLastError());
+}
+
+int scan_max_resident_blocks(uint32_t threads, bool fused, int device, int* out) {
+  int per_sm = 0, sms = 0;
+  cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<true>, (int)threads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<false>, (int)threads, 0);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return cuda_err(e);
+  *out = per_sm * sms;
+  return 0;
+}
+
+}  // namespace gfs

@@ -1,0 +1,173 @@
+// Host I/O service of the GPU file-read path.  Plain C++ (no CUDA calls here:
+// the sink decides how served bytes reach the frames).
+#include "gfs_service.h"
+
+#include <errno.h>
+#include <sys/prctl.h>
+#include <time.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <cstring>
+
+namespace gfs {
+
+IoService::IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files)
+    : cfg_(cfg), make_sink_(std::move(make_sink)), files_(std::move(files)) {}
+
+IoService::~IoService() { stop(); }
+
+int IoService::start() {
+  stop_.store(false);
+  for (uint32_t i = 0; i < cfg_.threads; ++i) {
+    Sink* s = make_sink_((int)i);
+    if (!s) {
+      stop();
+      return -ENOMEM;
+    }
+    sinks_.push_back(s);
+  }
+  try {
+    for (uint32_t i = 0; i < cfg_.threads; ++i) threads_.emplace_back(&IoService::run, this, (int)i);
+  } catch (...) {
+    stop();
+    return -EAGAIN;
+  }
+  return 0;
+}
+
+void IoService::stop() {
+  stop_.store(true);
+  for (auto& t : threads_)
+    if (t.joinable()) t.join();
+  threads_.clear();
+  for (Sink* s : sinks_) {
+    s->drain();
+    delete s;
+  }
+  sinks_.clear();
+}
+
+void IoService::drain_sinks() {
+  for (Sink* s : sinks_) s->drain();
+}
+
+void IoService::set_faults(uint32_t eio_every, uint32_t short_every, uint32_t delay_us) {
+  eio_every_.store(eio_every);
+  short_every_.store(short_every);
+  delay_us_.store(delay_us);
+}
+
+ssize_t IoService::do_pread(int fd, uint8_t* buf, size_t n, uint64_t off) {
+  const uint64_t k = pread_count_.fetch_add(1, std::memory_order_relaxed);
+  const uint32_t eio = eio_every_.load(std::memory_order_relaxed);
+  const uint32_t sh = short_every_.load(std::memory_order_relaxed);
+  const uint32_t delay = delay_us_.load(std::memory_order_relaxed);
+  if (delay) usleep(delay);
+  if (eio && k % eio == eio - 1) return -EIO;
+  if (sh && k % sh == sh - 1) n /= 2;
+  size_t got = 0;
+  while (got < n) {
+    ssize_t r = ::pread(fd, buf + got, n - got, (off_t)(off + got));
+    if (r < 0) {
+      if (errno == EINTR) continue;
+      return got ? (ssize_t)got : -errno;
+    }
+    if (r == 0) break;  // EOF
+    got += (size_t)r;
+  }
+  return (ssize_t)got;
+}
+
+void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames) {
+  FileView fv{-1, 0};
+  const bool have = files_(fid, &fv);
+  const uint64_t P = cfg_.page_size;
+  const uint64_t off0 = page_lo << cfg_.page_shift;
+  bool full[MAX_RPC_PAGES];
+  for (uint32_t c0 = 0; c0 < npages; c0 += cfg_.staging_pages) {
+    const uint32_t cn = std::min(cfg_.staging_pages, npages - c0);
+    const uint64_t coff = off0 + (uint64_t)c0 * P;
+    const int k = cur;
+    sink->wait_staging(k);
+    uint8_t* buf = sink->staging(k);
+    size_t want = 0;
+    if (have && coff < fv.size) want = (size_t)std::min<uint64_t>((uint64_t)cn * P, fv.size - coff);
+    ssize_t got = 0;
+    if (want) {
+      got = do_pread(fv.fd, buf, want, coff);
+      stats.preads.fetch_add(1, std::memory_order_relaxed);
+      if (got < 0) {
+        stats.errors.fetch_add(1, std::memory_order_relaxed);
+        got = 0;
+      } else {
+        stats.bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
+      }
+    }
+    // Section 4.1: the returned size decides which pages are delivered.
+    for (uint32_t i = 0; i < cn; ++i) {
+      const uint64_t base = coff + (uint64_t)i * P;
+      const uint64_t expect = (have && base < fv.size) ? std::min<uint64_t>(P, fv.size - base) : 0;
+      full[i] = expect > 0 && (uint64_t)got >= (uint64_t)i * P + expect;
+    }
+    for (uint32_t i = 0; i < cn;) {
+      if (!full[i]) {
+        ++i;
+        continue;
+      }
+      uint32_t j = i + 1;
+      while (j < cn && full[j] && frames[c0 + j] == frames[c0 + j - 1] + 1) ++j;
+      const uint64_t last_base = coff + (uint64_t)(j - 1) * P;
+      const uint64_t bytes = (uint64_t)(j - 1 - i) * P + std::min<uint64_t>(P, fv.size - last_base);
+      if (sink->copy(frames[c0 + i], buf + (size_t)i * P, (size_t)bytes) != 0) {
+        stats.errors.fetch_add(1, std::memory_order_relaxed);
+        for (uint32_t q = i; q < j; ++q) full[q] = false;
+      } else {
+        stats.copies.fetch_add(1, std::memory_order_relaxed);
+      }
+      i = j;
+    }
+    for (uint32_t i = 0; i < cn; ++i) sink->set_state(frames[c0 + i], full[i] ? FR_READY : FR_ERROR);
+    sink->end_chunk(k);
+    cur ^= 1;
+  }
+}
+
+void IoService::run(int idx) {
+  Sink* sink = sinks_[idx];
+  sink->thread_init();
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);  // short sleeps while polling the ring
+  int cur = 0;
+  uint32_t frames[MAX_RPC_PAGES];
+  while (!stop_.load(std::memory_order_relaxed)) {
+    const uint64_t h = head_.fetch_add(1, std::memory_order_relaxed);
+    RingSlot* s = (RingSlot*)(cfg_.ring + (size_t)(h % cfg_.slots) * cfg_.slot_stride);
+    uint64_t spins = 0;
+    while (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) {
+      if (stop_.load(std::memory_order_relaxed)) return;
+      ++spins;
+      if (spins > 20000) {
+        struct timespec ts = {0, spins > 2000000 ? 50000 : 2000};
+        nanosleep(&ts, nullptr);
+      }
+    }
+    const volatile RingSlot* vs = s;
+    const uint32_t fid = vs->fid;
+    const uint32_t npages = vs->npages;
+    const uint64_t page_lo = vs->page_lo;
+    const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
+    for (uint32_t i = 0; i < n; ++i) frames[i] = vs->frames[i];
+    __atomic_store_n(&s->seq, h + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
+    stats.requests.fetch_add(1, std::memory_order_relaxed);
+    bool bad = npages == 0 || npages > MAX_RPC_PAGES;
+    for (uint32_t i = 0; i < n && !bad; ++i) bad = frames[i] >= cfg_.n_frames;
+    if (bad) {
+      stats.errors.fetch_add(1, std::memory_order_relaxed);
+    } else {
+      serve(sink, cur, fid, page_lo, n, frames);
+    }
+    served_.fetch_add(1, std::memory_order_release);
+  }
+}
+
+}  // namespace gfs

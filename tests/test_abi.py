@@ -1,0 +1,100 @@
+"""C-ABI library: builds, loads, exports what include/gfs.h declares; host logic without a GPU."""
+import os
+import re
+
+import pytest
+
+import inputs
+from paper_2109_05366_gb300 import gfs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gfs.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gfs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = gfs.load()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(gfs.SIGNATURES), "binding and header disagree"
+
+
+def test_abi_version_and_errors():
+    lib = gfs.load()
+    assert lib.gfs_abi_version() == 1
+    assert lib.gfs_strerror(-22) == b"invalid argument"
+    assert lib.gfs_strerror(-110) == b"device wait timed out"
+
+
+def test_config_defaults():
+    c = gfs.default_config()
+    assert c.cache_bytes == 1 << 30 and c.page_size == 512 << 10
+    assert c.mode == gfs.MODE_READAHEAD and c.ra_cap_pages == 8 and c.async_ra == 1
+    assert c.rpc_slots == 128 and c.max_rpc_pages == 64 and c.host_threads == 16
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # compile a C program against include/gfs.h and compare sizes/offsets with ctypes
+    import ctypes
+    import subprocess
+    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "reserved"]),
+              ("gfs_stat", gfs.Stat, ["size", "advice"]),
+              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "reserved"]),
+              ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
+              ("gfs_evict_rec", gfs.EvictRec, ["new_fid", "new_page"]),
+              ("gfs_scan_args", gfs.ScanArgs, ["read_len", "fused", "reserved"])]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "%s"' % HEADER, "int main(void){"]
+    for cname, _, fields in checks:
+        src.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for f in fields:
+            src.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f))
+    src.append("return 0;}")
+    c = tmp_path / "l.c"
+    c.write_text("\n".join(src))
+    exe = str(tmp_path / "l")
+    subprocess.check_call(["gcc", "-o", exe, str(c)])
+    got = [int(x) for x in subprocess.check_output([exe]).split()]
+    want = []
+    for _, st, fields in checks:
+        want.append(ctypes.sizeof(st))
+        want.extend(getattr(st, f).offset for f in fields)
+    assert got == want
+
+
+def test_init_rejects_bad_config_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host has a GPU")
+    with pytest.raises(gfs.GfsError) as e:
+        gfs.Context()
+    assert e.value.errno == 19  # ENODEV: no device, no crash
+    with pytest.raises(gfs.GfsError) as e:
+        gfs.Context(page_size=3000)
+    assert e.value.errno == 22
+
+
+@pytest.mark.parametrize("page,frames,requests,max_pages,threads,slots,size", [
+    (4096, 512, 2000, 16, 4, 32, (3 << 20) + 12345),
+    (65536, 64, 400, 8, 8, 4, (5 << 20) + 1),
+    (4096, 64, 500, 1, 2, 1, 4096 * 10),
+    (16384, 256, 300, 64, 16, 128, 7 * 16384 - 5),
+])
+def test_ring_and_service_selftest(tmp_path, page, frames, requests, max_pages, threads, slots, size):
+    path = str(tmp_path / "f.bin")
+    inputs.write_file(path, 3, size)
+    served = gfs.selftest_ring(path, page, frames, requests, max_pages, threads, slots, seed=7)
+    assert served == requests
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # the product path has no fallback: a missing library is an error
+    monkeypatch.setattr(gfs, "_lib", None)
+    monkeypatch.setattr(gfs._build, "LIB", str(tmp_path / "nope.so"))
+    with pytest.raises(gfs.GfsError):
+        gfs.load(build_if_missing=False)

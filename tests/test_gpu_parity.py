@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA read path through the C ABI against the CPU oracle.
+
+Data (counts, per-stride byte sums and position hashes, delivered bytes) must
+be bit-exact.  In serialized mode (one gread at a time in stride order, each
+waiting for its requests) the GPU's RPC and eviction logs must equal the
+oracle's entry for entry; in concurrent mode the policy has several correct
+outcomes and only its invariants are checked.
+"""
+import os
+import random
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import plain, policy
+
+pytestmark = pytest.mark.gpu
+
+KiB, MiB = 1 << 10, 1 << 20
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    torch.cuda.set_device(0)
+    return torch
+
+
+@pytest.fixture(scope="module")
+def gfs():
+    from paper_2109_05366_gb300 import gfs as g
+    g.load()
+    return g
+
+
+def _file(datadir, seed, size):
+    path = os.path.join(datadir, "x%d_%d.bin" % (seed, size))
+    inputs.ensure_file(path, seed, size)
+    return path
+
+
+def _check_scan(gfs, path, stride, cnt, sm, hs, read_len=None):
+    c, s, h = plain.scan_plain(path, stride, read_len)
+    assert cnt.cpu().numpy().tolist() == c
+    assert np.array_equal(gfs.u64_view(sm)[:len(s)], np.array(s, dtype=np.uint64))
+    assert np.array_equal(gfs.u64_view(hs)[:len(h)], np.array(h, dtype=np.uint64))
+
+
+# ------------------------------------------------ config 1: 64 MiB, fits the cache
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fused", [False, True])
+def test_config1_scan_exact(torch_cuda, gfs, datadir, mode, fused):
+    path = _file(datadir, 1, 64 * MiB)
+    with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB, mode=mode, debug_counts=1) as ctx:
+        fid = ctx.open(path)
+        for rep in range(2):
+            out = ctx.scan(fid, 1 * MiB, blocks=64, threads=256, fused=fused)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            counts = ctx.fetch_counts(256)
+            assert st["pages_fetched"] == 256 and (counts == 1).all()  # fits: each page once
+            assert st["evictions"] == 0 and st["timeouts"] == 0 and st["eio"] == 0
+            if mode == 1:
+                assert st["rpcs"] == 256                                  # one page per request
+            ctx.reset_cache()
+
+
+def test_config1_second_pass_hits(torch_cuda, gfs, datadir):
+    path = _file(datadir, 1, 64 * MiB)
+    with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB) as ctx:
+        fid = ctx.open(path)
+        ctx.scan(fid, MiB, blocks=64)
+        out = ctx.scan(fid, MiB, blocks=64)  # everything cached now
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, MiB, *out)
+        st = ctx.stats()
+        assert st["pages_fetched"] == 256 and st["misses"] <= 256
+
+
+# ------------------------------------------------ serialized: exact policy logs
+@pytest.mark.parametrize("size,page,frames,blocks,stride,ra_cap,mode,async_ra", [
+    (64 * MiB, 256 * KiB, 512, 64, MiB, 8, 0, 1),          # config-1 shape
+    (64 * MiB + 12345, 512 * KiB, 16, 8, MiB, 8, 0, 1),    # config-2 shape, file 8x cache, ragged tail
+    (24 * MiB, 256 * KiB, 24, 6, 512 * KiB, 2, 0, 1),
+    (16 * MiB + 7, 64 * KiB, 40, 4, 192 * KiB, 8, 0, 0),   # sync readahead only
+    (8 * MiB, 128 * KiB, 10, 4, 256 * KiB, 8, 1, 1),       # on-demand
+])
+def test_serialized_logs_match_oracle(torch_cuda, gfs, datadir, size, page, frames, blocks, stride, ra_cap, mode,
+                                      async_ra):
+    path = _file(datadir, 2, size)
+    reserve = policy.default_reserve(blocks, stride, page)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=mode, ra_cap_pages=ra_cap, async_ra=async_ra,
+                     trace_capacity=1 << 16, reserve_frames=reserve, max_rpc_pages=64) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode=("ondemand" if mode else "readahead"),
+                               ra_cap=ra_cap, reserve=reserve, async_ra=bool(async_ra), max_rpc_pages=64)
+    assert nr == len(sim.rpc_log) and ne == len(sim.evict_log)
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
+# ------------------------------------------------ concurrent: larger than the cache
+@pytest.mark.parametrize("threads", [256, 512])
+def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads):
+    size, page, cache, blocks = 256 * MiB + 4096 * 3, 512 * KiB, 32 * MiB, 48
+    path = _file(datadir, 3, size)
+    with gfs.Context(cache_bytes=cache, page_size=page, debug_counts=1) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, MiB, blocks=blocks, threads=threads)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, MiB, *out)
+        st = ctx.stats()
+        npages = (size + page - 1) // page
+        counts = ctx.fetch_counts(npages)
+        assert st["timeouts"] == 0 and st["eio"] == 0 and st["enomem"] == 0
+        assert (counts >= 1).all()
+        assert st["evictions"] >= npages - cache // page
+
+
+@pytest.mark.parametrize("stride,read_len,page", [
+    (MiB + 16, MiB + 16, 256 * KiB),     # stride not a page multiple
+    (700 * KiB + 3, 300 * KiB + 5, 64 * KiB),  # odd offsets: unaligned copy path
+    (64 * KiB, 64 * KiB, 2 * MiB),       # 32 blocks share one page
+    (3 * MiB, 2 * MiB + 1, 1 * MiB),
+])
+def test_ragged_strides_exact(torch_cuda, gfs, datadir, stride, read_len, page):
+    size = 40 * MiB + 999
+    path = _file(datadir, 4, size)
+    with gfs.Context(cache_bytes=16 * MiB if page < 2 * MiB else 32 * MiB, page_size=page) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, read_len=read_len, blocks=32, threads=128)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out, read_len=read_len)
+
+
+# ------------------------------------------------ independent greads
+@pytest.mark.parametrize("mode,advice", [(0, 0), (1, 0), (0, 2)])
+def test_random_reads_exact(torch_cuda, gfs, datadir, mode, advice):
+    torch = torch_cuda
+    size = 12 * MiB + 77
+    path = _file(datadir, 5, size)
+    ref = np.fromfile(path, dtype=np.uint8)
+    rng = random.Random(mode * 10 + advice)
+    n = 400
+    offs = [rng.randrange(size + 3 * 65536) for _ in range(n)]
+    lens = [rng.choice([0, 1, 17, 4096, 65536, 200000, 1 << 20]) for _ in range(n)]
+    dsts, pos = [], 0
+    for ln in lens:
+        dsts.append(pos)
+        pos += (ln + 255) // 256 * 256
+    with gfs.Context(cache_bytes=4 * MiB, page_size=64 * KiB, mode=mode) as ctx:
+        fid = ctx.open(path)
+        if advice:
+            ctx.fadvise(fid, advice)
+        d_off = torch.tensor(offs, dtype=torch.int64, device="cuda")
+        d_len = torch.tensor(lens, dtype=torch.int64, device="cuda")
+        d_dst = torch.tensor(dsts, dtype=torch.int64, device="cuda")
+        d_buf = torch.zeros(max(pos, 1), dtype=torch.uint8, device="cuda")
+        d_ret = torch.full((n,), -999, dtype=torch.int64, device="cuda")
+        ctx.read_many(fid, d_off, d_len, d_dst, d_buf, d_ret, blocks=24, threads=256)
+        torch.cuda.synchronize()
+        ret = d_ret.cpu().numpy()
+        buf = d_buf.cpu().numpy()
+    for i in range(n):
+        want = ref[offs[i]:offs[i] + lens[i]] if offs[i] < size else ref[:0]
+        assert ret[i] == len(want)
+        assert np.array_equal(buf[dsts[i]:dsts[i] + len(want)], want)
+
+
+def test_edge_cases(torch_cuda, gfs, datadir):
+    torch = torch_cuda
+    empty = os.path.join(datadir, "empty.bin")
+    open(empty, "wb").close()
+    small = _file(datadir, 6, 100)
+    with gfs.Context(cache_bytes=MiB, page_size=64 * KiB) as ctx:
+        fe = ctx.open(empty)
+        assert ctx.fstat(fe).size == 0
+        cnt, sm, hs = ctx.scan_host(fe, 4096, blocks=4)
+        assert len(cnt) == 0
+        fs = ctx.open(small)
+        cnt, sm, hs = ctx.scan_host(fs, 64, blocks=4, threads=128)
+        c, s, h = plain.scan_plain(small, 64)
+        assert cnt.tolist() == c and sm.tolist() == s and hs.tolist() == h
+        d = torch.zeros(4, dtype=torch.int64, device="cuda")
+        r = torch.zeros(4, dtype=torch.int64, device="cuda")
+        buf = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+        ctx.read_many(fs, torch.tensor([100, 99, 0, 5000], device="cuda"),
+                      torch.tensor([10, 10, 0, 1], device="cuda"), d, buf, r, blocks=2, threads=128)
+        torch.cuda.synchronize()
+        assert r.cpu().tolist() == [0, 1, 0, 0]
+        with pytest.raises(gfs.GfsError):
+            ctx.scan(7, 4096)
+        with pytest.raises(gfs.GfsError):
+            ctx.open(os.path.join(datadir, "does-not-exist"))
+
+
+def test_host_read_errors_surface_as_eio(torch_cuda, gfs, datadir):
+    size = 16 * MiB
+    path = _file(datadir, 7, size)
+    with gfs.Context(cache_bytes=32 * MiB, page_size=256 * KiB, timeout_ns=5 * 10**9) as ctx:
+        fid = ctx.open(path)
+        ctx.set_faults(eio_every=5)
+        cnt, sm, hs = ctx.scan_host(fid, MiB, blocks=8)
+        c, s, h = plain.scan_plain(path, MiB)
+        bad = [i for i in range(len(c)) if cnt[i] < 0]
+        assert bad, "injected host errors must reach some greads"
+        assert all(cnt[i] == -5 for i in bad)
+        for i in range(len(c)):
+            if cnt[i] >= 0:
+                assert cnt[i] == c[i] and sm[i] == s[i] and hs[i] == h[i]
+        st = ctx.stats()
+        assert st["timeouts"] == 0 and st["host_errors"] > 0
+        ctx.set_faults()
+        ctx.reset_cache()
+        cnt, sm, hs = ctx.scan_host(fid, MiB, blocks=8)
+        assert cnt.tolist() == c and sm.tolist() == s and hs.tolist() == h
