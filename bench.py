@@ -224,7 +224,8 @@ def run_gfs(args):
         return ev
 
     cfg = dict(cache_bytes=cache, page_size=page, host_threads=args.host_threads, ra_cap_pages=args.ra_cap,
-               rpc_slots=args.rpc_slots, staging_bytes=args.staging_mib * MiB, max_rpc_pages=64)
+               rpc_slots=args.rpc_slots, staging_bytes=args.staging_mib * MiB, max_rpc_pages=args.max_rpc_pages,
+               xfer=gfs.XFER_PULL if args.xfer == "pull" else gfs.XFER_DMA)
     with gfs.Context(mode=gfs.MODE_READAHEAD, **cfg) as ctx:
         fid = ctx.open(path)
         # correctness of the timed configuration on sampled strides (full check in tests)
@@ -290,6 +291,7 @@ def run_gfs(args):
         "config": {"workload": args.workload, "file_bytes": size, "page_bytes": page, "cache_bytes": cache,
                    "blocks": blocks, "threads": args.threads, "stride_bytes": stride, "ra_cap_pages": args.ra_cap,
                    "host_threads": args.host_threads, "rpc_slots": args.rpc_slots, "fused": bool(args.fused),
+                   "xfer": args.xfer, "max_rpc_pages": args.max_rpc_pages,
                    "l2": "inputs larger than L2 (8 GiB file); no flush", "parallelism": "replicas" if world > 1 else "1gpu"},
         "clocks": clocks,
         "e2e": {"value": round(size / (sum(e2e_t) / len(e2e_t)) / 1e9, 3), "unit": "GB/s",
@@ -335,6 +337,8 @@ def main():
     ap.add_argument("--rpc-slots", type=int, default=128)
     ap.add_argument("--staging-mib", type=int, default=4)
     ap.add_argument("--fused", action="store_true")
+    ap.add_argument("--xfer", choices=["pull", "dma"], default="pull")
+    ap.add_argument("--max-rpc-pages", type=int, default=16)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

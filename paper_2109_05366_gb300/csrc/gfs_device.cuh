@@ -414,27 +414,214 @@ __device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned lo
   fifo_push(g, (uint32_t)f, deadline);
 }
 
+// ---------------------------------------------------------------- pull transfer (GFS_XFER_PULL)
+// The host preads a request into the slot's staging (mapped pinned memory) and
+// publishes a completion record; GPU threads copy each page into its frame over
+// the host link.  A page is claimed by CAS FILLING -> COPYING on its frame state,
+// so exactly one group copies it; the group that copies a request's last page
+// frees the ring slot.
+struct PullJob {
+  int f;                   // frame to fill, -1 = no job
+  uint32_t s, i;           // slot and page index within the request
+  unsigned long long t;    // ticket of the request
+  long long res;           // host pread result
+};
+
+__device__ __forceinline__ RingSlot* ring_slot(const DevHandle& g, uint32_t s) {
+  return (RingSlot*)(g.ring + (size_t)s * g.slot_stride);
+}
+
+// One thread: claim frame f if its request has been served.
+__device__ PullJob pull_claim_frame(const DevHandle& g, int f) {
+  PullJob j{-1, 0, 0, 0, 0};
+  const uint32_t src = ld_acq(&g.fsrc[f]);
+  if (src == SRC_NONE) return j;
+  const uint32_t s = src / g.max_rpc_pages, i = src % g.max_rpc_pages;
+  const unsigned long long t = ld_rlx64(&g.dticket[s]);
+  if (ld_acq_sys64(&g.done[s].done) != t + 1) return j;
+  if (atomicCAS(&g.fstate[f], (uint32_t)FR_FILLING, (uint32_t)FR_COPYING) != FR_FILLING) return j;
+  j.f = f;
+  j.s = s;
+  j.i = i;
+  j.t = t;
+  j.res = (long long)ld_rlx64((const unsigned long long*)&g.done[s].result);
+  return j;
+}
+
+// One warp: find a served request with pages still FILLING and claim one page.
+// Scans 32 slots starting at `start`.
+__device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
+  const int lane = lane_id();
+  PullJob j{-1, 0, 0, 0, 0};
+  const uint32_t s = (start + lane) % g.rpc_slots;
+  bool cand = false;
+  unsigned long long t = 0;
+  if ((uint32_t)lane < g.rpc_slots) {
+    t = ld_rlx64(&g.dticket[s]);
+    cand = ld_rlx(&g.dcopied[s]) < ld_rlx(&g.dnpages[s]) && ld_acq_sys64(&g.done[s].done) == t + 1;
+  }
+  unsigned m = __ballot_sync(kFull, cand);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const uint32_t ss = (uint32_t)__shfl_sync(kFull, (int)s, src);
+    const unsigned long long tt = __shfl_sync(kFull, t, src);
+    const uint32_t np = ld_rlx(&g.dnpages[ss]);
+    int got = -1;
+    for (uint32_t base = 0; base < np && got < 0; base += 32) {
+      const uint32_t i = base + lane;
+      int f = -1;
+      if (i < np) {
+        f = (int)ld_rlx(&g.dframes[(size_t)ss * g.max_rpc_pages + i]);
+        if (f >= (int)g.n_frames || ld_rlx(&g.fstate[f]) != FR_FILLING ||
+            ld_acq(&g.fsrc[f]) != ss * g.max_rpc_pages + i)
+          f = -1;
+      }
+      unsigned fm = __ballot_sync(kFull, f >= 0);
+      while (fm && got < 0) {
+        const int l = __ffs(fm) - 1;
+        fm &= fm - 1;
+        int ok = 0;
+        if (lane == l && atomicCAS(&g.fstate[f], (uint32_t)FR_FILLING, (uint32_t)FR_COPYING) == FR_FILLING) {
+          // the slot may have been freed and reused since it was found served:
+          // the claim only stands for the request that was checked
+          __threadfence();
+          ok = ld_rlx64(&g.dticket[ss]) == tt;
+          if (!ok) st_rel(&g.fstate[f], (uint32_t)FR_FILLING);
+        }
+        if (__shfl_sync(kFull, ok, l)) got = (int)(base + l);
+      }
+      if (got >= 0) {
+        j.f = (int)ld_rlx(&g.dframes[(size_t)ss * g.max_rpc_pages + got]);
+        j.s = ss;
+        j.i = (uint32_t)got;
+        j.t = tt;
+        j.res = (long long)ld_rlx64((const unsigned long long*)&g.done[ss].result);
+      }
+    }
+    if (got >= 0) break;
+  }
+  return j;
+}
+
+// Copy n bytes of host staging into a frame with `nt` threads (rank `r`).
+// Staging is read with ld.global.cv: the slot is rewritten by the host every lap.
+__device__ __forceinline__ void copy_in(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n,
+                                        uint32_t r, uint32_t nt) {
+  const uint32_t n16 = n >> 4;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  uint32_t i = r;
+  for (; i + 7 * nt < n16; i += 8 * nt) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcv(s4 + i + u * nt);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d4[i + u * nt] = v[u];
+  }
+  for (; i < n16; i += nt) d4[i] = __ldcv(s4 + i);
+  for (uint32_t b = 16 * n16 + r; b < n; b += nt) dst[b] = __ldcv(src + b);
+}
+
+// Copy a claimed page (all `nt` threads of the group), without the completion.
+__device__ __forceinline__ bool pull_copy(const DevHandle& g, const PullJob& j, uint32_t r, uint32_t nt) {
+  const uint32_t valid = ld_rlx(&g.fvalid[j.f]);
+  const bool ok = j.res >= (long long)j.i * g.page_size + valid;
+  if (ok)
+    copy_in(g.staging + (size_t)j.s * g.slot_bytes + (size_t)j.i * g.page_size,
+            g.frames + ((size_t)j.f << g.page_shift), valid, r, nt);
+  __threadfence();
+  return ok;
+}
+
+// One thread, after the group's copy: publish the page and free the slot after its last page.
+__device__ __forceinline__ void pull_finish(const DevHandle& g, const PullJob& j, bool ok) {
+  st_rlx(&g.fsrc[j.f], SRC_NONE);
+  st_rel(&g.fstate[j.f], ok ? (uint32_t)FR_READY : (uint32_t)FR_ERROR);
+  const uint32_t c = atomicAdd(&g.dcopied[j.s], 1u) + 1;
+  if (c == ld_rlx(&g.dnpages[j.s])) {
+    __threadfence_system();
+    st_rel_sys64(&ring_slot(g, j.s)->seq, j.t + g.rpc_slots);
+    atomicAdd(&g.ctrl->freed.v, 1ull);
+  }
+}
+
+// One warp: help with one served page.  Returns true if it copied one.
+__device__ bool warp_help(const DevHandle& g, uint32_t start) {
+  PullJob j = pull_claim_any(g, start);
+  if (j.f < 0) return false;
+  bool ok = pull_copy(g, j, (uint32_t)lane_id(), 32);
+  __syncwarp();
+  if (lane_id() == 0) pull_finish(g, j, ok);
+  __syncwarp();
+  return true;
+}
+
+// Whole block: copy frame f if served (target >= 0), else help with any served
+// page.  Returns true if the block copied a page.  Block-uniform.
+__device__ bool block_help(const DevHandle& g, int target, bool any) {
+  __shared__ PullJob s_job;
+  const uint32_t tid = threadIdx.x;
+  if (tid < 32) {
+    PullJob j{-1, 0, 0, 0, 0};
+    if (target >= 0 && tid == 0) j = pull_claim_frame(g, target);
+    j.f = bcast(j.f);
+    if (j.f < 0 && any) {
+      const uint32_t start = (uint32_t)((blockIdx.x * 37u + (uint32_t)(now_ns() >> 10)) % g.rpc_slots);
+      j = pull_claim_any(g, start);
+    }
+    if (tid == 0) s_job = j;
+  }
+  __syncthreads();
+  const PullJob j = s_job;
+  __syncthreads();
+  if (j.f < 0) return false;
+  const bool ok = pull_copy(g, j, tid, blockDim.x);
+  __syncthreads();
+  if (tid == 0) pull_finish(g, j, ok);
+  return true;
+}
+
 // ---------------------------------------------------------------- request ring
 __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
                           const uint32_t* s_frames, unsigned long long deadline) {
   const int lane = lane_id();
   unsigned long long t = 0;
-  int ok = 1;
-  if (lane == 0) {
-    t = atomicAdd(&g.ctrl->ring_tail.v, 1ull);
-    RingSlot* s = (RingSlot*)(g.ring + (size_t)(t % g.rpc_slots) * g.slot_stride);
-    while (ld_acq_sys64(&s->seq) != t) {
-      if (now_ns() > deadline) { ok = 0; break; }
-      __nanosleep(64);
-    }
-  }
+  if (lane == 0) t = atomicAdd(&g.ctrl->ring_tail.v, 1ull);
   t = bcast64(t);
-  if (!bcast(ok)) {
-    if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
-    return -kETIMEDOUT;
+  const uint32_t si = (uint32_t)(t % g.rpc_slots);
+  RingSlot* s = ring_slot(g, si);
+  for (unsigned ns = 64;;) {  // wait until the slot is free for this lap
+    int free_ = 0, late = 0;
+    if (lane == 0) {
+      free_ = ld_acq_sys64(&s->seq) == t;
+      late = now_ns() > deadline;
+    }
+    if (bcast(free_)) break;
+    if (bcast(late)) {
+      if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
+      return -kETIMEDOUT;
+    }
+    // in pull mode slots are freed by GPU copies: help instead of idling
+    if (g.xfer == GFS_XFER_PULL && warp_help(g, si)) continue;
+    if (lane == 0) __nanosleep(ns);
+    __syncwarp();
+    if (ns < 2048) ns <<= 1;
   }
-  RingSlot* s = (RingSlot*)(g.ring + (size_t)(t % g.rpc_slots) * g.slot_stride);
-  for (uint32_t i = lane; i < n; i += 32) st_sys32(&s->frames[i], s_frames[i]);
+  if (g.xfer == GFS_XFER_PULL) {
+    for (uint32_t i = lane; i < n; i += 32) g.dframes[(size_t)si * g.max_rpc_pages + i] = s_frames[i];
+    if (lane == 0) {
+      st_rlx64(&g.dticket[si], t);
+      st_rlx(&g.dnpages[si], n);
+      st_rlx(&g.dcopied[si], 0u);
+    }
+    __syncwarp();
+    __threadfence();
+    __syncwarp();
+    for (uint32_t i = lane; i < n; i += 32) st_rel(&g.fsrc[s_frames[i]], si * g.max_rpc_pages + i);
+  } else {
+    for (uint32_t i = lane; i < n; i += 32) st_sys32(&s->frames[i], s_frames[i]);
+  }
   if (lane == 0) {
     st_sys32(&s->fid, fid);
     st_sys32(&s->npages, n);
@@ -485,11 +672,17 @@ __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi
     const bool is_ra = i >= demand;
     int f = take_frame(g, is_ra, seq0, key, deadline);
     while (f < 0 && !is_ra && i == 0) {  // the first demand page waits for a victim
-      if (now_ns() > deadline) {
+      int late = 0;
+      if (lane == 0) late = now_ns() > deadline;
+      if (bcast(late)) {
         if (lane == 0) stat_add(g, ST_ENOMEM, 1);
         return -kENOMEM;
       }
-      __nanosleep(256);
+      // pull mode: frames may all be waiting to be copied out of staging
+      if (!(g.xfer == GFS_XFER_PULL && warp_help(g, (uint32_t)(q % g.rpc_slots)))) {
+        if (lane == 0) __nanosleep(256);
+        __syncwarp();
+      }
       f = take_frame(g, false, seq0, key, deadline);
     }
     if (f < 0) break;
@@ -501,6 +694,7 @@ __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi
       st_rlx(&g.fmark[f], 0u);
       st_rlx(&g.fvalid[f], expected_valid(g, fi, q));
       st_rlx64(&g.faseq[f], atomicAdd(&g.ctrl->alloc_counter.v, 1ull));
+      if (g.fsrc) st_rlx(&g.fsrc[f], SRC_NONE);
       __threadfence();
       if (pin) atomicAdd(&g.fpins[f], 1u);
       st_rel(&g.fstate[f], FR_FILLING);
@@ -607,22 +801,11 @@ __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, const F
   return f0;
 }
 
-// Wait until frame f leaves FILLING.  Returns the state or -ETIMEDOUT.
-__device__ int wait_filled(const DevHandle& g, int f, unsigned long long deadline) {  // one thread
-  uint32_t st;
-  unsigned ns = 64;
-  while ((st = ld_acq(&g.fstate[f])) == FR_FILLING) {
-    if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return -kETIMEDOUT; }
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
-  }
-  return (int)st;
-}
-
-// Make page p resident and pinned for the caller (warp 0).  Returns its frame or -errno.
-__device__ int acquire_page(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
-                            unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
-                            uint32_t* s_frames) {
+// Find or install page p and pin its frame for the caller (warp 0); does not
+// wait.  Returns the frame (its state in *state) or -errno.
+__device__ int acquire_begin(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
+                             unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
+                             uint32_t* s_frames, int* state) {
   const int lane = lane_id();
   const unsigned long long key = make_key(fid, p);
   for (;;) {
@@ -639,33 +822,14 @@ __device__ int acquire_page(const DevHandle& g, int stream, uint32_t fid, const 
         st = frame_pin(g, f, key);
         if (st >= 0) {
           stat_add(g, ST_HITS, 1);
-          if (st == FR_FILLING) {
-            stat_add(g, ST_COALESCED, 1);
-            st = wait_filled(g, f, deadline);
-          }
-          if (st != FR_READY) frame_unpin(g, f);
+          if (st == FR_FILLING || st == FR_COPYING) stat_add(g, ST_COALESCED, 1);
         } else {
           stat_add(g, ST_RETRIES, 1);
         }
       }
       st = bcast(st);
       if (st == -1) continue;
-      if (st == FR_ERROR) {
-        if (lane == 0) stat_add(g, ST_EIO, 1);
-        return -kEIO;
-      }
-      if (st < 0) return st;
-      if (st != FR_READY) continue;
-      if (g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra) {  // R4
-        uint32_t m = 0, w = 0;
-        if (lane == 0) {
-          m = atomicExch(&g.fmark[f], 0u);
-          w = ld_rlx(&g.fwindow[f]);
-        }
-        m = (uint32_t)bcast((int)m);
-        w = (uint32_t)bcast((int)w);
-        if (m) async_readahead(g, fid, fi, (unsigned long long)m - 1, w, seq0, deadline, s_frames);
-      }
+      *state = st;
       return f;
     }
     int r = handle_miss(g, stream, fid, fi, p, p1, seq0, deadline, s_frames);
@@ -674,18 +838,57 @@ __device__ int acquire_page(const DevHandle& g, int stream, uint32_t fid, const 
       continue;
     }
     if (r < 0) return r;
-    int st = 0;
-    if (lane == 0) {
-      st = wait_filled(g, r, deadline);
-      if (st != FR_READY) frame_unpin(g, r);
-      if (st == FR_ERROR) stat_add(g, ST_EIO, 1);
-    }
-    st = bcast(st);
-    if (st == FR_ERROR) return -kEIO;
-    if (st < 0) return st;
-    if (st != FR_READY) return -kEIO;
+    *state = FR_FILLING;
     return r;
   }
+}
+
+// Whole block: wait until pinned frame f leaves FILLING / COPYING (in pull mode
+// copying it, or other served pages, meanwhile).  Returns the state or
+// -ETIMEDOUT.  Block-uniform.
+__device__ int block_wait_ready(const DevHandle& g, int f, unsigned long long deadline) {
+  __shared__ int s_st;
+  unsigned ns = 64;
+  for (uint32_t it = 0;; ++it) {
+    if (threadIdx.x == 0) {
+      int st = (int)ld_acq(&g.fstate[f]);
+      if ((st == FR_FILLING || st == FR_COPYING) && now_ns() > deadline) {
+        stat_add(g, ST_TIMEOUTS, 1);
+        st = -kETIMEDOUT;
+      }
+      s_st = st;
+    }
+    __syncthreads();
+    const int st = s_st;
+    __syncthreads();
+    if (st != FR_FILLING && st != FR_COPYING) return st;
+    if (g.xfer == GFS_XFER_PULL) {
+      // the page itself first; other served pages only now and then (their
+      // completion records are read over the host link)
+      if (block_help(g, st == FR_FILLING ? f : -1, (it & 7) == 7)) {
+        ns = 64;
+        continue;
+      }
+    }
+    if (threadIdx.x == 0) __nanosleep(ns);
+    if (ns < 2048) ns <<= 1;
+  }
+}
+
+// R4 for a READY page just acquired: the first reader of a marked page issues
+// the asynchronous window (warp 0).
+__device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDev& fi, int f, unsigned long long seq0,
+                           unsigned long long deadline, uint32_t* s_frames) {
+  const int lane = lane_id();
+  if (!(g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra)) return;
+  uint32_t m = 0, w = 0;
+  if (lane == 0) {
+    m = atomicExch(&g.fmark[f], 0u);
+    if (m) w = ld_rlx(&g.fwindow[f]);
+  }
+  m = (uint32_t)bcast((int)m);
+  w = (uint32_t)bcast((int)w);
+  if (m) async_readahead(g, fid, fi, (unsigned long long)m - 1, w, seq0, deadline, s_frames);
 }
 
 // R5: account the delivered bytes, unpin, and queue the frame once fully consumed.
@@ -784,7 +987,7 @@ __device__ __forceinline__ void copy_out(const uint8_t* __restrict__ src, uint8_
 template <bool FUSED>
 __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigned long long off,
                                 unsigned long long len, uint8_t* buf, Sums& acc) {
-  __shared__ int s_frame;
+  __shared__ int s_frame, s_state;
   __shared__ unsigned long long s_seq0;
   __shared__ uint32_t s_frames[MAX_RPC_PAGES];
   const uint32_t tid = threadIdx.x;
@@ -802,15 +1005,32 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
   long long err = 0;
   for (unsigned long long p = p0; p <= p1; ++p) {
     if (tid < 32) {
-      int r = acquire_page(g, stream, (uint32_t)fid, fi, p, p1, seq0, deadline, s_frames);
-      if (tid == 0) s_frame = r;
+      int st = 0;
+      int r = acquire_begin(g, stream, (uint32_t)fid, fi, p, p1, seq0, deadline, s_frames, &st);
+      if (tid == 0) {
+        s_frame = r;
+        s_state = st;
+      }
     }
     __syncthreads();
     const int f = s_frame;
+    int st = s_state;
+    __syncthreads();
     if (f < 0) {
       err = f;
       break;
     }
+    if (st == FR_FILLING || st == FR_COPYING) st = block_wait_ready(g, f, deadline);
+    if (st != FR_READY) {
+      if (tid == 0) {
+        frame_unpin(g, f);
+        if (st == FR_ERROR) stat_add(g, ST_EIO, 1);
+      }
+      err = st < 0 ? st : -kEIO;
+      __syncthreads();
+      break;
+    }
+    if (tid < 32) check_mark(g, (uint32_t)fid, fi, f, seq0, deadline, s_frames);
     const unsigned long long base = p << g.page_shift;
     const unsigned long long lo = (off > base ? off : base) - base;
     const unsigned long long hi = (end < base + g.page_size ? end : base + g.page_size) - base;

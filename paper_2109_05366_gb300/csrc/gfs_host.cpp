@@ -269,6 +269,8 @@ int gfs_shutdown(gfs_ctx* ctx) {
   if (ctx->h_out) cudaFreeHost(ctx->h_out);
   if (ctx->dev.fetch_count) cudaFree(ctx->dev.fetch_count);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+  if (ctx->h_staging) cudaFreeHost(ctx->h_staging);
+  if (ctx->h_done) cudaFreeHost(ctx->h_done);
   delete ctx;
   return 0;
 }
@@ -278,12 +280,14 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   const gfs_config c = *cfg_in;
   if (!is_pow2(c.page_size) || c.page_size < 4096 || c.page_size > (64u << 20)) return -EINVAL;
   if (c.cache_bytes < c.page_size) return -EINVAL;
-  if (c.mode > GFS_MODE_ONDEMAND || c.xfer != GFS_XFER_DMA) return -EINVAL;
+  if (c.mode > GFS_MODE_ONDEMAND || c.xfer > GFS_XFER_PULL) return -EINVAL;
   if (c.rpc_slots < 1 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
   if (c.host_threads < 1 || c.host_threads > 256 || c.max_files < 1 || c.max_files > MAX_FILES) return -EINVAL;
   if (c.max_streams < 1 || c.timeout_ns == 0) return -EINVAL;
   const uint64_t F64 = c.cache_bytes / c.page_size;
   if (F64 > MAX_FRAMES) return -EINVAL;
+  const uint64_t slot_bytes = (uint64_t)c.max_rpc_pages * c.page_size;
+  if (c.xfer == GFS_XFER_PULL && slot_bytes * c.rpc_slots > (32ull << 30)) return -EINVAL;  // staging cap
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return -ENODEV;
   if (c.device < 0 || c.device >= ndev) return -EINVAL;
@@ -313,6 +317,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.rpc_slots = c.rpc_slots;
   g.slot_stride = slot_stride(c.max_rpc_pages);
   g.fifo_cap = F;
+  g.xfer = c.xfer;
+  g.slot_bytes = slot_bytes;
 
   // device arena
   size_t off = 0;
@@ -329,7 +335,10 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
                o_files = take((size_t)c.max_files * sizeof(FileDev)),
                o_last = take((size_t)c.max_streams * c.max_files * 8),
                o_trpc = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_rpc_rec)),
-               o_tev = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_evict_rec));
+               o_tev = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_evict_rec)),
+               o_dtick = take((size_t)c.rpc_slots * 8), o_dnp = take((size_t)c.rpc_slots * 4),
+               o_dcop = take((size_t)c.rpc_slots * 4), o_dfr = take((size_t)c.rpc_slots * c.max_rpc_pages * 4),
+               o_fsrc = take((size_t)F * 4);
   ctx->arena_bytes = off;
   rc = cuda_err(cudaMalloc(&ctx->d_arena, off));
   if (!rc) rc = cuda_err(cudaMemset(ctx->d_arena, 0, off));
@@ -359,6 +368,29 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.trace_evict = (gfs_evict_rec*)(a + o_tev);
   g.fetch_count = nullptr;
   g.debug_pages = 0;
+  g.dticket = (unsigned long long*)(a + o_dtick);
+  g.dnpages = (uint32_t*)(a + o_dnp);
+  g.dcopied = (uint32_t*)(a + o_dcop);
+  g.dframes = (uint32_t*)(a + o_dfr);
+  g.fsrc = (uint32_t*)(a + o_fsrc);
+  g.staging = nullptr;
+  g.done = nullptr;
+  if (c.xfer == GFS_XFER_PULL) {
+    rc = cuda_err(cudaHostAlloc((void**)&ctx->h_staging, slot_bytes * c.rpc_slots,
+                                cudaHostAllocMapped | cudaHostAllocPortable));
+    if (!rc) rc = cuda_err(cudaHostAlloc((void**)&ctx->h_done, sizeof(PullDone) * c.rpc_slots,
+                                         cudaHostAllocMapped | cudaHostAllocPortable));
+    void* dp = nullptr;
+    if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&dp, ctx->h_staging, 0));
+    g.staging = (uint8_t*)dp;
+    if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&dp, ctx->h_done, 0));
+    g.done = (PullDone*)dp;
+    if (rc) {
+      gfs_shutdown(ctx);
+      return rc;
+    }
+    memset(ctx->h_done, 0, sizeof(PullDone) * c.rpc_slots);
+  }
 
   // request ring in mapped pinned memory
   const size_t ring_bytes = (size_t)c.rpc_slots * g.slot_stride;
@@ -394,10 +426,16 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.staging_pages = std::max<uint32_t>(1, c.staging_bytes / c.page_size);
   sc.threads = c.host_threads;
   sc.n_frames = F;
+  if (c.xfer == GFS_XFER_PULL) {
+    sc.pull_staging = ctx->h_staging;
+    sc.pull_done = ctx->h_done;
+    sc.slot_bytes = slot_bytes;
+  }
   const size_t stg = (size_t)sc.staging_pages * c.page_size;
   ctx->io = new IoService(
       sc,
       [ctx, stg](int) -> Sink* {
+        if (ctx->cfg.xfer == GFS_XFER_PULL) return new (std::nothrow) HostSink(nullptr, nullptr, 0, 0);
         DmaSink* s = new (std::nothrow) DmaSink(ctx->cfg.device, ctx->d_frames, ctx->dev.fstate, ctx->dev.page_shift, stg);
         if (s && s->init() != 0) {
           delete s;
@@ -514,6 +552,14 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
     usleep(50);
   }
   ctx->io->drain_sinks();
+  if (ctx->cfg.xfer == GFS_XFER_PULL) {  // copy out what was served but never read
+    int rc = launch_drain(ctx->dev, s);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    unsigned long long freed = 0;
+    CK(cudaMemcpy(&freed, &ctx->dev.ctrl->freed.v, 8, cudaMemcpyDeviceToHost));
+    if (freed < tail) return -ETIMEDOUT;
+  }
   ctx->io->stats.requests = 0;
   ctx->io->stats.preads = 0;
   ctx->io->stats.bytes = 0;

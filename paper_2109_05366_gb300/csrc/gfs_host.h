@@ -32,6 +32,7 @@ class IoService;
 
 // Entry points of the device code, implemented in gfs_kernels.cu.
 int launch_reset(const DevHandle& g, cudaStream_t s);
+int launch_drain(const DevHandle& g, cudaStream_t s);
 int launch_scan(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
                 uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
 int launch_read_many(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
@@ -50,6 +51,8 @@ struct gfs_ctx {
   uint8_t* d_frames = nullptr;
   size_t arena_bytes = 0;
   uint8_t* h_ring = nullptr;  // mapped pinned
+  uint8_t* h_staging = nullptr;  // GFS_XFER_PULL: per-slot staging, mapped pinned
+  gfs::PullDone* h_done = nullptr;  // GFS_XFER_PULL: completion records, mapped pinned
   std::vector<gfs::HostFile> files;
   gfs::IoService* io = nullptr;
   uint8_t* d_scan_buf = nullptr;  // per-block gread buffers of gfs_scan

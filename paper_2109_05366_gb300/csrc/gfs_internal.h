@@ -19,8 +19,10 @@
 
 namespace gfs {
 
-// Frame states.  RECLAIM = claimed by an evictor, not yet reinstalled.
-enum : uint32_t { FR_EMPTY = 0, FR_FILLING = 1, FR_READY = 2, FR_ERROR = 3, FR_RECLAIM = 4 };
+// Frame states.  RECLAIM = claimed by an evictor, not yet reinstalled;
+// COPYING = (GFS_XFER_PULL) a threadblock is copying the page out of host staging.
+enum : uint32_t { FR_EMPTY = 0, FR_FILLING = 1, FR_READY = 2, FR_ERROR = 3, FR_RECLAIM = 4, FR_COPYING = 5 };
+constexpr uint32_t SRC_NONE = 0xffffffffu;
 
 constexpr uint64_t KEY_NONE = ~0ull;
 constexpr uint64_t ENTRY_EMPTY = ~0ull;
@@ -52,7 +54,15 @@ struct Ctrl {
   Line ticket;         // serialized mode: next stride allowed to gread
   Line trace_rpc_n;
   Line trace_evict_n;
+  Line freed;          // GFS_XFER_PULL: requests whose pages have all been copied out of staging
   unsigned long long stat[ST_COUNT];
+};
+
+// GFS_XFER_PULL completion record of a slot, in mapped pinned memory, written by
+// the host after its pread: result (bytes read or -errno), then done = ticket + 1.
+struct PullDone {
+  unsigned long long done;
+  long long result;
 };
 
 // Per-file device state.
@@ -121,6 +131,17 @@ struct DevHandle {
   gfs_rpc_rec* trace_rpc;
   gfs_evict_rec* trace_evict;
   uint32_t* fetch_count;  // per page of fid 0
+  // GFS_XFER_PULL: host staging per slot (device view), completion records, and
+  // the device copy of each in-flight request
+  uint32_t xfer;
+  unsigned long long slot_bytes;  // staging bytes per slot = max_rpc_pages * page_size
+  uint8_t* staging;               // rpc_slots * slot_bytes, mapped pinned
+  PullDone* done;                 // rpc_slots records, mapped pinned
+  unsigned long long* dticket;    // ticket of the request in each slot
+  uint32_t* dnpages;              // pages of that request
+  uint32_t* dcopied;              // pages copied out so far
+  uint32_t* dframes;              // rpc_slots * max_rpc_pages frame indices
+  uint32_t* fsrc;                 // per frame: slot * max_rpc_pages + page index, SRC_NONE when not in flight
 };
 
 }  // namespace gfs

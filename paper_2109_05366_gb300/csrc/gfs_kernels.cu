@@ -52,6 +52,35 @@ __device__ __forceinline__ void checksum_range(const uint8_t* __restrict__ p, un
   for (unsigned long long j = 16 * n16 + tid; j < n; j += nt) dev::sums_add1(acc, p[j], off + j);
 }
 
+// Serialized mode: wait (helping in pull mode) until no frame is being filled.
+__device__ void block_quiesce(const DevHandle& g) {
+  const unsigned long long dl = dev::now_ns() + g.timeout_ns;
+  __shared__ int s_late;
+  for (;;) {
+    bool busy = false;
+    for (uint32_t f = threadIdx.x; f < g.n_frames && !busy; f += blockDim.x) {
+      const uint32_t st = dev::ld_acq(&g.fstate[f]);
+      busy = st == FR_FILLING || st == FR_COPYING;
+    }
+    if (threadIdx.x == 0) s_late = dev::now_ns() > dl;
+    const int any_busy = __syncthreads_or(busy);
+    const int late = s_late;
+    __syncthreads();
+    if (!any_busy || late) break;
+    if (g.xfer == GFS_XFER_PULL && dev::block_help(g, -1, true)) continue;
+    if (threadIdx.x == 0) __nanosleep(256);
+  }
+  __syncthreads();
+}
+
+// Pull mode, before a block exits: copy out served requests nobody waits for
+// (asynchronous readahead at the end of a scan) so their ring slots free up.
+__device__ void block_help_drain(const DevHandle& g) {
+  if (g.xfer != GFS_XFER_PULL) return;
+  for (int i = 0; i < 4096; ++i)
+    if (!dev::block_help(g, -1, true)) break;
+}
+
 template <bool FUSED>
 __global__ void __launch_bounds__(512) k_scan(DevHandle g, int fid, unsigned long long stride,
                                                unsigned long long read_len, unsigned long long nstrides, int serialize,
@@ -77,10 +106,7 @@ __global__ void __launch_bounds__(512) k_scan(DevHandle g, int fid, unsigned lon
     Sums acc{0ull, 0ull};
     long long r = dev::gread_impl<FUSED>(g, (int)b, fid, off, read_len, buf, acc);
     if (serialize) {  // wait until every request of this gread has been served
-      const unsigned long long dl = dev::now_ns() + g.timeout_ns;
-      for (uint32_t f = tid; f < g.n_frames; f += blockDim.x)
-        while (dev::ld_acq(&g.fstate[f]) == FR_FILLING && dev::now_ns() < dl) __nanosleep(256);
-      __syncthreads();
+      block_quiesce(g);
       if (tid == 0) dev::st_rel64(&g.ctrl->ticket.v, s + 1);
     }
     if (!FUSED && r > 0) checksum_range(buf, (unsigned long long)r, off, acc);
@@ -92,6 +118,7 @@ __global__ void __launch_bounds__(512) k_scan(DevHandle g, int fid, unsigned lon
     }
     __syncthreads();
   }
+  block_help_drain(g);
 }
 
 __global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_t n, const uint64_t* off,
@@ -101,6 +128,23 @@ __global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_
     long long r = dev::gread(g, (int)blockIdx.x, fid, off[i], len[i], buf + dst[i]);
     if (threadIdx.x == 0) ret[i] = r;
     __syncthreads();
+  }
+  block_help_drain(g);
+}
+
+// GFS_XFER_PULL: copy out every request in flight (cache reset, end of use).
+__global__ void __launch_bounds__(512) k_drain(DevHandle g) {
+  if (g.xfer != GFS_XFER_PULL) return;
+  __shared__ int s_more;
+  const unsigned long long dl = dev::now_ns() + g.timeout_ns;
+  for (;;) {
+    if (threadIdx.x == 0)
+      s_more = dev::ld_acq64(&g.ctrl->freed.v) < dev::ld_acq64(&g.ctrl->ring_tail.v) && dev::now_ns() < dl;
+    __syncthreads();
+    const int more = s_more;
+    __syncthreads();
+    if (!more) break;
+    if (!dev::block_help(g, -1, true) && threadIdx.x == 0) __nanosleep(1000);
   }
 }
 
@@ -115,6 +159,7 @@ __global__ void k_reset(DevHandle g) {
     g.fwindow[f] = 0;
     g.fmark[f] = 0;
     g.faseq[f] = ~0ull;
+    if (g.fsrc) g.fsrc[f] = SRC_NONE;
   }
   const size_t nslots = (size_t)g.nbuckets * BUCKET;
   for (size_t i = tid; i < nslots; i += nt) g.tab[i] = ENTRY_EMPTY;
@@ -136,6 +181,7 @@ __global__ void k_reset(DevHandle g) {
     g.ctrl->trace_rpc_n.v = 0;
     g.ctrl->trace_evict_n.v = 0;
     for (int i = 0; i < ST_COUNT; ++i) g.ctrl->stat[i] = 0;
+    // ring_tail and freed keep counting across resets (requests still map to slots)
     // ring_tail is left alone: the ring keeps its position across resets
   }
 }
@@ -173,6 +219,11 @@ static int cuda_err(cudaError_t e) {
 
 int launch_reset(const DevHandle& g, cudaStream_t s) {
   k_reset<<<304, 512, 0, s>>>(g);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_drain(const DevHandle& g, cudaStream_t s) {
+  k_drain<<<32, 256, 0, s>>>(g);
   return cuda_err(cudaGetLastError());
 }
 

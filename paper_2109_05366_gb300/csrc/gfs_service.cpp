@@ -133,6 +133,30 @@ void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint
   }
 }
 
+void IoService::serve_pull(uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages) {
+  FileView fv{-1, 0};
+  const bool have = files_(fid, &fv);
+  const uint64_t off = page_lo << cfg_.page_shift;
+  long long result = -EBADF;
+  if (have) {
+    result = 0;
+    if (off < fv.size) {
+      const size_t want = (size_t)std::min<uint64_t>((uint64_t)npages << cfg_.page_shift, fv.size - off);
+      const ssize_t got = do_pread(fv.fd, cfg_.pull_staging + (size_t)slot * cfg_.slot_bytes, want, off);
+      stats.preads.fetch_add(1, std::memory_order_relaxed);
+      if (got < 0) {
+        stats.errors.fetch_add(1, std::memory_order_relaxed);
+      } else {
+        stats.bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
+      }
+      result = got;
+    }
+  }
+  PullDone* d = cfg_.pull_done + slot;
+  __atomic_store_n(&d->result, result, __ATOMIC_RELAXED);
+  __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);  // the GPU may copy now
+}
+
 void IoService::run(int idx) {
   Sink* sink = sinks_[idx];
   sink->thread_init();
@@ -156,9 +180,21 @@ void IoService::run(int idx) {
     const uint32_t npages = vs->npages;
     const uint64_t page_lo = vs->page_lo;
     const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
+    stats.requests.fetch_add(1, std::memory_order_relaxed);
+    if (cfg_.pull_staging) {  // the GPU frees the slot once it has copied the pages
+      if (npages == 0 || (uint64_t)npages << cfg_.page_shift > cfg_.slot_bytes) {
+        stats.errors.fetch_add(1, std::memory_order_relaxed);
+        PullDone* d = cfg_.pull_done + h % cfg_.slots;
+        __atomic_store_n(&d->result, (long long)-EINVAL, __ATOMIC_RELAXED);
+        __atomic_store_n(&d->done, h + 1, __ATOMIC_RELEASE);
+      } else {
+        serve_pull((uint32_t)(h % cfg_.slots), h, fid, page_lo, npages);
+      }
+      served_.fetch_add(1, std::memory_order_release);
+      continue;
+    }
     for (uint32_t i = 0; i < n; ++i) frames[i] = vs->frames[i];
     __atomic_store_n(&s->seq, h + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
-    stats.requests.fetch_add(1, std::memory_order_relaxed);
     bool bad = npages == 0 || npages > MAX_RPC_PAGES;
     for (uint32_t i = 0; i < n && !bad; ++i) bad = frames[i] >= cfg_.n_frames;
     if (bad) {

@@ -49,6 +49,11 @@ struct ServiceConfig {
   uint32_t staging_pages = 1;  // pages per staging buffer
   uint32_t threads = 1;
   uint32_t n_frames = 0xffffffffu;  // frame indices at or above this are rejected
+  // GFS_XFER_PULL: each slot preads into its own staging region and publishes a
+  // completion record; the GPU copies the pages and frees the slot.
+  uint8_t* pull_staging = nullptr;
+  PullDone* pull_done = nullptr;
+  uint64_t slot_bytes = 0;
 };
 
 struct ServiceStats {
@@ -74,6 +79,7 @@ class IoService {
  private:
   void run(int idx);
   void serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
+  void serve_pull(uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages);
   ssize_t do_pread(int fd, uint8_t* buf, size_t n, uint64_t off);
 
   ServiceConfig cfg_;

@@ -48,11 +48,16 @@ def _check_scan(gfs, path, stride, cnt, sm, hs, read_len=None):
 
 
 # ------------------------------------------------ config 1: 64 MiB, fits the cache
+XFERS = [0, 1]  # GFS_XFER_DMA, GFS_XFER_PULL
+
+
+@pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("fused", [False, True])
-def test_config1_scan_exact(torch_cuda, gfs, datadir, mode, fused):
+def test_config1_scan_exact(torch_cuda, gfs, datadir, mode, fused, xfer):
     path = _file(datadir, 1, 64 * MiB)
-    with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB, mode=mode, debug_counts=1) as ctx:
+    with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB, mode=mode, debug_counts=1, xfer=xfer,
+                     max_rpc_pages=16) as ctx:
         fid = ctx.open(path)
         for rep in range(2):
             out = ctx.scan(fid, 1 * MiB, blocks=64, threads=256, fused=fused)
@@ -80,6 +85,7 @@ def test_config1_second_pass_hits(torch_cuda, gfs, datadir):
 
 
 # ------------------------------------------------ serialized: exact policy logs
+@pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("size,page,frames,blocks,stride,ra_cap,mode,async_ra", [
     (64 * MiB, 256 * KiB, 512, 64, MiB, 8, 0, 1),          # config-1 shape
     (64 * MiB + 12345, 512 * KiB, 16, 8, MiB, 8, 0, 1),    # config-2 shape, file 8x cache, ragged tail
@@ -88,29 +94,30 @@ def test_config1_second_pass_hits(torch_cuda, gfs, datadir):
     (8 * MiB, 128 * KiB, 10, 4, 256 * KiB, 8, 1, 1),       # on-demand
 ])
 def test_serialized_logs_match_oracle(torch_cuda, gfs, datadir, size, page, frames, blocks, stride, ra_cap, mode,
-                                      async_ra):
+                                      async_ra, xfer):
     path = _file(datadir, 2, size)
     reserve = policy.default_reserve(blocks, stride, page)
     with gfs.Context(cache_bytes=frames * page, page_size=page, mode=mode, ra_cap_pages=ra_cap, async_ra=async_ra,
-                     trace_capacity=1 << 16, reserve_frames=reserve, max_rpc_pages=64) as ctx:
+                     trace_capacity=1 << 16, reserve_frames=reserve, max_rpc_pages=16, xfer=xfer) as ctx:
         fid = ctx.open(path)
         out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
         torch_cuda.cuda.synchronize()
         _check_scan(gfs, path, stride, *out)
         rpc, ev, nr, ne = ctx.trace()
     sim, res = policy.run_scan(path, page, frames, stride, blocks, mode=("ondemand" if mode else "readahead"),
-                               ra_cap=ra_cap, reserve=reserve, async_ra=bool(async_ra), max_rpc_pages=64)
+                               ra_cap=ra_cap, reserve=reserve, async_ra=bool(async_ra), max_rpc_pages=16)
     assert nr == len(sim.rpc_log) and ne == len(sim.evict_log)
     assert rpc == sim.rpc_log
     assert ev == sim.evict_log
 
 
 # ------------------------------------------------ concurrent: larger than the cache
+@pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("threads", [256, 512])
-def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads):
+def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads, xfer):
     size, page, cache, blocks = 256 * MiB + 4096 * 3, 512 * KiB, 32 * MiB, 48
     path = _file(datadir, 3, size)
-    with gfs.Context(cache_bytes=cache, page_size=page, debug_counts=1) as ctx:
+    with gfs.Context(cache_bytes=cache, page_size=page, debug_counts=1, xfer=xfer, max_rpc_pages=16) as ctx:
         fid = ctx.open(path)
         out = ctx.scan(fid, MiB, blocks=blocks, threads=threads)
         torch_cuda.cuda.synchronize()
@@ -123,16 +130,18 @@ def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads):
         assert st["evictions"] >= npages - cache // page
 
 
+@pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("stride,read_len,page", [
     (MiB + 16, MiB + 16, 256 * KiB),     # stride not a page multiple
     (700 * KiB + 3, 300 * KiB + 5, 64 * KiB),  # odd offsets: unaligned copy path
     (64 * KiB, 64 * KiB, 2 * MiB),       # 32 blocks share one page
     (3 * MiB, 2 * MiB + 1, 1 * MiB),
 ])
-def test_ragged_strides_exact(torch_cuda, gfs, datadir, stride, read_len, page):
+def test_ragged_strides_exact(torch_cuda, gfs, datadir, stride, read_len, page, xfer):
     size = 40 * MiB + 999
     path = _file(datadir, 4, size)
-    with gfs.Context(cache_bytes=16 * MiB if page < 2 * MiB else 32 * MiB, page_size=page) as ctx:
+    with gfs.Context(cache_bytes=16 * MiB if page < 2 * MiB else 32 * MiB, page_size=page, xfer=xfer,
+                     max_rpc_pages=16) as ctx:
         fid = ctx.open(path)
         out = ctx.scan(fid, stride, read_len=read_len, blocks=32, threads=128)
         torch_cuda.cuda.synchronize()
@@ -140,8 +149,9 @@ def test_ragged_strides_exact(torch_cuda, gfs, datadir, stride, read_len, page):
 
 
 # ------------------------------------------------ independent greads
+@pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("mode,advice", [(0, 0), (1, 0), (0, 2)])
-def test_random_reads_exact(torch_cuda, gfs, datadir, mode, advice):
+def test_random_reads_exact(torch_cuda, gfs, datadir, mode, advice, xfer):
     torch = torch_cuda
     size = 12 * MiB + 77
     path = _file(datadir, 5, size)
@@ -154,7 +164,7 @@ def test_random_reads_exact(torch_cuda, gfs, datadir, mode, advice):
     for ln in lens:
         dsts.append(pos)
         pos += (ln + 255) // 256 * 256
-    with gfs.Context(cache_bytes=4 * MiB, page_size=64 * KiB, mode=mode) as ctx:
+    with gfs.Context(cache_bytes=4 * MiB, page_size=64 * KiB, mode=mode, xfer=xfer, max_rpc_pages=32) as ctx:
         fid = ctx.open(path)
         if advice:
             ctx.fadvise(fid, advice)
@@ -173,12 +183,13 @@ def test_random_reads_exact(torch_cuda, gfs, datadir, mode, advice):
         assert np.array_equal(buf[dsts[i]:dsts[i] + len(want)], want)
 
 
-def test_edge_cases(torch_cuda, gfs, datadir):
+@pytest.mark.parametrize("xfer", XFERS)
+def test_edge_cases(torch_cuda, gfs, datadir, xfer):
     torch = torch_cuda
     empty = os.path.join(datadir, "empty.bin")
     open(empty, "wb").close()
     small = _file(datadir, 6, 100)
-    with gfs.Context(cache_bytes=MiB, page_size=64 * KiB) as ctx:
+    with gfs.Context(cache_bytes=MiB, page_size=64 * KiB, xfer=xfer) as ctx:
         fe = ctx.open(empty)
         assert ctx.fstat(fe).size == 0
         cnt, sm, hs = ctx.scan_host(fe, 4096, blocks=4)
@@ -200,10 +211,11 @@ def test_edge_cases(torch_cuda, gfs, datadir):
             ctx.open(os.path.join(datadir, "does-not-exist"))
 
 
-def test_host_read_errors_surface_as_eio(torch_cuda, gfs, datadir):
+@pytest.mark.parametrize("xfer", XFERS)
+def test_host_read_errors_surface_as_eio(torch_cuda, gfs, datadir, xfer):
     size = 16 * MiB
     path = _file(datadir, 7, size)
-    with gfs.Context(cache_bytes=32 * MiB, page_size=256 * KiB, timeout_ns=5 * 10**9) as ctx:
+    with gfs.Context(cache_bytes=32 * MiB, page_size=256 * KiB, timeout_ns=5 * 10**9, xfer=xfer) as ctx:
         fid = ctx.open(path)
         ctx.set_faults(eio_every=5)
         cnt, sm, hs = ctx.scan_host(fid, MiB, blocks=8)
