@@ -99,7 +99,10 @@ typedef struct gfs_stats {
   uint64_t timeouts, eio, enomem;
   uint64_t host_requests, host_preads, host_bytes, host_copies, host_errors;
   uint64_t trace_rpc_count, trace_evict_count;
-  uint64_t reserved[8];
+  uint64_t host_ns_pread;     /* host I/O threads: time inside pread, summed over threads */
+  uint64_t host_ns_wait_buf;  /* time waiting for a staging buffer to be copied out (pull) */
+  uint64_t host_ns_idle;      /* time waiting for a request */
+  uint64_t reserved[5];
 } gfs_stats;
 
 /* One entry of the RPC trace: a request as the GPU issued it. */

@@ -423,36 +423,44 @@ __device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned lo
 struct PullJob {
   int f;                   // frame to fill, -1 = no job
   uint32_t s, i;           // slot and page index within the request
+  uint32_t buf, ok;        // staging buffer holding the page; page complete
   unsigned long long t;    // ticket of the request
-  long long res;           // host pread result
+  unsigned long long src;  // byte offset of the page in the staging arena
 };
 
 __device__ __forceinline__ RingSlot* ring_slot(const DevHandle& g, uint32_t s) {
   return (RingSlot*)(g.ring + (size_t)s * g.slot_stride);
 }
 
-// One thread: claim frame f if its request has been served.
+__device__ __forceinline__ void pull_read_page(const DevHandle& g, PullJob& j) {
+  const PullPage* pp = &g.pages[(size_t)j.s * g.max_rpc_pages + j.i];
+  j.src = ld_rlx64((const unsigned long long*)&pp->src);
+  j.buf = ld_rlx((const uint32_t*)&pp->buf);
+  j.ok = ld_rlx((const uint32_t*)&pp->ok);
+}
+
+// One thread: claim frame f if its page has been published.
 __device__ PullJob pull_claim_frame(const DevHandle& g, int f) {
-  PullJob j{-1, 0, 0, 0, 0};
+  PullJob j{-1, 0, 0, 0, 0, 0, 0};
   const uint32_t src = ld_acq(&g.fsrc[f]);
   if (src == SRC_NONE) return j;
   const uint32_t s = src / g.max_rpc_pages, i = src % g.max_rpc_pages;
   const unsigned long long t = ld_rlx64(&g.dticket[s]);
-  if (ld_acq_sys64(&g.done[s].done) != t + 1) return j;
+  if (ld_acq_sys64(&g.pages[(size_t)s * g.max_rpc_pages + i].tag) != t + 1) return j;
   if (atomicCAS(&g.fstate[f], (uint32_t)FR_FILLING, (uint32_t)FR_COPYING) != FR_FILLING) return j;
   j.f = f;
   j.s = s;
   j.i = i;
   j.t = t;
-  j.res = (long long)ld_rlx64((const unsigned long long*)&g.done[s].result);
+  pull_read_page(g, j);
   return j;
 }
 
-// One warp: find a served request with pages still FILLING and claim one page.
-// Scans 32 slots starting at `start`.
+// One warp: find a fully published request with pages still FILLING and claim
+// one page.  Scans 32 slots starting at `start`.
 __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
   const int lane = lane_id();
-  PullJob j{-1, 0, 0, 0, 0};
+  PullJob j{-1, 0, 0, 0, 0, 0, 0};
   const uint32_t s = (start + lane) % g.rpc_slots;
   bool cand = false;
   unsigned long long t = 0;
@@ -496,7 +504,7 @@ __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
         j.s = ss;
         j.i = (uint32_t)got;
         j.t = tt;
-        j.res = (long long)ld_rlx64((const unsigned long long*)&g.done[ss].result);
+        pull_read_page(g, j);
       }
     }
     if (got >= 0) break;
@@ -505,7 +513,8 @@ __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
 }
 
 // Copy n bytes of host staging into a frame with `nt` threads (rank `r`).
-// Staging is read with ld.global.cv: the slot is rewritten by the host every lap.
+// Staging is read through L2 (ld.global.cg), never L1: the host rewrites a
+// buffer every lap and only L2 is kept coherent with the host over C2C.
 __device__ __forceinline__ void copy_in(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n,
                                         uint32_t r, uint32_t nt) {
   const uint32_t n16 = n >> 4;
@@ -515,29 +524,30 @@ __device__ __forceinline__ void copy_in(const uint8_t* __restrict__ src, uint8_t
   for (; i + 7 * nt < n16; i += 8 * nt) {
     uint4 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldcv(s4 + i + u * nt);
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(s4 + i + u * nt);
 #pragma unroll
     for (int u = 0; u < 8; ++u) d4[i + u * nt] = v[u];
   }
-  for (; i < n16; i += nt) d4[i] = __ldcv(s4 + i);
-  for (uint32_t b = 16 * n16 + r; b < n; b += nt) dst[b] = __ldcv(src + b);
+  for (; i < n16; i += nt) d4[i] = __ldcg(s4 + i);
+  for (uint32_t b = 16 * n16 + r; b < n; b += nt) dst[b] = __ldcg(src + b);
 }
 
 // Copy a claimed page (all `nt` threads of the group), without the completion.
 __device__ __forceinline__ bool pull_copy(const DevHandle& g, const PullJob& j, uint32_t r, uint32_t nt) {
   const uint32_t valid = ld_rlx(&g.fvalid[j.f]);
-  const bool ok = j.res >= (long long)j.i * g.page_size + valid;
-  if (ok)
-    copy_in(g.staging + (size_t)j.s * g.slot_bytes + (size_t)j.i * g.page_size,
-            g.frames + ((size_t)j.f << g.page_shift), valid, r, nt);
+  const bool ok = j.ok != 0;
+  if (ok) copy_in(g.staging + j.src, g.frames + ((size_t)j.f << g.page_shift), valid, r, nt);
   __threadfence();
   return ok;
 }
 
-// One thread, after the group's copy: publish the page and free the slot after its last page.
+// One thread, after the group's copy: publish the page, give the staging buffer
+// back to its host thread, and free the slot after the request's last page.
 __device__ __forceinline__ void pull_finish(const DevHandle& g, const PullJob& j, bool ok) {
   st_rlx(&g.fsrc[j.f], SRC_NONE);
   st_rel(&g.fstate[j.f], ok ? (uint32_t)FR_READY : (uint32_t)FR_ERROR);
+  __threadfence_system();
+  atomicAdd_system(&g.bcount[j.buf], 0xffffffffu);  // -1: the host may reuse the buffer once 0
   const uint32_t c = atomicAdd(&g.dcopied[j.s], 1u) + 1;
   if (c == ld_rlx(&g.dnpages[j.s])) {
     __threadfence_system();
@@ -563,7 +573,7 @@ __device__ bool block_help(const DevHandle& g, int target, bool any) {
   __shared__ PullJob s_job;
   const uint32_t tid = threadIdx.x;
   if (tid < 32) {
-    PullJob j{-1, 0, 0, 0, 0};
+    PullJob j{-1, 0, 0, 0, 0, 0, 0};
     if (target >= 0 && tid == 0) j = pull_claim_frame(g, target);
     j.f = bcast(j.f);
     if (j.f < 0 && any) {

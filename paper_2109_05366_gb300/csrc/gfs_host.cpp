@@ -270,7 +270,7 @@ int gfs_shutdown(gfs_ctx* ctx) {
   if (ctx->dev.fetch_count) cudaFree(ctx->dev.fetch_count);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
   if (ctx->h_staging) cudaFreeHost(ctx->h_staging);
-  if (ctx->h_done) cudaFreeHost(ctx->h_done);
+  if (ctx->h_pullmeta) cudaFreeHost(ctx->h_pullmeta);
   delete ctx;
   return 0;
 }
@@ -286,8 +286,11 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   if (c.max_streams < 1 || c.timeout_ns == 0) return -EINVAL;
   const uint64_t F64 = c.cache_bytes / c.page_size;
   if (F64 > MAX_FRAMES) return -EINVAL;
-  const uint64_t slot_bytes = (uint64_t)c.max_rpc_pages * c.page_size;
-  if (c.xfer == GFS_XFER_PULL && slot_bytes * c.rpc_slots > (32ull << 30)) return -EINVAL;  // staging cap
+  // pull staging: per host thread, a ring of small buffers of whole pages
+  const uint64_t chunk_bytes = std::max<uint64_t>(c.page_size, 1ull << 20);
+  const uint32_t bufs_per_thread = (uint32_t)std::max<uint64_t>(2, c.staging_bytes / chunk_bytes);
+  const uint32_t nbufs = c.host_threads * bufs_per_thread;
+  if (c.xfer == GFS_XFER_PULL && (uint64_t)nbufs * chunk_bytes > (16ull << 30)) return -EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return -ENODEV;
   if (c.device < 0 || c.device >= ndev) return -EINVAL;
@@ -318,7 +321,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.slot_stride = slot_stride(c.max_rpc_pages);
   g.fifo_cap = F;
   g.xfer = c.xfer;
-  g.slot_bytes = slot_bytes;
+  g.nbufs = nbufs;
+  g.chunk_bytes = chunk_bytes;
 
   // device arena
   size_t off = 0;
@@ -375,21 +379,34 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.fsrc = (uint32_t*)(a + o_fsrc);
   g.staging = nullptr;
   g.done = nullptr;
+  g.pages = nullptr;
+  g.bcount = nullptr;
   if (c.xfer == GFS_XFER_PULL) {
-    rc = cuda_err(cudaHostAlloc((void**)&ctx->h_staging, slot_bytes * c.rpc_slots,
+    const size_t pages_bytes = sizeof(PullPage) * c.rpc_slots * c.max_rpc_pages;
+    const size_t meta_bytes = align_up(sizeof(PullDone) * c.rpc_slots, 256) + align_up(pages_bytes, 256) +
+                              align_up((size_t)nbufs * 4, 256);
+    rc = cuda_err(cudaHostAlloc((void**)&ctx->h_staging, (size_t)nbufs * chunk_bytes,
                                 cudaHostAllocMapped | cudaHostAllocPortable));
-    if (!rc) rc = cuda_err(cudaHostAlloc((void**)&ctx->h_done, sizeof(PullDone) * c.rpc_slots,
+    if (!rc) rc = cuda_err(cudaHostAlloc((void**)&ctx->h_pullmeta, meta_bytes,
                                          cudaHostAllocMapped | cudaHostAllocPortable));
     void* dp = nullptr;
+    void* dm = nullptr;
     if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&dp, ctx->h_staging, 0));
-    g.staging = (uint8_t*)dp;
-    if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&dp, ctx->h_done, 0));
-    g.done = (PullDone*)dp;
+    if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&dm, ctx->h_pullmeta, 0));
     if (rc) {
       gfs_shutdown(ctx);
       return rc;
     }
-    memset(ctx->h_done, 0, sizeof(PullDone) * c.rpc_slots);
+    memset(ctx->h_pullmeta, 0, meta_bytes);
+    const size_t o_pages = align_up(sizeof(PullDone) * c.rpc_slots, 256);
+    const size_t o_bcount = o_pages + align_up(pages_bytes, 256);
+    ctx->h_done = (PullDone*)ctx->h_pullmeta;
+    ctx->h_pages = (PullPage*)(ctx->h_pullmeta + o_pages);
+    ctx->h_bcount = (uint32_t*)(ctx->h_pullmeta + o_bcount);
+    g.staging = (uint8_t*)dp;
+    g.done = (PullDone*)dm;
+    g.pages = (PullPage*)((uint8_t*)dm + o_pages);
+    g.bcount = (uint32_t*)((uint8_t*)dm + o_bcount);
   }
 
   // request ring in mapped pinned memory
@@ -427,9 +444,13 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.threads = c.host_threads;
   sc.n_frames = F;
   if (c.xfer == GFS_XFER_PULL) {
-    sc.pull_staging = ctx->h_staging;
+    sc.pull_arena = ctx->h_staging;
     sc.pull_done = ctx->h_done;
-    sc.slot_bytes = slot_bytes;
+    sc.pull_pages = ctx->h_pages;
+    sc.pull_bcount = ctx->h_bcount;
+    sc.chunk_bytes = chunk_bytes;
+    sc.bufs_per_thread = bufs_per_thread;
+    sc.max_pages = c.max_rpc_pages;
   }
   const size_t stg = (size_t)sc.staging_pages * c.page_size;
   ctx->io = new IoService(
@@ -560,11 +581,7 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
     CK(cudaMemcpy(&freed, &ctx->dev.ctrl->freed.v, 8, cudaMemcpyDeviceToHost));
     if (freed < tail) return -ETIMEDOUT;
   }
-  ctx->io->stats.requests = 0;
-  ctx->io->stats.preads = 0;
-  ctx->io->stats.bytes = 0;
-  ctx->io->stats.copies = 0;
-  ctx->io->stats.errors = 0;
+  ctx->io->stats.clear();
   if (ctx->dev.fetch_count) CK(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, s));
   int rc = launch_reset(ctx->dev, s);
   if (rc) return rc;
@@ -603,6 +620,9 @@ int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
   o->host_errors = ctx->io->stats.errors.load();
   o->trace_rpc_count = tr[0];
   o->trace_evict_count = tr[1];
+  o->host_ns_pread = ctx->io->stats.ns_pread.load();
+  o->host_ns_wait_buf = ctx->io->stats.ns_wait_buf.load();
+  o->host_ns_idle = ctx->io->stats.ns_idle.load();
   return 0;
 }
 

@@ -51,8 +51,11 @@ struct gfs_ctx {
   uint8_t* d_frames = nullptr;
   size_t arena_bytes = 0;
   uint8_t* h_ring = nullptr;  // mapped pinned
-  uint8_t* h_staging = nullptr;  // GFS_XFER_PULL: per-slot staging, mapped pinned
-  gfs::PullDone* h_done = nullptr;  // GFS_XFER_PULL: completion records, mapped pinned
+  uint8_t* h_staging = nullptr;     // GFS_XFER_PULL: staging arena, mapped pinned
+  uint8_t* h_pullmeta = nullptr;    // GFS_XFER_PULL: completion records + page descriptors + buffer counts
+  gfs::PullDone* h_done = nullptr;
+  gfs::PullPage* h_pages = nullptr;
+  uint32_t* h_bcount = nullptr;
   std::vector<gfs::HostFile> files;
   gfs::IoService* io = nullptr;
   uint8_t* d_scan_buf = nullptr;  // per-block gread buffers of gfs_scan

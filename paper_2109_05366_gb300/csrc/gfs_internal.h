@@ -59,10 +59,22 @@ struct Ctrl {
 };
 
 // GFS_XFER_PULL completion record of a slot, in mapped pinned memory, written by
-// the host after its pread: result (bytes read or -errno), then done = ticket + 1.
+// the host once every page of the request is published: result (bytes read or
+// -errno), then done = ticket + 1.
 struct PullDone {
   unsigned long long done;
   long long result;
+};
+
+// GFS_XFER_PULL per-page descriptor (mapped pinned), written by the host after
+// the pread of the chunk holding the page: where the page sits in the staging
+// arena, whether it holds all its bytes, then tag = ticket + 1.
+struct PullPage {
+  unsigned long long tag;
+  unsigned long long src;  // byte offset in the staging arena
+  uint32_t buf;            // staging buffer (host thread * buffers per thread + k)
+  uint32_t ok;
+  uint32_t pad[2];
 };
 
 // Per-file device state.
@@ -134,9 +146,12 @@ struct DevHandle {
   // GFS_XFER_PULL: host staging per slot (device view), completion records, and
   // the device copy of each in-flight request
   uint32_t xfer;
-  unsigned long long slot_bytes;  // staging bytes per slot = max_rpc_pages * page_size
-  uint8_t* staging;               // rpc_slots * slot_bytes, mapped pinned
+  uint32_t nbufs;                 // staging buffers in the arena (host threads * buffers per thread)
+  unsigned long long chunk_bytes; // bytes per staging buffer (whole pages)
+  uint8_t* staging;               // staging arena (device view), nbufs * chunk_bytes, mapped pinned
   PullDone* done;                 // rpc_slots records, mapped pinned
+  PullPage* pages;                // rpc_slots * max_rpc_pages descriptors, mapped pinned
+  uint32_t* bcount;               // per staging buffer: pages not yet copied out (GPU decrements)
   unsigned long long* dticket;    // ticket of the request in each slot
   uint32_t* dnpages;              // pages of that request
   uint32_t* dcopied;              // pages copied out so far

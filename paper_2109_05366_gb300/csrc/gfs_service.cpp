@@ -8,9 +8,16 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 
 namespace gfs {
+
+static inline uint64_t mono_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 IoService::IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files)
     : cfg_(cfg), make_sink_(std::move(make_sink)), files_(std::move(files)) {}
@@ -66,6 +73,12 @@ ssize_t IoService::do_pread(int fd, uint8_t* buf, size_t n, uint64_t off) {
   if (delay) usleep(delay);
   if (eio && k % eio == eio - 1) return -EIO;
   if (sh && k % sh == sh - 1) n /= 2;
+  const uint64_t t0 = mono_ns();
+  struct Acc {
+    std::atomic<uint64_t>& a;
+    uint64_t t0;
+    ~Acc() { a.fetch_add(mono_ns() - t0, std::memory_order_relaxed); }
+  } acc{stats.ns_pread, t0};
   size_t got = 0;
   while (got < n) {
     ssize_t r = ::pread(fd, buf + got, n - got, (off_t)(off + got));
@@ -133,28 +146,61 @@ void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint
   }
 }
 
-void IoService::serve_pull(uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages) {
+void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
+                           uint32_t npages) {
   FileView fv{-1, 0};
   const bool have = files_(fid, &fv);
-  const uint64_t off = page_lo << cfg_.page_shift;
-  long long result = -EBADF;
-  if (have) {
-    result = 0;
-    if (off < fv.size) {
-      const size_t want = (size_t)std::min<uint64_t>((uint64_t)npages << cfg_.page_shift, fv.size - off);
-      const ssize_t got = do_pread(fv.fd, cfg_.pull_staging + (size_t)slot * cfg_.slot_bytes, want, off);
+  const uint64_t P = cfg_.page_size;
+  const uint64_t off0 = page_lo << cfg_.page_shift;
+  const uint32_t cpages = (uint32_t)(cfg_.chunk_bytes >> cfg_.page_shift);
+  long long total = have ? 0 : -EBADF;
+  for (uint32_t c0 = 0; c0 < npages; c0 += cpages) {
+    const uint32_t cn = std::min(cpages, npages - c0);
+    const uint32_t id = (uint32_t)idx * cfg_.bufs_per_thread + cur;
+    cur = (cur + 1) % cfg_.bufs_per_thread;
+    uint8_t* buf = cfg_.pull_arena + (size_t)id * cfg_.chunk_bytes;
+    uint64_t spins = 0;
+    if (__atomic_load_n(&cfg_.pull_bcount[id], __ATOMIC_ACQUIRE) != 0) {
+      const uint64_t w0 = mono_ns();
+      while (__atomic_load_n(&cfg_.pull_bcount[id], __ATOMIC_ACQUIRE) != 0) {  // GPU still copying out of it
+        if (stop_.load(std::memory_order_relaxed)) return;
+        if (++spins > 20000) {
+          struct timespec ts = {0, 2000};
+          nanosleep(&ts, nullptr);
+        }
+      }
+      stats.ns_wait_buf.fetch_add(mono_ns() - w0, std::memory_order_relaxed);
+    }
+    const uint64_t coff = off0 + (uint64_t)c0 * P;
+    size_t want = 0;
+    if (have && coff < fv.size) want = (size_t)std::min<uint64_t>((uint64_t)cn * P, fv.size - coff);
+    ssize_t got = 0;
+    if (want) {
+      got = do_pread(fv.fd, buf, want, coff);
       stats.preads.fetch_add(1, std::memory_order_relaxed);
       if (got < 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);
+        if (total >= 0) total = got;
+        got = 0;
       } else {
         stats.bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
+        if (total >= 0) total += got;
       }
-      result = got;
+    }
+    __atomic_store_n(&cfg_.pull_bcount[id], cn, __ATOMIC_RELAXED);  // published by the page tags below
+    for (uint32_t i = 0; i < cn; ++i) {
+      const uint64_t base = coff + (uint64_t)i * P;
+      const uint64_t expect = (have && base < fv.size) ? std::min<uint64_t>(P, fv.size - base) : 0;
+      PullPage* pp = cfg_.pull_pages + (size_t)slot * cfg_.max_pages + c0 + i;
+      pp->src = (uint64_t)id * cfg_.chunk_bytes + (uint64_t)i * P;
+      pp->buf = id;
+      pp->ok = (expect > 0 && (uint64_t)got >= (uint64_t)i * P + expect) ? 1u : 0u;
+      __atomic_store_n(&pp->tag, ticket + 1, __ATOMIC_RELEASE);  // the GPU may copy this page now
     }
   }
   PullDone* d = cfg_.pull_done + slot;
-  __atomic_store_n(&d->result, result, __ATOMIC_RELAXED);
-  __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);  // the GPU may copy now
+  __atomic_store_n(&d->result, total, __ATOMIC_RELAXED);
+  __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);
 }
 
 void IoService::run(int idx) {
@@ -162,11 +208,13 @@ void IoService::run(int idx) {
   sink->thread_init();
   prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);  // short sleeps while polling the ring
   int cur = 0;
+  uint32_t pull_cur = 0;
   uint32_t frames[MAX_RPC_PAGES];
   while (!stop_.load(std::memory_order_relaxed)) {
     const uint64_t h = head_.fetch_add(1, std::memory_order_relaxed);
     RingSlot* s = (RingSlot*)(cfg_.ring + (size_t)(h % cfg_.slots) * cfg_.slot_stride);
     uint64_t spins = 0;
+    const uint64_t i0 = mono_ns();
     while (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) {
       if (stop_.load(std::memory_order_relaxed)) return;
       ++spins;
@@ -175,21 +223,16 @@ void IoService::run(int idx) {
         nanosleep(&ts, nullptr);
       }
     }
+    stats.ns_idle.fetch_add(mono_ns() - i0, std::memory_order_relaxed);
     const volatile RingSlot* vs = s;
     const uint32_t fid = vs->fid;
     const uint32_t npages = vs->npages;
     const uint64_t page_lo = vs->page_lo;
     const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
     stats.requests.fetch_add(1, std::memory_order_relaxed);
-    if (cfg_.pull_staging) {  // the GPU frees the slot once it has copied the pages
-      if (npages == 0 || (uint64_t)npages << cfg_.page_shift > cfg_.slot_bytes) {
-        stats.errors.fetch_add(1, std::memory_order_relaxed);
-        PullDone* d = cfg_.pull_done + h % cfg_.slots;
-        __atomic_store_n(&d->result, (long long)-EINVAL, __ATOMIC_RELAXED);
-        __atomic_store_n(&d->done, h + 1, __ATOMIC_RELEASE);
-      } else {
-        serve_pull((uint32_t)(h % cfg_.slots), h, fid, page_lo, npages);
-      }
+    if (cfg_.pull_arena) {  // the GPU frees the slot once it has copied the pages
+      serve_pull(idx, pull_cur, (uint32_t)(h % cfg_.slots), h, fid, page_lo,
+                 std::min<uint32_t>(npages, cfg_.max_pages));
       served_.fetch_add(1, std::memory_order_release);
       continue;
     }

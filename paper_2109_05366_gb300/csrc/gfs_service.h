@@ -49,15 +49,26 @@ struct ServiceConfig {
   uint32_t staging_pages = 1;  // pages per staging buffer
   uint32_t threads = 1;
   uint32_t n_frames = 0xffffffffu;  // frame indices at or above this are rejected
-  // GFS_XFER_PULL: each slot preads into its own staging region and publishes a
-  // completion record; the GPU copies the pages and frees the slot.
-  uint8_t* pull_staging = nullptr;
+  // GFS_XFER_PULL: every thread preads through its own ring of small staging
+  // buffers (small enough to stay in the CPU caches), publishes per-page
+  // descriptors and a per-request completion record; the GPU copies the pages,
+  // releases the buffers and frees the slot.
+  uint8_t* pull_arena = nullptr;
   PullDone* pull_done = nullptr;
-  uint64_t slot_bytes = 0;
+  PullPage* pull_pages = nullptr;
+  uint32_t* pull_bcount = nullptr;
+  uint64_t chunk_bytes = 0;
+  uint32_t bufs_per_thread = 0;
+  uint32_t max_pages = 0;
 };
 
 struct ServiceStats {
   std::atomic<uint64_t> requests{0}, preads{0}, bytes{0}, copies{0}, errors{0};
+  std::atomic<uint64_t> ns_pread{0}, ns_wait_buf{0}, ns_idle{0};
+  void clear() {
+    requests = 0; preads = 0; bytes = 0; copies = 0; errors = 0;
+    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0;
+  }
 };
 
 class IoService {
@@ -79,7 +90,8 @@ class IoService {
  private:
   void run(int idx);
   void serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
-  void serve_pull(uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages);
+  void serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
+                  uint32_t npages);
   ssize_t do_pread(int fd, uint8_t* buf, size_t n, uint64_t off);
 
   ServiceConfig cfg_;

@@ -40,11 +40,11 @@ class Stat(ctypes.Structure):
 STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fetched", "bytes_fetched",
                 "ra_pages_sync", "ra_pages_async", "evictions", "unconsumed_evictions", "retries", "timeouts",
                 "eio", "enomem", "host_requests", "host_preads", "host_bytes", "host_copies", "host_errors",
-                "trace_rpc_count", "trace_evict_count"]
+                "trace_rpc_count", "trace_evict_count", "host_ns_pread", "host_ns_wait_buf", "host_ns_idle"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 8)]
+    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 5)]
 
 
 class RpcRec(ctypes.Structure):
