@@ -194,6 +194,28 @@ int gfs_scan(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d_count,
 int gfs_scan_host(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* h_count,
                   uint64_t* h_sum, uint64_t* h_hash, void* stream);
 
+/* Allocation-free variant of gfs_scan.  The paper has no counterpart: this is a
+ * service of this library.  Some callers cannot call cudaMalloc while they
+ * run: serving loops that must not stall other streams (cudaMalloc and cudaFree
+ * can synchronise the device), and code that owns all of a device's memory
+ * through its own allocator and budget.  gfs_scan may allocate its
+ * per-threadblock gread buffers on first use or growth; this call never
+ * allocates (no cudaMalloc, cudaFree or allocating library routine): the
+ * buffers live in a file-scope device array of GFS_STATIC_SCRATCH_BYTES that
+ * every device loading the library holds until the process exits.
+ *   - blocks * round_up(read_len, 256) must fit in GFS_STATIC_SCRATCH_BYTES,
+ *     else the call returns -ENOSPC and launches nothing.
+ *   - The first call on a device looks the array's device address up (once per
+ *     device, with that device made current); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array and leaves its contents behind; nothing
+ *     in it needs to start at zero.  Calls whose kernels overlap on the GPU
+ *     race on the array: serialise them (one stream, or events).
+ * Arguments, outputs and the other errors are those of gfs_scan. */
+#define GFS_STATIC_SCRATCH_BYTES (64ull << 20)
+int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d_count, uint64_t* d_sum,
+                    uint64_t* d_hash, void* stream);
+
 /* n independent greads: request i reads [d_off[i], d_off[i]+d_len[i]) into
  * d_buf + d_dst[i] and writes its return value to d_ret[i]; `blocks`
  * threadblocks take requests i = b, b+blocks, ...; gread stream id = block

@@ -2,6 +2,9 @@
 // shape: block b greads strides b, b+B, ... and checksums each), independent
 // greads, cache reset, and the checksum kernel of the CPU-I/O baseline.
 #include <cuda_runtime.h>
+#include <errno.h>
+
+#include <mutex>
 
 #include "gfs_device.cuh"
 #include "gfs_host.h"
@@ -269,3 +272,67 @@ int scan_max_resident_blocks(uint32_t threads, bool fused, int device, int* out)
 }
 
 }  // namespace gfs
+
+// ---------------------------------------------------------------- allocation-free scan
+// gfs_scan_static keeps the per-threadblock gread buffers in this file-scope
+// device array instead of memory the context allocates, so the call itself never
+// allocates.  Every device that loads the library holds the array until exit.
+namespace {
+
+constexpr size_t kStaticScratchBytes = 64ull << 20;  // GFS_STATIC_SCRATCH_BYTES in include/gfs.h
+static __device__ __align__(256) uint8_t g_scan_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (current).  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once per
+// device and cached.
+int static_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return -EINVAL;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scan_scratch);
+    if (e != cudaSuccess || !p) return e == cudaErrorNoDevice ? -ENODEV : -EINVAL;
+    g_scratch_addr[device] = p;
+  }
+  *out = g_scratch_addr[device];
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* a, int64_t* d_count, uint64_t* d_sum,
+                               uint64_t* d_hash, void* stream) {
+  if (!ctx || !a) return -EINVAL;
+  if (fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
+  if (a->stride == 0 || a->read_len == 0 || a->blocks == 0) return -EINVAL;
+  if (a->threads != 128 && a->threads != 256 && a->threads != 512) return -EINVAL;
+  const uint64_t size = ctx->files[fid].size;
+  const uint64_t nstrides = size ? (size + a->stride - 1) / a->stride : 0;
+  const uint64_t buf_stride = (a->read_len + 255) / 256 * 256;
+  if ((uint64_t)a->blocks * buf_stride > kStaticScratchBytes) return -ENOSPC;  // beyond the static array
+  if (nstrides == 0) return 0;
+  if (!d_count || !d_sum || !d_hash) return -EINVAL;
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
+  void* scratch = nullptr;
+  int rc = static_scratch(ctx->cfg.device, &scratch);
+  if (rc) return rc;
+  gfs::DevHandle g = ctx->dev;
+  const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
+                                      : (uint32_t)((uint64_t)a->blocks * pages_per_read + 1 > 0xffffffffull
+                                                       ? 0xffffffffull
+                                                       : (uint64_t)a->blocks * pages_per_read + 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (a->serialize) {
+    int maxb = 0;
+    rc = gfs::scan_max_resident_blocks(a->threads, a->fused != 0, ctx->cfg.device, &maxb);
+    if (rc) return rc;
+    if ((int)a->blocks > maxb) return -EINVAL;
+    if (cudaMemsetAsync(&g.ctrl->ticket.v, 0, 8, s) != cudaSuccess) return -EINVAL;
+  }
+  return gfs::launch_scan(g, fid, *a, nstrides, (uint8_t*)scratch, buf_stride, d_count, d_sum, d_hash, s);
+}

@@ -78,6 +78,7 @@ SIGNATURES = {
     "gfs_get_fetch_counts": (ctypes.c_int, [vp, vp, u64, vp]),
     "gfs_scan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_host": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
+    "gfs_scan_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_read_many": (ctypes.c_int, [vp, ctypes.c_int, u32, vp, vp, vp, vp, vp, u32, u32, vp]),
     "gfs_cpuio_scan": (ctypes.c_int, [ctypes.c_char_p, u64, u64, u32, u64, vp, vp, vp, vp, vp,
                                       ctypes.POINTER(ctypes.c_double)]),
