@@ -36,6 +36,8 @@ WORKLOADS = {
     # name: (file bytes, seed, page, cache, blocks, stride)
     "cfg2_8GiB_file_1GiB_cache": (8 * GiB, 2, 512 * KiB, 1 * GiB, 296, MiB),
     "cfg1_64MiB_file_128MiB_cache": (64 * MiB, 1, 256 * KiB, 128 * MiB, 64, MiB),
+    # same shape as the 8 GiB workload at a quarter of the size (profiling captures)
+    "cfg2s_2GiB_file_256MiB_cache": (2 * GiB, 2, 512 * KiB, 256 * MiB, 296, MiB),
 }
 DEFAULT_WORKLOAD = "cfg2_8GiB_file_1GiB_cache"
 METRIC = "sequential gread GB/s (readahead vs on-demand vs CPU-I/O) + % link roofline; p50/p99 latency"
@@ -334,7 +336,7 @@ def main():
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--host-threads", type=int, default=16)
     ap.add_argument("--ra-cap", type=int, default=8)
-    ap.add_argument("--rpc-slots", type=int, default=128)
+    ap.add_argument("--rpc-slots", type=int, default=512)
     ap.add_argument("--staging-mib", type=int, default=4)
     ap.add_argument("--fused", action="store_true")
     ap.add_argument("--xfer", choices=["pull", "dma"], default="pull")

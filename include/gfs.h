@@ -53,6 +53,10 @@ extern "C" {
 /* How a served request reaches the cache frames. */
 #define GFS_XFER_DMA 0  /* host: pread -> pinned staging -> cudaMemcpyAsync -> stream write of the frame state */
 #define GFS_XFER_PULL 1 /* host: pread -> pinned staging; GPU copies staging -> frames over the host link */
+#define GFS_XFER_MAPPED 2 /* the file's page cache is mapped for the GPU (shared mapping registered with
+                           * CUDA); the host serves a request by publishing where its pages are and the
+                           * GPU copies them into frames over the host link.  Files that cannot be mapped
+                           * read-write (permissions, file system) fall back to GFS_XFER_PULL. */
 
 /* Request kinds in the RPC trace. */
 #define GFS_KIND_DEMAND 0
@@ -88,7 +92,7 @@ typedef struct gfs_stat {
   uint32_t page_size; /* cache page size */
   uint32_t flags;     /* open flags */
   uint32_t advice;    /* current fadvise hint */
-  uint32_t reserved;
+  uint32_t mapped;    /* 1 if the file's page cache is mapped for the GPU (GFS_XFER_MAPPED) */
 } gfs_stat;
 
 /* Counters since the last gfs_reset_cache (device side and host side). */

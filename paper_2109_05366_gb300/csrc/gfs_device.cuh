@@ -536,7 +536,10 @@ __device__ __forceinline__ void copy_in(const uint8_t* __restrict__ src, uint8_t
 __device__ __forceinline__ bool pull_copy(const DevHandle& g, const PullJob& j, uint32_t r, uint32_t nt) {
   const uint32_t valid = ld_rlx(&g.fvalid[j.f]);
   const bool ok = j.ok != 0;
-  if (ok) copy_in(g.staging + j.src, g.frames + ((size_t)j.f << g.page_shift), valid, r, nt);
+  if (ok) {
+    const uint8_t* src = j.buf == BUF_MAPPED ? (const uint8_t*)j.src : g.staging + j.src;
+    copy_in(src, g.frames + ((size_t)j.f << g.page_shift), valid, r, nt);
+  }
   __threadfence();
   return ok;
 }
@@ -546,8 +549,10 @@ __device__ __forceinline__ bool pull_copy(const DevHandle& g, const PullJob& j, 
 __device__ __forceinline__ void pull_finish(const DevHandle& g, const PullJob& j, bool ok) {
   st_rlx(&g.fsrc[j.f], SRC_NONE);
   st_rel(&g.fstate[j.f], ok ? (uint32_t)FR_READY : (uint32_t)FR_ERROR);
-  __threadfence_system();
-  atomicAdd_system(&g.bcount[j.buf], 0xffffffffu);  // -1: the host may reuse the buffer once 0
+  if (j.buf != BUF_MAPPED) {
+    __threadfence_system();
+    atomicAdd_system(&g.bcount[j.buf], 0xffffffffu);  // -1: the host may reuse the buffer once 0
+  }
   const uint32_t c = atomicAdd(&g.dcopied[j.s], 1u) + 1;
   if (c == ld_rlx(&g.dnpages[j.s])) {
     __threadfence_system();
@@ -613,12 +618,12 @@ __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long p
       return -kETIMEDOUT;
     }
     // in pull mode slots are freed by GPU copies: help instead of idling
-    if (g.xfer == GFS_XFER_PULL && warp_help(g, si)) continue;
+    if (g.xfer != GFS_XFER_DMA && warp_help(g, si)) continue;
     if (lane == 0) __nanosleep(ns);
     __syncwarp();
     if (ns < 2048) ns <<= 1;
   }
-  if (g.xfer == GFS_XFER_PULL) {
+  if (g.xfer != GFS_XFER_DMA) {
     for (uint32_t i = lane; i < n; i += 32) g.dframes[(size_t)si * g.max_rpc_pages + i] = s_frames[i];
     if (lane == 0) {
       st_rlx64(&g.dticket[si], t);
@@ -689,7 +694,7 @@ __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi
         return -kENOMEM;
       }
       // pull mode: frames may all be waiting to be copied out of staging
-      if (!(g.xfer == GFS_XFER_PULL && warp_help(g, (uint32_t)(q % g.rpc_slots)))) {
+      if (!(g.xfer != GFS_XFER_DMA && warp_help(g, (uint32_t)(q % g.rpc_slots)))) {
         if (lane == 0) __nanosleep(256);
         __syncwarp();
       }
@@ -872,7 +877,7 @@ __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long long de
     const int st = s_st;
     __syncthreads();
     if (st != FR_FILLING && st != FR_COPYING) return st;
-    if (g.xfer == GFS_XFER_PULL) {
+    if (g.xfer != GFS_XFER_DMA) {
       // the page itself first; other served pages only now and then (their
       // completion records are read over the host link)
       if (block_help(g, st == FR_FILLING ? f : -1, (it & 7) == 7)) {

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <errno.h>
 #include <fcntl.h>
+#include <sys/mman.h>
 #include <sys/stat.h>
 #include <unistd.h>
 
@@ -192,7 +193,47 @@ bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
   if (!f.open) return false;
   out->fd = f.fd;
   out->size = f.size;
+  out->dev_map = f.dev_map;
   return true;
+}
+
+// GFS_XFER_MAPPED: map the file shared and register the mapping with CUDA so the
+// GPU can read its page-cache pages.  Registration of read-only mappings is not
+// available on every platform, so the mapping is read-write; nothing ever writes
+// through it.  Returns false (and leaves the file unmapped) when any step fails.
+bool map_file(HostFile& hf) {
+  if (hf.size == 0) return false;
+  int rw = open(hf.path.c_str(), O_RDWR | O_CLOEXEC);
+  if (rw < 0) return false;
+  const size_t len = (hf.size + 4095) & ~(size_t)4095;
+  void* m = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_SHARED, rw, 0);
+  close(rw);
+  if (m == MAP_FAILED) return false;
+  if (cudaHostRegister(m, len, cudaHostRegisterMapped) != cudaSuccess) {
+    cudaGetLastError();
+    munmap(m, len);
+    return false;
+  }
+  void* dp = nullptr;
+  if (cudaHostGetDevicePointer(&dp, m, 0) != cudaSuccess || !dp) {
+    cudaGetLastError();
+    cudaHostUnregister(m);
+    munmap(m, len);
+    return false;
+  }
+  hf.map = m;
+  hf.map_len = len;
+  hf.dev_map = (uint64_t)(uintptr_t)dp;
+  return true;
+}
+
+void unmap_file(HostFile& hf) {
+  if (!hf.map) return;
+  cudaHostUnregister(hf.map);
+  munmap(hf.map, hf.map_len);
+  hf.map = nullptr;
+  hf.map_len = 0;
+  hf.dev_map = 0;
 }
 
 int push_file(gfs_ctx* ctx, int fid) {
@@ -260,8 +301,10 @@ int gfs_shutdown(gfs_ctx* ctx) {
     ctx->io = nullptr;
   }
   cudaDeviceSynchronize();
-  for (auto& f : ctx->files)
+  for (auto& f : ctx->files) {
+    unmap_file(f);
     if (f.fd >= 0) close(f.fd);
+  }
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   if (ctx->d_frames) cudaFree(ctx->d_frames);
   if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
@@ -280,7 +323,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   const gfs_config c = *cfg_in;
   if (!is_pow2(c.page_size) || c.page_size < 4096 || c.page_size > (64u << 20)) return -EINVAL;
   if (c.cache_bytes < c.page_size) return -EINVAL;
-  if (c.mode > GFS_MODE_ONDEMAND || c.xfer > GFS_XFER_PULL) return -EINVAL;
+  if (c.mode > GFS_MODE_ONDEMAND || c.xfer > GFS_XFER_MAPPED) return -EINVAL;
   if (c.rpc_slots < 1 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
   if (c.host_threads < 1 || c.host_threads > 256 || c.max_files < 1 || c.max_files > MAX_FILES) return -EINVAL;
   if (c.max_streams < 1 || c.timeout_ns == 0) return -EINVAL;
@@ -290,7 +333,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   const uint64_t chunk_bytes = std::max<uint64_t>(c.page_size, 1ull << 20);
   const uint32_t bufs_per_thread = (uint32_t)std::max<uint64_t>(2, c.staging_bytes / chunk_bytes);
   const uint32_t nbufs = c.host_threads * bufs_per_thread;
-  if (c.xfer == GFS_XFER_PULL && (uint64_t)nbufs * chunk_bytes > (16ull << 30)) return -EINVAL;
+  if (c.xfer != GFS_XFER_DMA && (uint64_t)nbufs * chunk_bytes > (16ull << 30)) return -EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return -ENODEV;
   if (c.device < 0 || c.device >= ndev) return -EINVAL;
@@ -381,7 +424,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.done = nullptr;
   g.pages = nullptr;
   g.bcount = nullptr;
-  if (c.xfer == GFS_XFER_PULL) {
+  if (c.xfer != GFS_XFER_DMA) {
     const size_t pages_bytes = sizeof(PullPage) * c.rpc_slots * c.max_rpc_pages;
     const size_t meta_bytes = align_up(sizeof(PullDone) * c.rpc_slots, 256) + align_up(pages_bytes, 256) +
                               align_up((size_t)nbufs * 4, 256);
@@ -443,7 +486,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.staging_pages = std::max<uint32_t>(1, c.staging_bytes / c.page_size);
   sc.threads = c.host_threads;
   sc.n_frames = F;
-  if (c.xfer == GFS_XFER_PULL) {
+  if (c.xfer != GFS_XFER_DMA) {
     sc.pull_arena = ctx->h_staging;
     sc.pull_done = ctx->h_done;
     sc.pull_pages = ctx->h_pages;
@@ -456,7 +499,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   ctx->io = new IoService(
       sc,
       [ctx, stg](int) -> Sink* {
-        if (ctx->cfg.xfer == GFS_XFER_PULL) return new (std::nothrow) HostSink(nullptr, nullptr, 0, 0);
+        if (ctx->cfg.xfer != GFS_XFER_DMA) return new (std::nothrow) HostSink(nullptr, nullptr, 0, 0);
         DmaSink* s = new (std::nothrow) DmaSink(ctx->cfg.device, ctx->d_frames, ctx->dev.fstate, ctx->dev.page_shift, stg);
         if (s && s->init() != 0) {
           delete s;
@@ -507,6 +550,7 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
   hf.open = true;
   hf.path = path;
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->cfg.xfer == GFS_XFER_MAPPED) map_file(hf);  // falls back to pread staging when it fails
   if (slot == 0 && ctx->cfg.debug_counts) {
     const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
     if (ctx->dev.fetch_count) cudaFree(ctx->dev.fetch_count);
@@ -520,6 +564,7 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
   }
   int rc = push_file(ctx, slot);
   if (rc) {
+    unmap_file(hf);
     close(fd);
     hf = HostFile();
     return rc;
@@ -535,6 +580,8 @@ int gfs_close(gfs_ctx* ctx, int fid) {
   hf.open = false;
   CK(cudaSetDevice(ctx->cfg.device));
   int rc = push_file(ctx, fid);
+  if (hf.map) cudaDeviceSynchronize();  // no kernel may still read the mapping
+  unmap_file(hf);
   close(hf.fd);
   hf = HostFile();
   return rc;
@@ -557,6 +604,7 @@ int gfs_fstat(gfs_ctx* ctx, int fid, gfs_stat* st) {
   st->page_size = ctx->cfg.page_size;
   st->flags = (uint32_t)ctx->files[fid].flags;
   st->advice = (uint32_t)ctx->files[fid].advice;
+  st->mapped = ctx->files[fid].map ? 1u : 0u;
   return 0;
 }
 
@@ -573,7 +621,7 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
     usleep(50);
   }
   ctx->io->drain_sinks();
-  if (ctx->cfg.xfer == GFS_XFER_PULL) {  // copy out what was served but never read
+  if (ctx->cfg.xfer != GFS_XFER_DMA) {  // copy out what was served but never read
     int rc = launch_drain(ctx->dev, s);
     if (rc) return rc;
     CK(cudaStreamSynchronize(s));

@@ -22,6 +22,9 @@ namespace gfs {
 struct HostFile {
   int fd = -1;
   uint64_t size = 0;
+  void* map = nullptr;     // GFS_XFER_MAPPED: shared mapping registered with CUDA
+  size_t map_len = 0;
+  uint64_t dev_map = 0;    // its device address
   int flags = 0;
   int advice = GFS_ADV_NORMAL;
   bool open = false;

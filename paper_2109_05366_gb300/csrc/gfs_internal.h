@@ -23,6 +23,7 @@ namespace gfs {
 // COPYING = (GFS_XFER_PULL) a threadblock is copying the page out of host staging.
 enum : uint32_t { FR_EMPTY = 0, FR_FILLING = 1, FR_READY = 2, FR_ERROR = 3, FR_RECLAIM = 4, FR_COPYING = 5 };
 constexpr uint32_t SRC_NONE = 0xffffffffu;
+constexpr uint32_t BUF_MAPPED = 0xffffffffu;  // PullPage.buf: src is a device address in a mapped file
 
 constexpr uint64_t KEY_NONE = ~0ull;
 constexpr uint64_t ENTRY_EMPTY = ~0ull;
@@ -71,8 +72,8 @@ struct PullDone {
 // arena, whether it holds all its bytes, then tag = ticket + 1.
 struct PullPage {
   unsigned long long tag;
-  unsigned long long src;  // byte offset in the staging arena
-  uint32_t buf;            // staging buffer (host thread * buffers per thread + k)
+  unsigned long long src;  // byte offset in the staging arena, or (buf == BUF_MAPPED) a device address
+  uint32_t buf;            // staging buffer (host thread * buffers per thread + k), or BUF_MAPPED
   uint32_t ok;
   uint32_t pad[2];
 };

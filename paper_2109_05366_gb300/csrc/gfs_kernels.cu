@@ -70,7 +70,7 @@ __device__ void block_quiesce(const DevHandle& g) {
     const int late = s_late;
     __syncthreads();
     if (!any_busy || late) break;
-    if (g.xfer == GFS_XFER_PULL && dev::block_help(g, -1, true)) continue;
+    if (g.xfer != GFS_XFER_DMA && dev::block_help(g, -1, true)) continue;
     if (threadIdx.x == 0) __nanosleep(256);
   }
   __syncthreads();
@@ -79,7 +79,7 @@ __device__ void block_quiesce(const DevHandle& g) {
 // Pull mode, before a block exits: copy out served requests nobody waits for
 // (asynchronous readahead at the end of a scan) so their ring slots free up.
 __device__ void block_help_drain(const DevHandle& g) {
-  if (g.xfer != GFS_XFER_PULL) return;
+  if (g.xfer == GFS_XFER_DMA) return;
   for (int i = 0; i < 4096; ++i)
     if (!dev::block_help(g, -1, true)) break;
 }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_
 
 // GFS_XFER_PULL: copy out every request in flight (cache reset, end of use).
 __global__ void __launch_bounds__(512) k_drain(DevHandle g) {
-  if (g.xfer != GFS_XFER_PULL) return;
+  if (g.xfer == GFS_XFER_DMA) return;
   __shared__ int s_more;
   const unsigned long long dl = dev::now_ns() + g.timeout_ns;
   for (;;) {

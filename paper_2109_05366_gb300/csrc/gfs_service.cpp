@@ -93,7 +93,7 @@ ssize_t IoService::do_pread(int fd, uint8_t* buf, size_t n, uint64_t off) {
 }
 
 void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames) {
-  FileView fv{-1, 0};
+  FileView fv{-1, 0, 0};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
   const uint64_t off0 = page_lo << cfg_.page_shift;
@@ -148,12 +148,36 @@ void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint
 
 void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
                            uint32_t npages) {
-  FileView fv{-1, 0};
+  FileView fv{-1, 0, 0};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
   const uint64_t off0 = page_lo << cfg_.page_shift;
   const uint32_t cpages = (uint32_t)(cfg_.chunk_bytes >> cfg_.page_shift);
   long long total = have ? 0 : -EBADF;
+  if (have && fv.dev_map) {  // mapped file: the pages are already in host memory the GPU can read
+    // injected host read errors apply here too (the request fails as a whole)
+    const uint64_t k = pread_count_.fetch_add(1, std::memory_order_relaxed);
+    const uint32_t eio = eio_every_.load(std::memory_order_relaxed);
+    const bool fail = eio && k % eio == eio - 1;
+    if (fail) {
+      stats.errors.fetch_add(1, std::memory_order_relaxed);
+      total = -EIO;
+    }
+    for (uint32_t i = 0; i < npages; ++i) {
+      const uint64_t base = off0 + (uint64_t)i * P;
+      PullPage* pp = cfg_.pull_pages + (size_t)slot * cfg_.max_pages + i;
+      pp->src = fv.dev_map + base;
+      pp->buf = BUF_MAPPED;
+      pp->ok = (!fail && base < fv.size) ? 1u : 0u;
+      if (!fail && base < fv.size) total += (long long)std::min<uint64_t>(P, fv.size - base);
+      __atomic_store_n(&pp->tag, ticket + 1, __ATOMIC_RELEASE);
+    }
+    if (total > 0) stats.bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
+    PullDone* d = cfg_.pull_done + slot;
+    __atomic_store_n(&d->result, total, __ATOMIC_RELAXED);
+    __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);
+    return;
+  }
   for (uint32_t c0 = 0; c0 < npages; c0 += cpages) {
     const uint32_t cn = std::min(cpages, npages - c0);
     const uint32_t id = (uint32_t)idx * cfg_.bufs_per_thread + cur;

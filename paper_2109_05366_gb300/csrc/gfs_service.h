@@ -40,6 +40,7 @@ class Sink {
 struct FileView {
   int fd;
   uint64_t size;
+  uint64_t dev_map;  // device address of the file's registered mapping, 0 if not mapped
 };
 
 struct ServiceConfig {

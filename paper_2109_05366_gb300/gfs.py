@@ -18,7 +18,7 @@ from . import build as _build
 RDONLY, RDWR = 0, 2
 MODE_READAHEAD, MODE_ONDEMAND = 0, 1
 ADV_NORMAL, ADV_SEQUENTIAL, ADV_RANDOM = 0, 1, 2
-XFER_DMA, XFER_PULL = 0, 1
+XFER_DMA, XFER_PULL, XFER_MAPPED = 0, 1, 2
 KIND_DEMAND, KIND_SYNC_RA, KIND_ASYNC_RA = 0, 1, 2
 
 u32, u64, i32, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
 
 
 class Stat(ctypes.Structure):
-    _fields_ = [("size", u64), ("page_size", u32), ("flags", u32), ("advice", u32), ("reserved", u32)]
+    _fields_ = [("size", u64), ("page_size", u32), ("flags", u32), ("advice", u32), ("mapped", u32)]
 
 
 STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fetched", "bytes_fetched",

@@ -14,7 +14,15 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def datadir(tmp_path_factory):
-    return str(tmp_path_factory.mktemp("gfs_data"))
+    # tmpfs when there is one: its files can be mapped for the GPU (GFS_XFER_MAPPED)
+    if os.path.isdir("/dev/shm") and os.access("/dev/shm", os.W_OK):
+        import shutil
+        import tempfile
+        d = tempfile.mkdtemp(prefix="gfs_tests_", dir="/dev/shm")
+        yield d
+        shutil.rmtree(d, ignore_errors=True)
+    else:
+        yield str(tmp_path_factory.mktemp("gfs_data"))
 
 
 def pytest_runtest_setup(item):

@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(tmp_path):
     import ctypes
     import subprocess
     checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "reserved"]),
-              ("gfs_stat", gfs.Stat, ["size", "advice"]),
+              ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
               ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
               ("gfs_evict_rec", gfs.EvictRec, ["new_fid", "new_page"]),

@@ -48,7 +48,7 @@ def _check_scan(gfs, path, stride, cnt, sm, hs, read_len=None):
 
 
 # ------------------------------------------------ config 1: 64 MiB, fits the cache
-XFERS = [0, 1]  # GFS_XFER_DMA, GFS_XFER_PULL
+XFERS = [0, 1, 2]  # GFS_XFER_DMA, GFS_XFER_PULL, GFS_XFER_MAPPED
 
 
 @pytest.mark.parametrize("xfer", XFERS)
@@ -232,3 +232,22 @@ def test_host_read_errors_surface_as_eio(torch_cuda, gfs, datadir, xfer):
         ctx.reset_cache()
         cnt, sm, hs = ctx.scan_host(fid, MiB, blocks=8)
         assert cnt.tolist() == c and sm.tolist() == s and hs.tolist() == h
+
+
+def test_mapped_file_is_mapped_and_exact(torch_cuda, gfs, datadir):
+    """GFS_XFER_MAPPED on a tmpfs file: the GPU reads the page cache directly."""
+    if not datadir.startswith("/dev/shm"):
+        pytest.skip("no tmpfs for a mappable file")
+    size = 96 * MiB + 333
+    path = _file(datadir, 8, size)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=512 * KiB, xfer=2, max_rpc_pages=16, debug_counts=1) as ctx:
+        fid = ctx.open(path)
+        assert ctx.fstat(fid).mapped == 1
+        for _ in range(2):
+            out = ctx.scan(fid, MiB, blocks=48, threads=256)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            assert st["host_preads"] == 0 and st["timeouts"] == 0
+            ctx.reset_cache()
+        ctx.close(fid)
