@@ -227,7 +227,7 @@ def run_gfs(args):
 
     cfg = dict(cache_bytes=cache, page_size=page, host_threads=args.host_threads, ra_cap_pages=args.ra_cap,
                rpc_slots=args.rpc_slots, staging_bytes=args.staging_mib * MiB, max_rpc_pages=args.max_rpc_pages,
-               xfer=gfs.XFER_PULL if args.xfer == "pull" else gfs.XFER_DMA)
+               xfer={"pull": gfs.XFER_PULL, "dma": gfs.XFER_DMA, "mapped": gfs.XFER_MAPPED}[args.xfer])
     with gfs.Context(mode=gfs.MODE_READAHEAD, **cfg) as ctx:
         fid = ctx.open(path)
         # correctness of the timed configuration on sampled strides (full check in tests)
@@ -272,11 +272,20 @@ def run_gfs(args):
         h2d = gfs.probe_h2d(GiB, 16 * MiB, 3)
         h2d_page = gfs.probe_h2d(GiB, page, 3)
         prd = gfs.probe_pread(path, 16, 4 * MiB, 2)
+        pull = gfs.probe_pull(GiB, 3)
         extra["link_probe"] = {"h2d_pinned_16MiB_gbps": round(h2d, 1), "h2d_pinned_page_gbps": round(h2d_page, 1),
-                               "pread_16thr_gbps": round(prd, 1)}
-        binding = min(h2d, prd)
+                               "pread_16thr_gbps": round(prd, 1), "gpu_read_host_gbps": round(pull, 1)}
+        # the link the chosen transfer moves data over: mapped = GPU reads of host
+        # memory; pull = host pread + GPU reads; dma = host pread + copy engine
+        if args.xfer == "mapped":
+            binding, binding_src = pull, "GPU threads reading mapped host memory"
+        elif args.xfer == "pull":
+            binding, binding_src = min(pull, prd), "min(GPU reads of host memory, 16-thread pread)"
+        else:
+            binding, binding_src = min(h2d, prd), "min(pinned H2D copy, 16-thread pread)"
+
     else:
-        binding = None
+        binding, binding_src = None, None
 
     if rank != 0:
         if world > 1:
@@ -307,7 +316,7 @@ def run_gfs(args):
     if binding:
         line["roofline"] = {"bound": "link", "achieved": round(value / world, 2), "peak": round(binding, 1),
                             "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": None,
-                            "peak_source": "measured in this run: min(pinned H2D copy, 16-thread pread)"}
+                            "peak_source": "measured in this run: " + binding_src}
         hbm = peaks.get("hbm_gbs", 6800.0)
         line["hbm_roofline"] = {"bound": "hbm", "achieved": round(nbytes_hbm / kt / 1e9, 1), "peak": hbm,
                                 "unit": "GB/s", "frac": round(nbytes_hbm / kt / 1e9 / hbm, 4),
@@ -339,7 +348,7 @@ def main():
     ap.add_argument("--rpc-slots", type=int, default=512)
     ap.add_argument("--staging-mib", type=int, default=4)
     ap.add_argument("--fused", action="store_true")
-    ap.add_argument("--xfer", choices=["pull", "dma"], default="pull")
+    ap.add_argument("--xfer", choices=["mapped", "pull", "dma"], default="mapped")
     ap.add_argument("--max-rpc-pages", type=int, default=16)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -241,6 +241,9 @@ int gfs_cpuio_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_
  * `chunk`-byte copies over `bytes`, and multi-thread pread GB/s of a file. */
 int gfs_probe_h2d(uint64_t bytes, uint64_t chunk, int reps, double* gbps);
 int gfs_probe_pread(const char* path, uint32_t threads, uint64_t chunk, int reps, double* gbps);
+/* GB/s of GPU threads copying `bytes` of mapped pinned host memory into device
+ * memory (the link GFS_XFER_MAPPED and GFS_XFER_PULL move data over). */
+int gfs_probe_pull(uint64_t bytes, int reps, double* gbps);
 
 /* Self-test of the request ring and the host I/O service without a GPU: a host
  * thread plays the device client (same slot protocol), the service preads the

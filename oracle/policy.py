@@ -55,6 +55,9 @@ Rules (R1-R7) as implemented below:
   size); the window and the demand run are cut to it.
   R7 readahead is enabled only for read-only opens without the RANDOM hint;
      otherwise R1 applies.
+  R8 data read sequentially is used once (Section 5.1): a readahead window is
+     also cut at the first page already fetched since the last cache reset
+     (it was read and evicted, or is being read); demand misses always fetch.
 A demand page that finds no victim at all (every frame belongs to the current
 gread) makes the gread return -ENOMEM; later pages of a demand run just end the
 request early.
@@ -148,6 +151,7 @@ class PageCacheSim:
         self.rpc_log: list[tuple] = []     # (fid, page_lo, npages, kind)
         self.evict_log: list[tuple] = []   # (frame, old_key, new_key)
         self.stats = Stats()
+        self.fetched: set[tuple] = set()     # pages fetched since the last reset (R8)
         self._busy: set[int] = set()        # frames of the request being built
         self._pinned: int | None = None      # frame of the page being delivered
 
@@ -169,6 +173,7 @@ class PageCacheSim:
         self.fifo.clear()
         self.alloc_counter = 0
         self.last_end.clear()
+        self.fetched.clear()
 
     def present(self, fid: int, page: int) -> bool:
         return (fid, page) in self.table
@@ -253,6 +258,8 @@ class PageCacheSim:
         for q in range(p, p + want):
             if q >= fi.npages or (fid, q) in self.table:
                 break
+            if q - p >= demand and (fid, q) in self.fetched:      # R8
+                break
             try:
                 f = self._take(q - p >= demand, gread_seq0, (fid, q))
             except NoFrame:
@@ -262,6 +269,7 @@ class PageCacheSim:
             if f is None:
                 break
             self._install(f, (fid, q))
+            self.fetched.add((fid, q))
             taken.append(f)
         return taken
 
@@ -296,7 +304,7 @@ class PageCacheSim:
 
     # ---- R4: a readahead mark ---------------------------------------------------
     def _async(self, fi: FileInfo, fid: int, end: int, t: int, gread_seq0: int):
-        if end >= fi.npages or (fid, end) in self.table:
+        if end >= fi.npages or (fid, end) in self.table or (fid, end) in self.fetched:
             return
         taken = self._request(fi, fid, end, min(self.Wmax, 2 * t), 0, gread_seq0)
         if not taken:

@@ -685,6 +685,8 @@ __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi
     const unsigned long long key = make_key(fid, q);
     if (i > 0 && tab_lookup(g, key) >= 0) break;
     const bool is_ra = i >= demand;
+    // R8: readahead does not fetch a page again once fetched (sequential data is used once)
+    if (is_ra && fi.fetched && (ld_rlx(&fi.fetched[q >> 5]) >> (q & 31)) & 1u) break;
     int f = take_frame(g, is_ra, seq0, key, deadline);
     while (f < 0 && !is_ra && i == 0) {  // the first demand page waits for a victim
       int late = 0;
@@ -724,6 +726,7 @@ __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi
     }
     if (lane == 0) {
       s_frames[n] = (uint32_t)f;
+      if (fi.fetched) atomicOr(&fi.fetched[q >> 5], 1u << (q & 31));
       if (g.fetch_count && fid == 0 && q < g.debug_pages) atomicAdd(&g.fetch_count[q], 1u);
     }
     __syncwarp();
@@ -756,6 +759,7 @@ __device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& f
 __device__ void async_readahead(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long end, uint32_t t,
                                 unsigned long long seq0, unsigned long long deadline, uint32_t* s_frames) {
   if (end >= fi.npages) return;
+  if (fi.fetched && (ld_rlx(&fi.fetched[end >> 5]) >> (end & 31)) & 1u) return;  // R8
   if (tab_lookup(g, make_key(fid, end)) >= 0) return;
   uint32_t want = 2 * t < g.ra_cap ? 2 * t : g.ra_cap;
   if (want == 0) return;

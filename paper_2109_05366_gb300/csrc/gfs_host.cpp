@@ -243,6 +243,7 @@ int push_file(gfs_ctx* ctx, int fid) {
   fd.npages = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
   fd.open = hf.open ? 1u : 0u;
   fd.ra = (hf.open && (hf.flags & 3) == GFS_RDONLY && hf.advice != GFS_ADV_RANDOM) ? 1u : 0u;
+  fd.fetched = hf.open ? hf.d_fetched : nullptr;
   CK(cudaMemcpy(ctx->dev.files + fid, &fd, sizeof(fd), cudaMemcpyHostToDevice));
   return 0;
 }
@@ -303,6 +304,7 @@ int gfs_shutdown(gfs_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& f : ctx->files) {
     unmap_file(f);
+    if (f.d_fetched) cudaFree(f.d_fetched);
     if (f.fd >= 0) close(f.fd);
   }
   if (ctx->d_arena) cudaFree(ctx->d_arena);
@@ -551,6 +553,20 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
   hf.path = path;
   CK(cudaSetDevice(ctx->cfg.device));
   if (ctx->cfg.xfer == GFS_XFER_MAPPED) map_file(hf);  // falls back to pread staging when it fails
+  {
+    const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+    hf.fetched_bytes = (size_t)((np + 31) / 32) * 4;
+    if (hf.fetched_bytes) {
+      if (cudaMalloc((void**)&hf.d_fetched, hf.fetched_bytes) != cudaSuccess ||
+          cudaMemset(hf.d_fetched, 0, hf.fetched_bytes) != cudaSuccess) {
+        if (hf.d_fetched) cudaFree(hf.d_fetched);
+        unmap_file(hf);
+        close(fd);
+        hf = HostFile();
+        return -ENOMEM;
+      }
+    }
+  }
   if (slot == 0 && ctx->cfg.debug_counts) {
     const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
     if (ctx->dev.fetch_count) cudaFree(ctx->dev.fetch_count);
@@ -564,6 +580,7 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
   }
   int rc = push_file(ctx, slot);
   if (rc) {
+    if (hf.d_fetched) cudaFree(hf.d_fetched);
     unmap_file(hf);
     close(fd);
     hf = HostFile();
@@ -580,8 +597,9 @@ int gfs_close(gfs_ctx* ctx, int fid) {
   hf.open = false;
   CK(cudaSetDevice(ctx->cfg.device));
   int rc = push_file(ctx, fid);
-  if (hf.map) cudaDeviceSynchronize();  // no kernel may still read the mapping
+  cudaDeviceSynchronize();  // no kernel may still read the mapping or the fetched bits
   unmap_file(hf);
+  if (hf.d_fetched) cudaFree(hf.d_fetched);
   close(hf.fd);
   hf = HostFile();
   return rc;
@@ -631,6 +649,8 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
   }
   ctx->io->stats.clear();
   if (ctx->dev.fetch_count) CK(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, s));
+  for (auto& f : ctx->files)
+    if (f.open && f.d_fetched) CK(cudaMemsetAsync(f.d_fetched, 0, f.fetched_bytes, s));
   int rc = launch_reset(ctx->dev, s);
   if (rc) return rc;
   return cuda_err(cudaStreamSynchronize(s));
@@ -906,6 +926,43 @@ int gfs_probe_h2d(uint64_t bytes, uint64_t chunk, int reps, double* gbps) {
       if (r > 0 && bw > best) best = bw;  // r == 0 is a warm-up
     }
   }
+  if (s) cudaStreamDestroy(s);
+  if (d) cudaFree(d);
+  if (h) cudaFreeHost(h);
+  *gbps = best;
+  return rc;
+}
+
+int gfs_probe_pull(uint64_t bytes, int reps, double* gbps) {
+  if (!gbps || bytes < 16 || reps < 1) return -EINVAL;
+  bytes &= ~(uint64_t)15;
+  uint8_t* h = nullptr;
+  uint8_t* dh = nullptr;
+  uint8_t* d = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_err(cudaHostAlloc((void**)&h, bytes, cudaHostAllocMapped));
+  if (!rc) rc = cuda_err(cudaHostGetDevicePointer((void**)&dh, h, 0));
+  if (!rc) rc = cuda_err(cudaMalloc((void**)&d, bytes));
+  if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  if (!rc) rc = cuda_err(cudaEventCreate(&e0));
+  if (!rc) rc = cuda_err(cudaEventCreate(&e1));
+  double best = 0;
+  if (!rc) {
+    memset(h, 1, bytes);
+    for (int r = 0; r <= reps && !rc; ++r) {
+      cudaEventRecord(e0, s);
+      rc = launch_pull_probe(dh, d, bytes, s);
+      cudaEventRecord(e1, s);
+      if (!rc) rc = cuda_err(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double bw = bytes / (ms * 1e-3) / 1e9;
+      if (r > 0 && bw > best) best = bw;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   if (s) cudaStreamDestroy(s);
   if (d) cudaFree(d);
   if (h) cudaFreeHost(h);

@@ -25,6 +25,8 @@ struct HostFile {
   void* map = nullptr;     // GFS_XFER_MAPPED: shared mapping registered with CUDA
   size_t map_len = 0;
   uint64_t dev_map = 0;    // its device address
+  uint32_t* d_fetched = nullptr;  // per-page fetched bits (device)
+  size_t fetched_bytes = 0;
   int flags = 0;
   int advice = GFS_ADV_NORMAL;
   bool open = false;
@@ -44,6 +46,7 @@ int launch_read_many(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_
 int launch_checksum(const uint8_t* d_file, uint64_t size, uint64_t stride, uint64_t read_len, int64_t* d_count,
                     uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
 int scan_max_resident_blocks(uint32_t threads, bool fused, int device, int* out);
+int launch_pull_probe(const uint8_t* src, uint8_t* dst, uint64_t n, cudaStream_t s);
 
 }  // namespace gfs
 

@@ -84,7 +84,7 @@ struct FileDev {
   unsigned long long npages;
   uint32_t open;     // 1 if the fid is open
   uint32_t ra;       // readahead enabled (read-only, not ADV_RANDOM)
-  uint32_t pad[2];
+  uint32_t* fetched; // one bit per page: fetched since the last reset (readahead skips those)
 };
 
 // One request-ring slot in mapped pinned memory (64-byte header + frame list).

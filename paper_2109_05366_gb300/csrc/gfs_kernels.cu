@@ -213,6 +213,14 @@ __global__ void __launch_bounds__(512) k_checksum(const uint8_t* file, unsigned 
   }
 }
 
+// Link probe: GPU threads copy mapped host memory into device memory.
+__global__ void __launch_bounds__(512) k_pull_probe(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                   unsigned long long n16) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dst[i] = __ldcg(src + i);
+}
+
 static int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return 0;
   if (e == cudaErrorMemoryAllocation) return -12;
@@ -257,6 +265,11 @@ int launch_checksum(const uint8_t* d_file, uint64_t size, uint64_t stride, uint6
   unsigned grid = ns < 152ull * 8 ? (unsigned)ns : 152u * 8;
   k_checksum<<<grid, 512, 0, s>>>(d_file, size, stride, read_len, ns, (long long*)d_count,
                                    (unsigned long long*)d_sum, (unsigned long long*)d_hash);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_pull_probe(const uint8_t* src, uint8_t* dst, uint64_t n, cudaStream_t s) {
+  k_pull_probe<<<304, 512, 0, s>>>((const uint4*)src, (uint4*)dst, n / 16);
   return cuda_err(cudaGetLastError());
 }
 

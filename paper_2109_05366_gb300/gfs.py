@@ -84,6 +84,7 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_h2d": (ctypes.c_int, [u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pread": (ctypes.c_int, [ctypes.c_char_p, u32, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gfs_probe_pull": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u64, ctypes.POINTER(u64)]),
     "gfs_abi_version": (ctypes.c_int, []),
     "gfs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -283,6 +284,12 @@ def cpuio_scan(path: str, stride: int, read_len: int | None, threads: int, chunk
 def probe_h2d(nbytes: int, chunk: int, reps: int = 3) -> float:
     g = ctypes.c_double(0.0)
     _check(load().gfs_probe_h2d(nbytes, chunk, reps, ctypes.byref(g)), "gfs_probe_h2d")
+    return g.value
+
+
+def probe_pull(nbytes: int, reps: int = 3) -> float:
+    g = ctypes.c_double(0.0)
+    _check(load().gfs_probe_pull(nbytes, reps, ctypes.byref(g)), "gfs_probe_pull")
     return g.value
 
 

@@ -399,3 +399,38 @@ def test_eviction_never_takes_unconsumed_while_fifo_nonempty(tmp_path):
     for stream, fid, off, ln in _random_trace(rng, size, 400, 3, 3 * P):
         sim.gread(stream, fid, off, ln)
     sim.close_all()
+
+
+def _streaming_trace(rng, npages, streams, steps):
+    """Interleaved sequential readers that start at different places and skip ahead."""
+    pos = [rng.randrange(npages) for _ in range(streams)]
+    out = []
+    for _ in range(steps):
+        s = rng.randrange(streams)
+        if rng.random() < 0.05:
+            pos[s] = rng.randrange(npages)
+        out.append((s, 0, pos[s] * P, P))
+        pos[s] = (pos[s] + 1) % npages
+    return out
+
+
+def test_readahead_never_refetches(tmp_path):
+    # R8 (Section 5.1: data read sequentially is used once): asynchronous
+    # readahead only requests pages not fetched since the last reset
+    size = 64 * P
+    path = _file(tmp_path, "r8", 9, size)
+    rng = random.Random(8)
+    sim = policy.PageCacheSim(P, 8, ra_cap=8, reserve=1)
+    sim.open(0, path)
+    for t in _streaming_trace(rng, 64, 3, 600):
+        sim.gread(*t)
+    seen = set()
+    asyncs = 0
+    for fid, lo, n, kind in sim.rpc_log:
+        pages = {(fid, q) for q in range(lo, lo + n)}
+        if kind == policy.ASYNC_RA:
+            asyncs += 1
+            assert not (pages & seen), "asynchronous readahead refetched a page"
+        seen |= pages
+    assert asyncs > 0 and sim.stats.evictions > 0
+    sim.close_all()
