@@ -84,7 +84,8 @@ typedef struct gfs_config {
   uint32_t xfer;           /* GFS_XFER_* */
   uint32_t debug_counts;   /* 1: keep per-page fetch counts for file id 0 */
   int32_t device;          /* CUDA device ordinal */
-  uint32_t reserved[7];
+  uint32_t latency_capacity; /* greads whose latency (globaltimer ns, entry to exit) is kept; 0 = off */
+  uint32_t reserved[6];
 } gfs_config;
 
 typedef struct gfs_stat {
@@ -178,6 +179,11 @@ int gfs_get_stats(gfs_ctx* ctx, gfs_stats* out, void* stream);
 int gfs_get_trace(gfs_ctx* ctx, gfs_rpc_rec* h_rpc, gfs_evict_rec* h_evict, uint32_t cap,
                   uint64_t* n_rpc, uint64_t* n_evict, void* stream);
 
+/* Latencies (ns) of the greads recorded since the last reset (latency_capacity
+ * > 0): copies min(cap, recorded) values to h_ns; *n receives the number of
+ * greads that finished (may exceed the capacity). */
+int gfs_get_latencies(gfs_ctx* ctx, uint64_t* h_ns, uint64_t cap, uint64_t* n, void* stream);
+
 /* Per-page fetch counts of file id 0 (debug_counts=1); copies min(cap, pages). */
 int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* stream);
 
@@ -227,6 +233,45 @@ int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d
 int gfs_read_many(gfs_ctx* ctx, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
                   const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks,
                   uint32_t threads, void* stream);
+
+/* ---------------------------------------------------------------- serving
+ * A persistent kernel runs many sequential-scan requests at once through the
+ * shared page cache (continuous batching).  Requests wait in a submission ring
+ * and are admitted in arrival order while their frame reservation
+ * (min(units, units_in_flight) * pages per unit) fits the frame budget; CTAs
+ * take units of the admitted requests round-robin, so requests that arrive
+ * while others run share the GPU with them.  Each request reports the byte sum
+ * and position hash of its range (the stride-scan checksums), the bytes read
+ * and device timestamps.  The paper has no serving loop: this extends its
+ * read path (Sections 2.2, 4, 5) to many concurrent readers. */
+typedef struct gfs_serve_config {
+  uint32_t ctas;            /* persistent CTAs; all must be resident at once */
+  uint32_t threads;         /* 128, 256 or 512 */
+  uint64_t unit_bytes;      /* bytes per unit of work (one gread) */
+  uint32_t max_requests;    /* requests active at once */
+  uint32_t queue_slots;     /* submission and completion ring slots */
+  uint32_t units_in_flight; /* per-request reservation in units (0 = 16) */
+  uint32_t frame_budget;    /* frames admission may reserve (0 = cache frames - ctas * pages per unit) */
+  uint32_t idle_exit_ms;    /* the kernel ends after this long with no work (0 = 60 s) */
+  uint32_t reserved[5];
+} gfs_serve_config;
+
+typedef struct gfs_completion {
+  uint64_t tag;        /* the caller's tag */
+  int64_t status;      /* 0, or the first -errno of a unit */
+  uint64_t sum, hash;  /* sum of bytes, sum of byte * (offset + 1), mod 2^64, over the range */
+  uint64_t bytes;      /* bytes read */
+  uint64_t t_admit_ns, t_done_ns; /* %globaltimer at admission and completion */
+} gfs_completion;
+
+/* Launch the serving kernel on `stream` (asynchronous).  -EBUSY if one runs. */
+int gfs_serve_start(gfs_ctx* ctx, const gfs_serve_config* cfg, void* stream);
+/* Queue a scan of [off, off+len) of fid; -EAGAIN when the submission ring is full. */
+int gfs_submit_scan(gfs_ctx* ctx, int fid, uint64_t off, uint64_t len, uint64_t tag);
+/* Copy up to `max` completions (in completion order); returns how many. */
+int gfs_poll(gfs_ctx* ctx, gfs_completion* out, int max);
+/* Ask the kernel to finish once every submitted request is done, wait, free. */
+int gfs_serve_stop(gfs_ctx* ctx);
 
 /* CPU-I/O baseline (Section 6.2 comparison): `threads` host threads pread the
  * file in `chunk` pieces into pinned buffers and cudaMemcpyAsync them into

@@ -19,8 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgfs.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gfs_kernels.cu", "gfs_host.cpp", "gfs_service.cpp"]
-HEADERS = ["gfs_internal.h", "gfs_device.cuh", "gfs_host.h", "gfs_service.h"]
+SOURCES = ["gfs_kernels.cu", "gfs_serve.cu", "gfs_host.cpp", "gfs_service.cpp"]
+HEADERS = ["gfs_internal.h", "gfs_device.cuh", "gfs_host.h", "gfs_service.h", "gfs_serve.h"]
 
 
 def _nvcc() -> str:

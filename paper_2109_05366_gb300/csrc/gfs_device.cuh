@@ -114,7 +114,7 @@ __device__ __forceinline__ uint32_t expected_valid(const DevHandle& g, const Fil
 
 // ---------------------------------------------------------------- page table
 // Warp-cooperative lookup: each lane reads one slot of the bucket (256 B).
-__device__ int tab_lookup(const DevHandle& g, unsigned long long key) {
+static __device__ int tab_lookup(const DevHandle& g, unsigned long long key) {
   const int lane = lane_id();
   uint32_t b = bucket_of(key, g.nbuckets);
   for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {
@@ -133,7 +133,7 @@ __device__ int tab_lookup(const DevHandle& g, unsigned long long key) {
   return -1;
 }
 
-__device__ bool bucket_lock(const DevHandle& g, uint32_t b, unsigned long long deadline) {
+static __device__ bool bucket_lock(const DevHandle& g, uint32_t b, unsigned long long deadline) {
   // lane 0 only
   while (atomicCAS(&g.tlock[b], 0u, 1u) != 0u) {
     if (now_ns() > deadline) return false;
@@ -142,14 +142,14 @@ __device__ bool bucket_lock(const DevHandle& g, uint32_t b, unsigned long long d
   __threadfence();
   return true;
 }
-__device__ void bucket_unlock(const DevHandle& g, uint32_t b) {
+static __device__ void bucket_unlock(const DevHandle& g, uint32_t b) {
   __threadfence();
   atomicExch(&g.tlock[b], 0u);
 }
 
 // Map key -> f unless key is already mapped.  Returns the frame now mapped for
 // the key (f if this call inserted it), -ETIMEDOUT, or -ENOMEM (table full).
-__device__ int tab_insert(const DevHandle& g, unsigned long long key, uint32_t f, unsigned long long deadline) {
+static __device__ int tab_insert(const DevHandle& g, unsigned long long key, uint32_t f, unsigned long long deadline) {
   const int lane = lane_id();
   const uint32_t home = bucket_of(key, g.nbuckets);
   int ok = 0;
@@ -197,7 +197,7 @@ __device__ int tab_insert(const DevHandle& g, unsigned long long key, uint32_t f
 }
 
 // Remove the mapping key -> f if present.
-__device__ void tab_remove(const DevHandle& g, unsigned long long key, uint32_t f, unsigned long long deadline) {
+static __device__ void tab_remove(const DevHandle& g, unsigned long long key, uint32_t f, unsigned long long deadline) {
   const int lane = lane_id();
   const uint32_t home = bucket_of(key, g.nbuckets);
   int ok = 0;
@@ -224,7 +224,7 @@ __device__ void tab_remove(const DevHandle& g, unsigned long long key, uint32_t 
 
 // ---------------------------------------------------------------- consumed FIFO
 // Bounded MPMC queue (Vyukov) over fifo_cap cells; each frame is in it at most once.
-__device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
+static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
   unsigned long long t = atomicAdd(&g.ctrl->fifo_tail.v, 1ull);
   unsigned long long* c = &g.fifo[t % g.fifo_cap];
   while ((ld_acq64(c) >> FRAME_BITS) != t) {
@@ -236,7 +236,7 @@ __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long dea
 }
 
 // Returns a frame, -1 when empty, -ETIMEDOUT.
-__device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
+static __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
   for (;;) {
     unsigned long long h = ld_acq64(&g.ctrl->fifo_head.v);
     unsigned long long t = ld_acq64(&g.ctrl->fifo_tail.v);
@@ -255,7 +255,7 @@ __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // o
 
 // ---------------------------------------------------------------- frames
 // Pin frame f for key.  Returns its state, or -1 if the mapping went stale.
-__device__ int frame_pin(const DevHandle& g, int f, unsigned long long key) {  // one thread
+static __device__ int frame_pin(const DevHandle& g, int f, unsigned long long key) {  // one thread
   atomicAdd(&g.fpins[f], 1u);
   __threadfence();
   uint32_t st = ld_acq(&g.fstate[f]);
@@ -266,7 +266,7 @@ __device__ int frame_pin(const DevHandle& g, int f, unsigned long long key) {  /
   return (int)st;
 }
 
-__device__ void frame_unpin(const DevHandle& g, int f) {  // one thread
+static __device__ void frame_unpin(const DevHandle& g, int f) {  // one thread
   __threadfence();
   atomicSub(&g.fpins[f], 1u);
 }
@@ -274,7 +274,7 @@ __device__ void frame_unpin(const DevHandle& g, int f) {  // one thread
 // Claim frame f for eviction.  from_fifo: only a still-consumed READY frame or a
 // returned (EMPTY, keyless) frame qualifies.  Returns 1 claimed, 0 pinned (try
 // later), -1 not a victim (stale entry).
-__device__ int frame_claim(const DevHandle& g, int f, bool from_fifo) {  // one thread
+static __device__ int frame_claim(const DevHandle& g, int f, bool from_fifo) {  // one thread
   uint32_t st = ld_acq(&g.fstate[f]);
   if (from_fifo) {
     if (st == FR_READY) {
@@ -295,7 +295,7 @@ __device__ int frame_claim(const DevHandle& g, int f, bool from_fifo) {  // one 
 }
 
 // Unmap a claimed frame's old page and record the eviction.
-__device__ void evict_key(const DevHandle& g, int f, unsigned long long new_key, unsigned long long deadline) {
+static __device__ void evict_key(const DevHandle& g, int f, unsigned long long new_key, unsigned long long deadline) {
   const int lane = lane_id();
   unsigned long long old = 0;
   uint32_t consumed = 0, valid = 0;
@@ -329,7 +329,7 @@ __device__ void evict_key(const DevHandle& g, int f, unsigned long long new_key,
 }
 
 // Readahead may only use free / consumed frames above the reserve (victim classes 1, 2).
-__device__ bool ra_allowed(const DevHandle& g) {  // one thread
+static __device__ bool ra_allowed(const DevHandle& g) {  // one thread
   unsigned long long used = ld_rlx64(&g.ctrl->next_unused.v);
   unsigned long long never = used >= g.n_frames ? 0 : g.n_frames - used;
   unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
@@ -340,7 +340,7 @@ __device__ bool ra_allowed(const DevHandle& g) {  // one thread
 // Victim selection (Section 5.1 restated; classes 1-3).  Returns a frame owned
 // by the caller with its old mapping removed, -1 if none (readahead), or a
 // negative errno.
-__device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long long seq0, unsigned long long new_key,
+static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long long seq0, unsigned long long new_key,
                           unsigned long long deadline) {
   const int lane = lane_id();
   int r = 0;
@@ -407,7 +407,7 @@ __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long long se
 }
 
 // Give a frame that lost an insert race back as a keyless FIFO entry.
-__device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned long long deadline) {  // one thread
+static __device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned long long deadline) {  // one thread
   if (pinned) atomicSub(&g.fpins[f], 1u);
   st_rlx64(&g.fkey[f], KEY_NONE);
   st_rel(&g.fstate[f], FR_EMPTY);
@@ -440,7 +440,7 @@ __device__ __forceinline__ void pull_read_page(const DevHandle& g, PullJob& j) {
 }
 
 // One thread: claim frame f if its page has been published.
-__device__ PullJob pull_claim_frame(const DevHandle& g, int f) {
+static __device__ PullJob pull_claim_frame(const DevHandle& g, int f) {
   PullJob j{-1, 0, 0, 0, 0, 0, 0};
   const uint32_t src = ld_acq(&g.fsrc[f]);
   if (src == SRC_NONE) return j;
@@ -458,7 +458,7 @@ __device__ PullJob pull_claim_frame(const DevHandle& g, int f) {
 
 // One warp: find a fully published request with pages still FILLING and claim
 // one page.  Scans 32 slots starting at `start`.
-__device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
+static __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
   const int lane = lane_id();
   PullJob j{-1, 0, 0, 0, 0, 0, 0};
   const uint32_t s = (start + lane) % g.rpc_slots;
@@ -562,7 +562,7 @@ __device__ __forceinline__ void pull_finish(const DevHandle& g, const PullJob& j
 }
 
 // One warp: help with one served page.  Returns true if it copied one.
-__device__ bool warp_help(const DevHandle& g, uint32_t start) {
+static __device__ bool warp_help(const DevHandle& g, uint32_t start) {
   PullJob j = pull_claim_any(g, start);
   if (j.f < 0) return false;
   bool ok = pull_copy(g, j, (uint32_t)lane_id(), 32);
@@ -574,7 +574,7 @@ __device__ bool warp_help(const DevHandle& g, uint32_t start) {
 
 // Whole block: copy frame f if served (target >= 0), else help with any served
 // page.  Returns true if the block copied a page.  Block-uniform.
-__device__ bool block_help(const DevHandle& g, int target, bool any) {
+static __device__ bool block_help(const DevHandle& g, int target, bool any) {
   __shared__ PullJob s_job;
   const uint32_t tid = threadIdx.x;
   if (tid < 32) {
@@ -598,7 +598,7 @@ __device__ bool block_help(const DevHandle& g, int target, bool any) {
 }
 
 // ---------------------------------------------------------------- request ring
-__device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
+static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
                           const uint32_t* s_frames, unsigned long long deadline) {
   const int lane = lane_id();
   unsigned long long t = 0;
@@ -673,7 +673,7 @@ __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long p
 // when no readahead victim is allowed.  Frames go to s_frames; the first is
 // pinned when pin_first.  Returns the page count, -EAGAIN when page p was
 // inserted by someone else meanwhile, or a negative errno.
-__device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t want,
+static __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t want,
                              uint32_t demand, bool pin_first, unsigned long long seq0, unsigned long long deadline,
                              uint32_t* s_frames) {
   const int lane = lane_id();
@@ -736,7 +736,7 @@ __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi
 }
 
 // Finish a request: record windows and the readahead mark, send it, count it.
-__device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t n,
+static __device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t n,
                               uint32_t demand, uint32_t window, uint32_t kind, unsigned long long mark_end,
                               int mark_idx, const uint32_t* s_frames, unsigned long long deadline) {
   const int lane = lane_id();
@@ -756,7 +756,7 @@ __device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& f
 }
 
 // R4: asynchronous readahead of [end, end + min(Wmax, 2T)) from a readahead mark.
-__device__ void async_readahead(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long end, uint32_t t,
+static __device__ void async_readahead(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long end, uint32_t t,
                                 unsigned long long seq0, unsigned long long deadline, uint32_t* s_frames) {
   if (end >= fi.npages) return;
   if (fi.fetched && (ld_rlx(&fi.fetched[end >> 5]) >> (end & 31)) & 1u) return;  // R8
@@ -771,7 +771,7 @@ __device__ void async_readahead(const DevHandle& g, uint32_t fid, const FileDev&
 
 // R1-R3: a miss on page p (p1 = last page of the gread).  Returns the pinned,
 // FILLING frame of page p, -EAGAIN to look p up again, or a negative errno.
-__device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
+static __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
                            unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
                            uint32_t* s_frames) {
   const int lane = lane_id();
@@ -822,7 +822,7 @@ __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, const F
 
 // Find or install page p and pin its frame for the caller (warp 0); does not
 // wait.  Returns the frame (its state in *state) or -errno.
-__device__ int acquire_begin(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
+static __device__ int acquire_begin(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
                              unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
                              uint32_t* s_frames, int* state) {
   const int lane = lane_id();
@@ -865,7 +865,7 @@ __device__ int acquire_begin(const DevHandle& g, int stream, uint32_t fid, const
 // Whole block: wait until pinned frame f leaves FILLING / COPYING (in pull mode
 // copying it, or other served pages, meanwhile).  Returns the state or
 // -ETIMEDOUT.  Block-uniform.
-__device__ int block_wait_ready(const DevHandle& g, int f, unsigned long long deadline) {
+static __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long long deadline) {
   __shared__ int s_st;
   unsigned ns = 64;
   for (uint32_t it = 0;; ++it) {
@@ -896,7 +896,7 @@ __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long long de
 
 // R4 for a READY page just acquired: the first reader of a marked page issues
 // the asynchronous window (warp 0).
-__device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDev& fi, int f, unsigned long long seq0,
+static __device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDev& fi, int f, unsigned long long seq0,
                            unsigned long long deadline, uint32_t* s_frames) {
   const int lane = lane_id();
   if (!(g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra)) return;
@@ -911,7 +911,7 @@ __device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDev& fi, 
 }
 
 // R5: account the delivered bytes, unpin, and queue the frame once fully consumed.
-__device__ void release_page(const DevHandle& g, int f, uint32_t nbytes, unsigned long long deadline) {  // one thread
+static __device__ void release_page(const DevHandle& g, int f, uint32_t nbytes, unsigned long long deadline) {  // one thread
   uint32_t c = atomicAdd(&g.fconsumed[f], nbytes);
   uint32_t v = ld_rlx(&g.fvalid[f]);
   bool push = c < v && c + nbytes >= v;
@@ -998,6 +998,30 @@ __device__ __forceinline__ void copy_out(const uint8_t* __restrict__ src, uint8_
   }
 }
 
+// Block-wide sum of two u64 values (mod 2^64); the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(unsigned long long& a, unsigned long long& b) {
+  __shared__ unsigned long long ra[32], rb[32];
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    b += __shfl_xor_sync(kFull, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) {
+    ra[w] = a;
+    rb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < nw ? ra[l] : 0ull;
+    b = l < nw ? rb[l] : 0ull;
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- gread
 // Threadblock-collective read of [off, off + len) of file `fid` into buf.
 // Every thread of the block must call it with the same arguments.  `stream`
@@ -1060,6 +1084,10 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
   }
   if (tid == 0 && stream >= 0 && (uint32_t)stream < g.max_streams)
     st_rlx64(&g.last_end[(size_t)stream * g.max_files + fid], p1 + 2);  // end page + 1
+  if (tid == 0 && g.lat_cap) {
+    const unsigned long long i = atomicAdd(&g.ctrl->lat_n.v, 1ull);
+    if (i < g.lat_cap) g.lat[i] = now_ns() - (deadline - g.timeout_ns);
+  }
   __syncthreads();
   return err ? err : (long long)(end - off);
 }

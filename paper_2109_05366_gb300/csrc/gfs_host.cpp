@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 
+#include "gfs_serve.h"
 #include "gfs_service.h"
 
 using namespace gfs;
@@ -296,6 +297,7 @@ int gfs_config_default(gfs_config* c) {
 int gfs_shutdown(gfs_ctx* ctx) {
   if (!ctx) return 0;
   cudaSetDevice(ctx->cfg.device);
+  if (ctx->server) gfs_serve_stop(ctx);
   if (ctx->io) {
     ctx->io->stop();
     delete ctx->io;
@@ -387,7 +389,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
                o_tev = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_evict_rec)),
                o_dtick = take((size_t)c.rpc_slots * 8), o_dnp = take((size_t)c.rpc_slots * 4),
                o_dcop = take((size_t)c.rpc_slots * 4), o_dfr = take((size_t)c.rpc_slots * c.max_rpc_pages * 4),
-               o_fsrc = take((size_t)F * 4);
+               o_fsrc = take((size_t)F * 4), o_lat = take((size_t)std::max<uint32_t>(1, c.latency_capacity) * 8);
   ctx->arena_bytes = off;
   rc = cuda_err(cudaMalloc(&ctx->d_arena, off));
   if (!rc) rc = cuda_err(cudaMemset(ctx->d_arena, 0, off));
@@ -422,6 +424,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.dcopied = (uint32_t*)(a + o_dcop);
   g.dframes = (uint32_t*)(a + o_dfr);
   g.fsrc = (uint32_t*)(a + o_fsrc);
+  g.lat = (unsigned long long*)(a + o_lat);
+  g.lat_cap = c.latency_capacity;
   g.staging = nullptr;
   g.done = nullptr;
   g.pages = nullptr;
@@ -708,6 +712,18 @@ int gfs_get_trace(gfs_ctx* ctx, gfs_rpc_rec* h_rpc, gfs_evict_rec* h_evict, uint
   if (h_evict && ke) CK(cudaMemcpy(h_evict, ctx->dev.trace_evict, ke * sizeof(gfs_evict_rec), cudaMemcpyDeviceToHost));
   if (n_rpc) *n_rpc = nr;
   if (n_evict) *n_evict = ne;
+  return 0;
+}
+
+int gfs_get_latencies(gfs_ctx* ctx, uint64_t* h_ns, uint64_t cap, uint64_t* n, void* stream) {
+  if (!ctx) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned long long k = 0;
+  CK(cudaMemcpy(&k, &ctx->dev.ctrl->lat_n.v, 8, cudaMemcpyDeviceToHost));
+  const uint64_t c = std::min<uint64_t>({k, cap, (uint64_t)ctx->dev.lat_cap});
+  if (h_ns && c) CK(cudaMemcpy(h_ns, ctx->dev.lat, c * 8, cudaMemcpyDeviceToHost));
+  if (n) *n = k;
   return 0;
 }
 

@@ -50,7 +50,10 @@ int launch_pull_probe(const uint8_t* src, uint8_t* dst, uint64_t n, cudaStream_t
 
 }  // namespace gfs
 
+struct gfs_server;
+
 struct gfs_ctx {
+  gfs_server* server = nullptr;  // running serving kernel, if any
   gfs_config cfg{};
   gfs::DevHandle dev{};
   void* d_arena = nullptr;

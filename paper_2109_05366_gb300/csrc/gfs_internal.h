@@ -56,6 +56,7 @@ struct Ctrl {
   Line trace_rpc_n;
   Line trace_evict_n;
   Line freed;          // GFS_XFER_PULL: requests whose pages have all been copied out of staging
+  Line lat_n;          // greads whose latency was recorded
   unsigned long long stat[ST_COUNT];
 };
 
@@ -158,6 +159,9 @@ struct DevHandle {
   uint32_t* dcopied;              // pages copied out so far
   uint32_t* dframes;              // rpc_slots * max_rpc_pages frame indices
   uint32_t* fsrc;                 // per frame: slot * max_rpc_pages + page index, SRC_NONE when not in flight
+  // gread latency trace (ns), lat_cap entries
+  unsigned long long* lat;
+  uint32_t lat_cap;
 };
 
 }  // namespace gfs

@@ -13,30 +13,6 @@ namespace gfs {
 
 using dev::Sums;
 
-// Block-wide sum of two u64 values; result valid in thread 0.
-__device__ __forceinline__ void block_reduce2(unsigned long long& a, unsigned long long& b) {
-  __shared__ unsigned long long ra[32], rb[32];
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(dev::kFull, a, o);
-    b += __shfl_xor_sync(dev::kFull, b, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (l == 0) {
-    ra[w] = a;
-    rb[w] = b;
-  }
-  __syncthreads();
-  if (w == 0) {
-    a = l < nw ? ra[l] : 0ull;
-    b = l < nw ? rb[l] : 0ull;
-    for (int o = 16; o; o >>= 1) {
-      a += __shfl_xor_sync(dev::kFull, a, o);
-      b += __shfl_xor_sync(dev::kFull, b, o);
-    }
-  }
-}
-
 // Checksums of n bytes at p (file offset `off` of p[0]); p is 16-byte aligned.
 __device__ __forceinline__ void checksum_range(const uint8_t* __restrict__ p, unsigned long long n,
                                                unsigned long long off, Sums& acc) {
@@ -113,7 +89,7 @@ __global__ void __launch_bounds__(512) k_scan(DevHandle g, int fid, unsigned lon
       if (tid == 0) dev::st_rel64(&g.ctrl->ticket.v, s + 1);
     }
     if (!FUSED && r > 0) checksum_range(buf, (unsigned long long)r, off, acc);
-    block_reduce2(acc.sum, acc.hash);
+    dev::block_sum2(acc.sum, acc.hash);
     if (tid == 0) {
       cnt[s] = r;
       sum[s] = r > 0 ? acc.sum : 0ull;
@@ -183,6 +159,7 @@ __global__ void k_reset(DevHandle g) {
     g.ctrl->ticket.v = 0;
     g.ctrl->trace_rpc_n.v = 0;
     g.ctrl->trace_evict_n.v = 0;
+    g.ctrl->lat_n.v = 0;
     for (int i = 0; i < ST_COUNT; ++i) g.ctrl->stat[i] = 0;
     // ring_tail and freed keep counting across resets (requests still map to slots)
     // ring_tail is left alone: the ring keeps its position across resets
@@ -203,7 +180,7 @@ __global__ void __launch_bounds__(512) k_checksum(const uint8_t* file, unsigned 
     } else {
       for (unsigned long long j = threadIdx.x; j < n; j += blockDim.x) dev::sums_add1(acc, file[off + j], off + j);
     }
-    block_reduce2(acc.sum, acc.hash);
+    dev::block_sum2(acc.sum, acc.hash);
     if (threadIdx.x == 0) {
       cnt[s] = (long long)n;
       sum[s] = acc.sum;

@@ -30,7 +30,7 @@ class Config(ctypes.Structure):
                 ("ra_cap_pages", u32), ("async_ra", u32), ("reserve_frames", u32), ("rpc_slots", u32),
                 ("max_rpc_pages", u32), ("host_threads", u32), ("staging_bytes", u32), ("max_streams", u32),
                 ("max_files", u32), ("trace_capacity", u32), ("xfer", u32), ("debug_counts", u32),
-                ("device", i32), ("reserved", u32 * 7)]
+                ("device", i32), ("latency_capacity", u32), ("reserved", u32 * 6)]
 
 
 class Stat(ctypes.Structure):
@@ -61,6 +61,16 @@ class ScanArgs(ctypes.Structure):
                 ("fused", u32), ("reserved", u32 * 4)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("ctas", u32), ("threads", u32), ("unit_bytes", u64), ("max_requests", u32), ("queue_slots", u32),
+                ("units_in_flight", u32), ("frame_budget", u32), ("idle_exit_ms", u32), ("reserved", u32 * 5)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", u64), ("status", i64), ("sum", u64), ("hash", u64), ("bytes", u64), ("t_admit_ns", u64),
+                ("t_done_ns", u64)]
+
+
 # name -> (restype, argtypes); every symbol include/gfs.h declares.
 SIGNATURES = {
     "gfs_config_default": (ctypes.c_int, [ctypes.POINTER(Config)]),
@@ -76,6 +86,7 @@ SIGNATURES = {
     "gfs_get_trace": (ctypes.c_int, [vp, ctypes.POINTER(RpcRec), ctypes.POINTER(EvictRec), u32,
                                      ctypes.POINTER(u64), ctypes.POINTER(u64), vp]),
     "gfs_get_fetch_counts": (ctypes.c_int, [vp, vp, u64, vp]),
+    "gfs_get_latencies": (ctypes.c_int, [vp, vp, u64, ctypes.POINTER(u64), vp]),
     "gfs_scan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_host": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
@@ -86,6 +97,10 @@ SIGNATURES = {
     "gfs_probe_pread": (ctypes.c_int, [ctypes.c_char_p, u32, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pull": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u64, ctypes.POINTER(u64)]),
+    "gfs_serve_start": (ctypes.c_int, [vp, ctypes.POINTER(ServeConfig), vp]),
+    "gfs_submit_scan": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64]),
+    "gfs_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), ctypes.c_int]),
+    "gfs_serve_stop": (ctypes.c_int, [vp]),
     "gfs_abi_version": (ctypes.c_int, []),
     "gfs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -221,6 +236,15 @@ class Context:
         el = [(e.frame, (e.old_fid, e.old_page), (e.new_fid, e.new_page)) for e in ev[:ke]]
         return rl, el, nr.value, ne.value
 
+    def latencies(self, stream=None) -> np.ndarray:
+        """gread latencies (ns) recorded since the last reset."""
+        cap = int(self.cfg.latency_capacity)
+        out = np.zeros(max(cap, 1), dtype=np.uint64)
+        n = u64()
+        _check(load().gfs_get_latencies(self.handle, out.ctypes.data, cap, ctypes.byref(n), _stream(stream)),
+               "gfs_get_latencies")
+        return out[:min(cap, n.value)]
+
     def fetch_counts(self, n: int, stream=None) -> np.ndarray:
         out = np.zeros(n, dtype=np.uint32)
         _check(load().gfs_get_fetch_counts(self.handle, out.ctypes.data, n, _stream(stream)),
@@ -263,6 +287,32 @@ class Context:
         _check(load().gfs_scan_host(self.handle, fid, ctypes.byref(a), cnt.ctypes.data, sm.ctypes.data,
                                     hs.ctypes.data, _stream(stream)), "gfs_scan_host")
         return cnt[:ns], sm[:ns], hs[:ns]
+
+    # ---- serving
+    def serve_start(self, ctas: int = 152, threads: int = 256, unit_bytes: int = 1 << 20, max_requests: int = 64,
+                    queue_slots: int = 256, units_in_flight: int = 16, frame_budget: int = 0, idle_exit_ms: int = 0,
+                    stream=None):
+        c = ServeConfig()
+        c.ctas, c.threads, c.unit_bytes, c.max_requests = ctas, threads, unit_bytes, max_requests
+        c.queue_slots, c.units_in_flight, c.frame_budget, c.idle_exit_ms = queue_slots, units_in_flight, frame_budget, idle_exit_ms
+        _check(load().gfs_serve_start(self.handle, ctypes.byref(c), _stream(stream)), "gfs_serve_start")
+
+    def submit_scan(self, fid: int, off: int, length: int, tag: int) -> bool:
+        """Queue a scan; False when the submission ring is full (try again)."""
+        rc = load().gfs_submit_scan(self.handle, fid, off, length, tag)
+        if rc == -errno.EAGAIN:
+            return False
+        _check(rc, "gfs_submit_scan")
+        return True
+
+    def poll(self, max_n: int = 64) -> list:
+        buf = (Completion * max_n)()
+        n = _check(load().gfs_poll(self.handle, buf, max_n), "gfs_poll")
+        return [{"tag": c.tag, "status": c.status, "sum": c.sum, "hash": c.hash, "bytes": c.bytes,
+                 "t_admit_ns": c.t_admit_ns, "t_done_ns": c.t_done_ns} for c in buf[:n]]
+
+    def serve_stop(self):
+        _check(load().gfs_serve_stop(self.handle), "gfs_serve_stop")
 
     def read_many(self, fid: int, d_off, d_len, d_dst, d_buf, d_ret, blocks: int = 32, threads: int = 256,
                   stream=None):

@@ -43,7 +43,7 @@ def test_struct_layouts_match_header(tmp_path):
     # compile a C program against include/gfs.h and compare sizes/offsets with ctypes
     import ctypes
     import subprocess
-    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "reserved"]),
+    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "reserved"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
               ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
