@@ -151,6 +151,40 @@ def oracle_sample(path, page, frames, blocks, stride, budget_s, mode="readahead"
     return nbytes, dt, done
 
 
+def serving_bench(args, xfer, mode):
+    """Config 5: 64 scans over log-uniform 16 MiB - 4 GiB files, Poisson 20 req/s, 6 GiB cache."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_2109_05366_gb300 import gfs, serving
+    sizes = serving.log_uniform_sizes(64, 24, 32, seed=5)
+    paths = []
+    for i, sz in enumerate(sizes):
+        p = os.path.join(data_dir(), "gfs_serve_%d_%d.bin" % (i, sz))
+        inputs.ensure_file(p, 1000 + i, sz)
+        paths.append(p)
+    arrivals = serving.poisson_arrivals(64, 20.0, seed=5)
+    out = {}
+    with gfs.Context(cache_bytes=6 * GiB, page_size=512 * KiB, mode=mode, xfer=xfer, max_rpc_pages=16,
+                     rpc_slots=512, latency_capacity=1 << 20, max_files=80, max_streams=1024) as ctx:
+        fids = [ctx.open(p) for p in paths]
+        reqs = [(fid, 0, sz) for fid, sz in zip(fids, sizes)]
+        stream = torch.cuda.Stream()
+        ctx.serve_start(ctas=296, threads=256, unit_bytes=MiB, max_requests=64, queue_slots=128, stream=stream)
+        try:
+            res, t0 = serving.run(ctx, reqs, arrivals, timeout_s=300)
+        finally:
+            ctx.serve_stop()
+        out = serving.summarize(res, t0)
+        lat = ctx.latencies()
+        if len(lat):
+            out["gread_p50_us"] = round(float(np.percentile(lat, 50)) / 1e3, 1)
+            out["gread_p99_us"] = round(float(np.percentile(lat, 99)) / 1e3, 1)
+        out["total_file_bytes"] = int(sum(sizes))
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -226,6 +260,7 @@ def run_gfs(args):
         return ev
 
     cfg = dict(cache_bytes=cache, page_size=page, host_threads=args.host_threads, ra_cap_pages=args.ra_cap,
+               latency_capacity=1 << 16,
                rpc_slots=args.rpc_slots, staging_bytes=args.staging_mib * MiB, max_rpc_pages=args.max_rpc_pages,
                xfer={"pull": gfs.XFER_PULL, "dma": gfs.XFER_DMA, "mapped": gfs.XFER_MAPPED}[args.xfer])
     with gfs.Context(mode=gfs.MODE_READAHEAD, **cfg) as ctx:
@@ -236,6 +271,7 @@ def run_gfs(args):
                 dist.barrier()
             times = timed_scans(ctx, fid, args.steps, args.warmup, fused=args.fused)
         st = ctx.stats(stream)
+        lat = ctx.latencies(stream)
         cnt = out[0].cpu().numpy()
         assert (cnt[:-1] == stride).all() and cnt[-1] == size - (nstr - 1) * stride, "scan returned short counts"
         # e2e: the C-ABI call with host result buffers, wall clock, cache reset outside
@@ -313,6 +349,11 @@ def run_gfs(args):
                                                "unconsumed_evictions", "timeouts", "eio")},
         "input_gen_s": round(gen_s, 1),
     }
+    if len(lat):
+        import numpy as np
+        line["gread_latency_us"] = {"p50": round(float(np.percentile(lat, 50)) / 1e3, 1),
+                                    "p99": round(float(np.percentile(lat, 99)) / 1e3, 1),
+                                    "greads": int(len(lat)), "read_len": stride}
     if binding:
         line["roofline"] = {"bound": "link", "achieved": round(value / world, 2), "peak": round(binding, 1),
                             "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": None,
@@ -322,6 +363,12 @@ def run_gfs(args):
                                 "unit": "GB/s", "frac": round(nbytes_hbm / kt / 1e9 / hbm, 4),
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     line.update(extra)
+    if rank == 0 and not args.quick and not args.no_serving:
+        xf = {"pull": gfs.XFER_PULL, "dma": gfs.XFER_DMA, "mapped": gfs.XFER_MAPPED}[args.xfer]
+        line["serving"] = {"workload": "64 scans, files 2^(24+8u) B (log-uniform 16 MiB-4 GiB), Poisson 20/s, "
+                                       "6 GiB cache, 296 CTAs, 1 MiB units",
+                           "readahead": serving_bench(args, xf, gfs.MODE_READAHEAD),
+                           "ondemand": serving_bench(args, xf, gfs.MODE_ONDEMAND)}
     if not args.quick and not args.no_cpu_baseline:
         size_, seed_, page_, cache_, blocks_, stride_ = WORKLOADS[args.workload]
         b, t, n = oracle_sample(path, page_, cache_ // page_, blocks_, stride_, args.cpu_seconds)
@@ -352,6 +399,7 @@ def main():
     ap.add_argument("--max-rpc-pages", type=int, default=16)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     args = ap.parse_args()
