@@ -226,6 +226,15 @@ int gfs_scan_host(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* h_c
 int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d_count, uint64_t* d_sum,
                     uint64_t* d_hash, void* stream);
 
+/* The steady loop of gfs_scan captured in a CUDA graph: `reps` times
+ * (copy out requests in flight, clear the cache, scan), launched as one graph on
+ * `stream`.  Every repetition starts from an empty cache and rewrites the same
+ * outputs.  Needs GFS_XFER_MAPPED or GFS_XFER_PULL (the DMA transfer's reset
+ * waits on the host); -ENOTSUP otherwise.  The graph is cached in the context
+ * and rebuilt when fid, args, reps or outputs change. */
+int gfs_scan_graph(gfs_ctx* ctx, int fid, const gfs_scan_args* args, uint32_t reps, int64_t* d_count,
+                   uint64_t* d_sum, uint64_t* d_hash, void* stream);
+
 /* n independent greads: request i reads [d_off[i], d_off[i]+d_len[i]) into
  * d_buf + d_dst[i] and writes its return value to d_ret[i]; `blocks`
  * threadblocks take requests i = b, b+blocks, ...; gread stream id = block

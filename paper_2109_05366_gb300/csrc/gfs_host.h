@@ -69,6 +69,8 @@ struct gfs_ctx {
   gfs::IoService* io = nullptr;
   uint8_t* d_scan_buf = nullptr;  // per-block gread buffers of gfs_scan
   size_t scan_buf_bytes = 0;
+  cudaGraphExec_t graph = nullptr;  // gfs_scan_graph: cached executable and its key
+  unsigned long long graph_key[8] = {};
   uint8_t* d_out = nullptr;        // gfs_scan_host results: device side
   uint8_t* h_out = nullptr;        // and a pinned host copy
   size_t out_bytes = 0;

@@ -91,6 +91,7 @@ SIGNATURES = {
     "gfs_scan_host": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_read_many": (ctypes.c_int, [vp, ctypes.c_int, u32, vp, vp, vp, vp, vp, u32, u32, vp]),
+    "gfs_scan_graph": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), u32, vp, vp, vp, vp]),
     "gfs_cpuio_scan": (ctypes.c_int, [ctypes.c_char_p, u64, u64, u32, u64, vp, vp, vp, vp, vp,
                                       ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_h2d": (ctypes.c_int, [u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -273,6 +274,19 @@ class Context:
         a = self._args(stride, read_len, blocks, threads, serialize, fused)
         _check(load().gfs_scan(self.handle, fid, ctypes.byref(a), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
                                _stream(stream)), "gfs_scan")
+        return out
+
+    def scan_graph(self, fid: int, stride: int, reps: int, read_len: int | None = None, blocks: int = 64,
+                   threads: int = 256, serialize: bool = False, fused: bool = False, out=None, stream=None):
+        """reps x (drain, reset, scan) as one captured CUDA graph; returns the last scan's outputs."""
+        import torch
+        size = self.fstat(fid).size
+        ns = (size + stride - 1) // stride if size else 0
+        if out is None:
+            out = tuple(torch.empty(max(ns, 1), dtype=torch.int64, device="cuda") for _ in range(3))
+        a = self._args(stride, read_len, blocks, threads, serialize, fused)
+        _check(load().gfs_scan_graph(self.handle, fid, ctypes.byref(a), reps, _ptr(out[0]), _ptr(out[1]),
+                                     _ptr(out[2]), _stream(stream)), "gfs_scan_graph")
         return out
 
     def scan_host(self, fid: int, stride: int, read_len: int | None = None, blocks: int = 64, threads: int = 256,

@@ -251,3 +251,36 @@ def test_mapped_file_is_mapped_and_exact(torch_cuda, gfs, datadir):
             assert st["host_preads"] == 0 and st["timeouts"] == 0
             ctx.reset_cache()
         ctx.close(fid)
+
+
+@pytest.mark.parametrize("xfer", [1, 2])
+def test_scan_graph_steady_loop_exact(torch_cuda, gfs, datadir, xfer):
+    path = _file(datadir, 1, 64 * MiB)
+    with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB, xfer=xfer, max_rpc_pages=16) as ctx:
+        fid = ctx.open(path)
+        for reps in (1, 3, 3):
+            out = ctx.scan_graph(fid, MiB, reps, blocks=64)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            assert st["pages_fetched"] == 256 and st["timeouts"] == 0  # last repetition, from an empty cache
+
+
+def test_scan_graph_refuses_dma(torch_cuda, gfs, datadir):
+    path = _file(datadir, 1, 64 * MiB)
+    with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB, xfer=0) as ctx:
+        fid = ctx.open(path)
+        with pytest.raises(gfs.GfsError):
+            ctx.scan_graph(fid, MiB, 2)
+
+
+def test_tuner_measures_and_persists(torch_cuda, datadir, tmp_path):
+    from paper_2109_05366_gb300 import tune
+    path = _file(datadir, 3, 64 * MiB)
+    space = {"page_size": [256 * KiB, 1 * MiB], "ra_cap_pages": [1, 8], "rpc_slots": [128], "blocks": [64]}
+    start = {"page_size": 256 * KiB, "ra_cap_pages": 8, "rpc_slots": 128, "blocks": 64}
+    best, allp = tune.tune(path, MiB, space, start, rounds=1, cache_bytes=32 * MiB, reps=1)
+    assert len(allp) == 3 and best["gbps"] > 0 and all(p["short_strides"] == 0 for p in allp)
+    f = str(tmp_path / "best.json")
+    tune.save(best, f)
+    assert tune.load(f) == best
