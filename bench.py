@@ -185,6 +185,57 @@ def serving_bench(args, xfer, mode):
     return out
 
 
+def run_cfg3(args):
+    """Config 3: autotuned sweep over a 16 GiB file (one JSON line per result)."""
+    import torch
+
+    from paper_2109_05366_gb300 import gfs, tune
+    size = 16 * GiB
+    path = os.path.join(data_dir(), "gfs_bench_s3_%d.bin" % size)
+    ensure_input(path, 3, size)
+    results = {"workload": "cfg3_16GiB_sweep", "cache_bytes": 2 * GiB, "strides": {}}
+    for stride in (64 * KiB, MiB, 16 * MiB):
+        best, allp = tune.tune(path, stride, xfer=gfs.XFER_MAPPED, reps=2)
+        print(json.dumps({"stride": stride, "tuning_points": allp}), flush=True)
+        cmp = {}
+        for label, xf, mode, page in (("mapped_readahead", gfs.XFER_MAPPED, 0, best["page_size"]),
+                                      ("mapped_ondemand", gfs.XFER_MAPPED, 1, best["page_size"]),
+                                      ("pull_readahead", gfs.XFER_PULL, 0, best["page_size"]),
+                                      ("pull_ondemand", gfs.XFER_PULL, 1, best["page_size"]),
+                                      ("pull_readahead_64K", gfs.XFER_PULL, 0, 64 * KiB),
+                                      ("pull_ondemand_64K", gfs.XFER_PULL, 1, 64 * KiB)):
+            pt = dict(best)
+            pt.pop("gbps"), pt.pop("ms"), pt.pop("rpcs"), pt.pop("timeouts"), pt.pop("short_strides"), pt.pop("stride")
+            pt["page_size"] = page
+            cmp[label] = tune.measure(path, stride, pt, xfer=xf, mode=mode, reps=2)["gbps"]
+        # the captured steady loop: 4 scans in one graph
+        with gfs.Context(cache_bytes=2 * GiB, page_size=best["page_size"], ra_cap_pages=best["ra_cap_pages"],
+                         rpc_slots=best["rpc_slots"], xfer=gfs.XFER_MAPPED,
+                         max_rpc_pages=min(256, max(16, best["ra_cap_pages"] + stride // best["page_size"] + 1)),
+                         max_streams=4096) as ctx:
+            fid = ctx.open(path)
+            st = torch.cuda.Stream()
+            ns = (size + stride - 1) // stride
+            out = tuple(torch.empty(ns, dtype=torch.int64, device="cuda") for _ in range(3))
+            ctx.scan_graph(fid, stride, 4, blocks=best["blocks"], out=out, stream=st)
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.scan_graph(fid, stride, 4, blocks=best["blocks"], out=out, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            cmp["graph_loop_4_scans"] = round(4 * size / (e0.elapsed_time(e1) / 1e3) / 1e9, 2)
+        d_file = torch.empty(size, dtype=torch.uint8, device="cuda")
+        out = tuple(torch.empty((size + stride - 1) // stride, dtype=torch.int64, device="cuda") for _ in range(3))
+        t = min(gfs.cpuio_scan(path, stride, stride, 16, 8 * MiB, d_file, out) for _ in range(2))
+        cmp["cpuio_16thr"] = round(size / t / 1e9, 2)
+        del d_file
+        results["strides"][str(stride)] = {"best": best, "compare_gbps": cmp}
+        print(json.dumps({"stride": stride, "best": best, "compare_gbps": cmp}), flush=True)
+    print(json.dumps(results), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -400,11 +451,14 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--sweep", choices=["cfg3"], default=None, help="run a sweep instead of the bench line")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep == "cfg3":
+        return run_cfg3(args)
     return run_gfs(args)
 
 

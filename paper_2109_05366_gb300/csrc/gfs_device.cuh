@@ -456,8 +456,11 @@ static __device__ PullJob pull_claim_frame(const DevHandle& g, int f) {
   return j;
 }
 
-// One warp: find a fully published request with pages still FILLING and claim
-// one page.  Scans 32 slots starting at `start`.
+// One warp: find a request with published pages still FILLING and claim one
+// page.  A request counts once its first page is published: a host thread
+// waiting for one of its staging buffers may be in the middle of the request,
+// and only a copy of the pages already published lets it go on.  Scans 32
+// slots starting at `start`.
 static __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
   const int lane = lane_id();
   PullJob j{-1, 0, 0, 0, 0, 0, 0};
@@ -466,7 +469,8 @@ static __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
   unsigned long long t = 0;
   if ((uint32_t)lane < g.rpc_slots) {
     t = ld_rlx64(&g.dticket[s]);
-    cand = ld_rlx(&g.dcopied[s]) < ld_rlx(&g.dnpages[s]) && ld_acq_sys64(&g.done[s].done) == t + 1;
+    cand = ld_rlx(&g.dcopied[s]) < ld_rlx(&g.dnpages[s]) &&
+           ld_acq_sys64(&g.pages[(size_t)s * g.max_rpc_pages].tag) == t + 1;
   }
   unsigned m = __ballot_sync(kFull, cand);
   while (m) {
@@ -482,7 +486,8 @@ static __device__ PullJob pull_claim_any(const DevHandle& g, uint32_t start) {
       if (i < np) {
         f = (int)ld_rlx(&g.dframes[(size_t)ss * g.max_rpc_pages + i]);
         if (f >= (int)g.n_frames || ld_rlx(&g.fstate[f]) != FR_FILLING ||
-            ld_acq(&g.fsrc[f]) != ss * g.max_rpc_pages + i)
+            ld_acq(&g.fsrc[f]) != ss * g.max_rpc_pages + i ||
+            ld_acq_sys64(&g.pages[(size_t)ss * g.max_rpc_pages + i].tag) != tt + 1)
           f = -1;
       }
       unsigned fm = __ballot_sync(kFull, f >= 0);

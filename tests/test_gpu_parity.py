@@ -284,3 +284,18 @@ def test_tuner_measures_and_persists(torch_cuda, datadir, tmp_path):
     f = str(tmp_path / "best.json")
     tune.save(best, f)
     assert tune.load(f) == best
+
+
+def test_pull_partial_requests_are_helped(torch_cuda, gfs, datadir):
+    # Large pages, small strides, few slots: a host thread's staging buffers
+    # cycle inside one readahead request; the pages it already published must be
+    # copied out by helpers even before the request is complete.
+    size = 256 * MiB
+    path = _file(datadir, 9, size)
+    with gfs.Context(cache_bytes=512 * MiB, page_size=2 * MiB, xfer=1, rpc_slots=32, max_rpc_pages=16,
+                     timeout_ns=3 * 10**9, max_streams=1024) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, 64 * KiB, blocks=592, threads=256)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, 64 * KiB, *out)
+        assert ctx.stats()["timeouts"] == 0
