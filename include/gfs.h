@@ -282,6 +282,27 @@ int gfs_poll(gfs_ctx* ctx, gfs_completion* out, int max);
 /* Ask the kernel to finish once every submitted request is done, wait, free. */
 int gfs_serve_stop(gfs_ctx* ctx);
 
+/* ---------------------------------------------------------------- application streams
+ * Consumers shaped like the paper's GPU applications (Section 6.2), reading their
+ * input through the page cache.
+ *
+ * gfs_rowdot: file fid holds a row-major float32 matrix (rows x cols, cols a
+ * multiple of 4).  Block b takes stripes b, b+blocks, ... of stripe_rows rows and
+ * greads each stripe in pieces of read_len bytes (a multiple of the row size);
+ * d_out[r] = sum_c A[r][c] * d_vec[c] in float32 (FMA, any summation order);
+ * d_stripe_sum / d_stripe_hash[s] = the byte checksums of stripe s (as in
+ * gfs_scan); *d_status = 0 or the first -errno.  d_vec holds cols floats. */
+int gfs_rowdot(gfs_ctx* ctx, int fid, uint32_t rows, uint32_t cols, const float* d_vec, float* d_out,
+               uint32_t stripe_rows, uint64_t read_len, uint32_t blocks, uint64_t* d_stripe_sum,
+               uint64_t* d_stripe_hash, int64_t* d_status, void* stream);
+
+/* gfs_histogram: file fid holds int32 values; d_hist[nbins] (zeroed by the call)
+ * receives the count of each value v < nbins; d_sums[0] = sum of all bytes read
+ * mod 2^64, d_sums[1] = values >= nbins; *d_status = 0 or the first -errno.
+ * Block b greads pieces b, b+blocks, ... of read_len bytes (a multiple of 16). */
+int gfs_histogram(gfs_ctx* ctx, int fid, uint32_t nbins, uint32_t* d_hist, uint64_t read_len, uint32_t blocks,
+                  uint64_t* d_sums, int64_t* d_status, void* stream);
+
 /* CPU-I/O baseline (Section 6.2 comparison): `threads` host threads pread the
  * file in `chunk` pieces into pinned buffers and cudaMemcpyAsync them into
  * d_file (>= size bytes, caller-owned); then the same per-stride checksum

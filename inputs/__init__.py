@@ -27,7 +27,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -43,6 +43,13 @@ def _load():
             lib.xs_fill.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
             lib.xs_write_file.restype = ctypes.c_int
             lib.xs_write_file.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+            lib.xs_write_f32.restype = ctypes.c_int
+            lib.xs_write_f32.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+            lib.xs_write_zipf.restype = ctypes.c_int
+            lib.xs_write_zipf.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.c_double, ctypes.c_int]
+            lib.xs_zipf_cdf.restype = ctypes.c_int
+            lib.xs_zipf_cdf.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -109,3 +116,67 @@ def ensure_file(path: str, seed: int, size: int, threads: int | None = None) -> 
         if head == fill(seed, 0, k) and tail == fill(seed, size - k, k):
             return path
     return write_file(path, seed, size, threads)
+
+
+# ---------------------------------------------------------------- typed streams
+def f32_of_word(x: int) -> float:
+    """Uniform [-1, 1) value of one output word: ((x >> 40) * 2^-24) * 2 - 1 (exact in float32)."""
+    return ((x >> 40) * 2.0 ** -24) * 2.0 - 1.0
+
+
+def f32_values(seed: int, n: int):
+    """Plain definition of the first n float32 elements (small n)."""
+    import numpy as np
+    return np.array([f32_of_word(x) for x in xorshift64_words(seed, n)], dtype=np.float32)
+
+
+def zipf_cdf(nbins: int, s: float):
+    import numpy as np
+    w = (np.arange(1, nbins + 1, dtype=np.float64)) ** (-s)
+    c = np.cumsum(w)
+    c /= c[-1]
+    c[-1] = 1.0
+    return c
+
+
+def zipf_values(seed: int, n: int, nbins: int, s: float):
+    """Plain definition of the first n Zipf(s) values over [0, nbins) (small n)."""
+    import bisect
+
+    import numpy as np
+    cdf = list(zipf_cdf(nbins, s))
+    out = []
+    for x in xorshift64_words(seed, n):
+        u = (x >> 11) * 2.0 ** -53
+        out.append(bisect.bisect_right(cdf, u))  # first k with cdf[k] > u
+    return np.array(out, dtype=np.int32)
+
+
+def write_f32(path: str, seed: int, n: int, threads: int | None = None) -> str:
+    threads = threads or min(32, os.cpu_count() or 1)
+    rc = _load().xs_write_f32(path.encode(), seed, n, threads)
+    if rc != 0:
+        raise OSError(-rc, "xs_write_f32(%s)" % path)
+    return path
+
+
+def write_zipf(path: str, seed: int, n: int, nbins: int = 1 << 20, s: float = 1.1,
+               threads: int | None = None) -> str:
+    threads = threads or min(32, os.cpu_count() or 1)
+    rc = _load().xs_write_zipf(path.encode(), seed, n, nbins, s, threads)
+    if rc != 0:
+        raise OSError(-rc, "xs_write_zipf(%s)" % path)
+    return path
+
+
+def ensure_typed(path: str, kind: str, seed: int, n: int, **kw) -> str:
+    """Write the f32 or zipf file unless one of the right size with the right head exists."""
+    import numpy as np
+    k = min(n, 64)
+    if os.path.exists(path) and os.path.getsize(path) == 4 * n:
+        head = np.fromfile(path, dtype=np.float32 if kind == "f32" else np.int32, count=k)
+        ref = f32_values(seed, k) if kind == "f32" else zipf_values(seed, k, kw.get("nbins", 1 << 20),
+                                                                      kw.get("s", 1.1))
+        if np.array_equal(head, ref):
+            return path
+    return write_f32(path, seed, n) if kind == "f32" else write_zipf(path, seed, n, **kw)

@@ -140,3 +140,117 @@ int xs_write_file(const char* path, uint64_t seed, uint64_t size, int threads) {
   if (close(fd) != 0 && !err) err = errno;
   return -err;
 }
+
+/* ---------------------------------------------------------------- typed streams
+ * Element j of a typed stream uses output word j of the xorshift64 stream
+ * (the state after j + 1 steps).
+ *   f32:  v = ((x >> 40) * 2^-24) * 2 - 1, uniform in [-1, 1), exact in float.
+ *   zipf: u = (x >> 11) * 2^-53; v = the first k with cdf[k] > u, where
+ *         cdf[k] = sum_{i<=k} (i+1)^-s / sum_{i<nbins} (i+1)^-s (computed in double).
+ */
+#include <math.h>
+
+float xs_f32_of(uint64_t x) { return (float)((double)(x >> 40) * (1.0 / 16777216.0) * 2.0 - 1.0); }
+
+typedef struct {
+  int fd;
+  uint64_t seed, begin, end; /* element range */
+  int kind;                  /* 0 f32, 1 zipf */
+  const double* cdf;
+  uint32_t nbins;
+  int err;
+} typed_job;
+
+static uint32_t zipf_pick(const double* cdf, uint32_t nbins, uint64_t x) {
+  const double u = (double)(x >> 11) * (1.0 / 9007199254740992.0);
+  uint32_t lo = 0, hi = nbins - 1; /* first k with cdf[k] > u; cdf[nbins-1] == 1 > u */
+  while (lo < hi) {
+    uint32_t mid = lo + (hi - lo) / 2;
+    if (cdf[mid] > u) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+static void* typed_worker(void* arg) {
+  typed_job* j = (typed_job*)arg;
+  const uint64_t CH = 1u << 20; /* elements per write */
+  uint32_t* buf = (uint32_t*)malloc(CH * 4);
+  if (!buf) { j->err = ENOMEM; return NULL; }
+  uint64_t x = xs_state_after(j->seed, j->begin);
+  for (uint64_t e = j->begin; e < j->end; e += CH) {
+    uint64_t n = j->end - e < CH ? j->end - e : CH;
+    for (uint64_t i = 0; i < n; ++i) {
+      x = xs_step(x);
+      if (j->kind == 0) {
+        float f = xs_f32_of(x);
+        memcpy(&buf[i], &f, 4);
+      } else {
+        buf[i] = zipf_pick(j->cdf, j->nbins, x);
+      }
+    }
+    uint64_t put = 0, bytes = n * 4;
+    while (put < bytes) {
+      ssize_t r = pwrite(j->fd, (uint8_t*)buf + put, bytes - put, (off_t)(e * 4 + put));
+      if (r <= 0) { j->err = r < 0 ? errno : EIO; free(buf); return NULL; }
+      put += (uint64_t)r;
+    }
+  }
+  free(buf);
+  return NULL;
+}
+
+/* cdf of Zipf(s) over nbins values (double), written to out[nbins]. */
+int xs_zipf_cdf(double* out, uint32_t nbins, double s) {
+  if (!out || nbins == 0) return -EINVAL;
+  double acc = 0.0;
+  for (uint32_t k = 0; k < nbins; ++k) { acc += pow((double)k + 1.0, -s); out[k] = acc; }
+  for (uint32_t k = 0; k < nbins; ++k) out[k] /= acc;
+  out[nbins - 1] = 1.0;
+  return 0;
+}
+
+static int write_typed(const char* path, uint64_t seed, uint64_t n, int threads, int kind, uint32_t nbins, double s) {
+  if (seed == 0) return -EINVAL;
+  if (threads < 1) threads = 1;
+  if (threads > 64) threads = 64;
+  double* cdf = NULL;
+  if (kind == 1) {
+    if (nbins == 0) return -EINVAL;
+    cdf = (double*)malloc(sizeof(double) * nbins);
+    if (!cdf) return -ENOMEM;
+    xs_zipf_cdf(cdf, nbins, s);
+  }
+  int fd = open(path, O_CREAT | O_TRUNC | O_WRONLY, 0644);
+  if (fd < 0) { free(cdf); return -errno; }
+  if (n && ftruncate(fd, (off_t)(n * 4)) != 0) { int e = errno; close(fd); free(cdf); return -e; }
+  pthread_t tid[64];
+  typed_job jobs[64];
+  uint64_t per = (n / (uint64_t)threads + (1u << 20) - 1) & ~(uint64_t)((1u << 20) - 1);
+  if (per == 0) per = 1u << 20;
+  int started = 0, err = 0;
+  for (int t = 0; t < threads; ++t) {
+    uint64_t b = per * (uint64_t)t;
+    if (b >= n) break;
+    uint64_t e = b + per < n ? b + per : n;
+    jobs[t] = (typed_job){fd, seed, b, e, kind, cdf, nbins, 0};
+    if (pthread_create(&tid[t], NULL, typed_worker, &jobs[t]) != 0) { err = EAGAIN; break; }
+    ++started;
+  }
+  for (int t = 0; t < started; ++t) {
+    pthread_join(tid[t], NULL);
+    if (jobs[t].err && !err) err = jobs[t].err;
+  }
+  if (close(fd) != 0 && !err) err = errno;
+  free(cdf);
+  return -err;
+}
+
+/* n float32 elements (4n bytes). */
+int xs_write_f32(const char* path, uint64_t seed, uint64_t n, int threads) {
+  return write_typed(path, seed, n, threads, 0, 0, 0.0);
+}
+
+/* n int32 Zipf(s) values over [0, nbins) (4n bytes). */
+int xs_write_zipf(const char* path, uint64_t seed, uint64_t n, uint32_t nbins, double s, int threads) {
+  return write_typed(path, seed, n, threads, 1, nbins, s);
+}

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgfs.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gfs_kernels.cu", "gfs_serve.cu", "gfs_host.cpp", "gfs_service.cpp"]
+SOURCES = ["gfs_kernels.cu", "gfs_serve.cu", "gfs_apps.cu", "gfs_host.cpp", "gfs_service.cpp"]
 HEADERS = ["gfs_internal.h", "gfs_device.cuh", "gfs_host.h", "gfs_service.h", "gfs_serve.h"]
 
 

@@ -740,6 +740,21 @@ int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* s
   return 0;
 }
 
+}  // extern "C"
+
+int ensure_scan_buf(gfs_ctx* ctx, size_t need) {
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
+  if (need <= ctx->scan_buf_bytes) return 0;
+  if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
+  ctx->d_scan_buf = nullptr;
+  ctx->scan_buf_bytes = 0;
+  CK(cudaMalloc((void**)&ctx->d_scan_buf, need));
+  ctx->scan_buf_bytes = need;
+  return 0;
+}
+
+extern "C" {
+
 static int scan_prepare(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint64_t* nstrides, uint64_t* buf_stride,
                         DevHandle* g) {
   if (!ctx || !a) return -EINVAL;

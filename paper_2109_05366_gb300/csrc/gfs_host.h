@@ -47,6 +47,11 @@ int launch_checksum(const uint8_t* d_file, uint64_t size, uint64_t stride, uint6
                     uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
 int scan_max_resident_blocks(uint32_t threads, bool fused, int device, int* out);
 int launch_pull_probe(const uint8_t* src, uint8_t* dst, uint64_t n, cudaStream_t s);
+}  // namespace gfs
+struct gfs_ctx;
+// Grow the context's per-block gread buffers to at least `bytes` (before a launch).
+int ensure_scan_buf(gfs_ctx* ctx, size_t bytes);
+namespace gfs {
 
 }  // namespace gfs
 

@@ -98,6 +98,8 @@ SIGNATURES = {
     "gfs_probe_pread": (ctypes.c_int, [ctypes.c_char_p, u32, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pull": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u64, ctypes.POINTER(u64)]),
+    "gfs_rowdot": (ctypes.c_int, [vp, ctypes.c_int, u32, u32, vp, vp, u32, u64, u32, vp, vp, vp, vp]),
+    "gfs_histogram": (ctypes.c_int, [vp, ctypes.c_int, u32, vp, u64, u32, vp, vp, vp]),
     "gfs_serve_start": (ctypes.c_int, [vp, ctypes.POINTER(ServeConfig), vp]),
     "gfs_submit_scan": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64]),
     "gfs_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), ctypes.c_int]),
@@ -301,6 +303,32 @@ class Context:
         _check(load().gfs_scan_host(self.handle, fid, ctypes.byref(a), cnt.ctypes.data, sm.ctypes.data,
                                     hs.ctypes.data, _stream(stream)), "gfs_scan_host")
         return cnt[:ns], sm[:ns], hs[:ns]
+
+    # ---- application streams
+    def rowdot(self, fid: int, rows: int, cols: int, d_vec, stripe_rows: int = 128, read_len: int = 1 << 20,
+               blocks: int = 296, stream=None):
+        """Per-row float32 dot products of a row-major matrix file with d_vec.
+
+        Returns device tensors (out float32[rows], stripe_sum int64, stripe_hash int64, status int64[1])."""
+        import torch
+        ns = (rows + stripe_rows - 1) // stripe_rows
+        out = torch.empty(rows, dtype=torch.float32, device="cuda")
+        ssum = torch.empty(ns, dtype=torch.int64, device="cuda")
+        shash = torch.empty(ns, dtype=torch.int64, device="cuda")
+        status = torch.zeros(1, dtype=torch.int64, device="cuda")
+        _check(load().gfs_rowdot(self.handle, fid, rows, cols, _ptr(d_vec), _ptr(out), stripe_rows, read_len,
+                                 blocks, _ptr(ssum), _ptr(shash), _ptr(status), _stream(stream)), "gfs_rowdot")
+        return out, ssum, shash, status
+
+    def histogram(self, fid: int, nbins: int = 1 << 20, read_len: int = 1 << 20, blocks: int = 296, stream=None):
+        """Histogram of an int32 file.  Returns device tensors (hist int32[nbins], sums int64[2], status int64[1])."""
+        import torch
+        hist = torch.empty(nbins, dtype=torch.int32, device="cuda")
+        sums = torch.empty(2, dtype=torch.int64, device="cuda")
+        status = torch.zeros(1, dtype=torch.int64, device="cuda")
+        _check(load().gfs_histogram(self.handle, fid, nbins, _ptr(hist), read_len, blocks, _ptr(sums), _ptr(status),
+                                    _stream(stream)), "gfs_histogram")
+        return hist, sums, status
 
     # ---- serving
     def serve_start(self, ctas: int = 152, threads: int = 256, unit_bytes: int = 1 << 20, max_requests: int = 64,

@@ -67,3 +67,24 @@ def test_thread_count_independent(tmp_path):
 def test_seed_zero_rejected(tmp_path):
     with pytest.raises(OSError):
         inputs.write_file(str(tmp_path / "z"), 0, 10)
+
+
+def test_f32_stream_definition(tmp_path):
+    import numpy as np
+    p = str(tmp_path / "a.f32")
+    inputs.write_f32(p, 7, 3000, threads=3)
+    a = np.fromfile(p, dtype=np.float32)
+    assert np.array_equal(a, inputs.f32_values(7, 3000))
+    x0 = inputs.xorshift64_words(7, 1)[0]
+    assert a[0] == np.float32(((x0 >> 40) * 2.0 ** -24) * 2 - 1)
+    assert a.min() >= -1.0 and a.max() < 1.0
+
+
+def test_zipf_stream_definition(tmp_path):
+    import numpy as np
+    p = str(tmp_path / "z.i32")
+    inputs.write_zipf(p, 8, 4000, 1 << 20, 1.1, threads=2)
+    z = np.fromfile(p, dtype=np.int32)
+    assert np.array_equal(z, inputs.zipf_values(8, 4000, 1 << 20, 1.1))
+    # P(0) = 1 / H(2^20, 1.1); H(2^20, 1.1) is about 7.9, so the top bin holds ~12.6 %
+    assert 0.09 < (z == 0).mean() < 0.16 and z.min() >= 0 and z.max() < (1 << 20)

@@ -434,3 +434,41 @@ def test_readahead_never_refetches(tmp_path):
         seen |= pages
     assert asyncs > 0 and sim.stats.evictions > 0
     sim.close_all()
+
+
+# ---------------------------------------------------------------- application consumers
+def test_rowdot_matches_fsum_and_closed_forms(tmp_path):
+    import math
+
+    from oracle import apps
+    rows, cols = 6, 40
+    path = str(tmp_path / "m.f32")
+    inputs.write_f32(path, 7, rows * cols)
+    a = np.fromfile(path, dtype=np.float32).reshape(rows, cols)
+    v = inputs.f32_values(8, cols)
+    dot, ab = apps.rowdot(path, rows, cols, v)
+    for r in range(rows):
+        exact = math.fsum(float(x) * float(y) for x, y in zip(a[r], v))
+        assert abs(dot[r] - exact) <= 1e-12 * ab[r]
+        assert ab[r] == pytest.approx(math.fsum(abs(float(x) * float(y)) for x, y in zip(a[r], v)), rel=1e-12)
+    ones = np.ones(cols, dtype=np.float32)
+    dot1, _ = apps.rowdot(path, rows, cols, ones)
+    assert np.allclose(dot1, a.astype(np.float64).sum(axis=1), rtol=0, atol=1e-12)   # v = 1: row sums
+    dot2, _ = apps.rowdot(path, rows, cols, ones, row_lo=2, row_hi=4)
+    assert np.array_equal(dot2, dot1[2:4])
+    assert apps.gamma(32768) == pytest.approx(32768 * 2.0 ** -24 / (1 - 32768 * 2.0 ** -24))
+
+
+def test_histogram_brute_force(tmp_path):
+    from collections import Counter
+
+    from oracle import apps
+    path = str(tmp_path / "z.i32")
+    inputs.write_zipf(path, 8, 5000, 1 << 10, 1.1)
+    x = np.fromfile(path, dtype=np.int32)
+    counts, out = apps.histogram(path, 1 << 10)
+    c = Counter(x.tolist())
+    assert out == 0 and int(counts.sum()) == 5000
+    assert all(int(counts[k]) == c.get(k, 0) for k in range(1 << 10))
+    counts, out = apps.histogram(path, 4)       # values >= 4 are counted as outside
+    assert out == sum(v for k, v in c.items() if k >= 4)
