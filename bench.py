@@ -236,6 +236,147 @@ def run_cfg3(args):
     return 0
 
 
+def run_cfg4(args):
+    """Config 4: float32 32768x32768 row dots by 128-row stripes; 8 GiB Zipf int32 histogram."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from oracle import apps
+    from paper_2109_05366_gb300 import gfs
+    rows = cols = 32768
+    mpath = os.path.join(data_dir(), "gfs_cfg4_mat_%d.f32" % rows)
+    vpath = os.path.join(data_dir(), "gfs_cfg4_vec_%d.f32" % cols)
+    zpath = os.path.join(data_dir(), "gfs_cfg4_zipf.i32")
+    nz = 1 << 31
+    t0 = time.time()
+    inputs.ensure_typed(mpath, "f32", 7, rows * cols)
+    inputs.ensure_typed(vpath, "f32", 8, cols)
+    inputs.ensure_typed(zpath, "zipf", 9, nz, nbins=1 << 20, s=1.1)
+    gen_s = time.time() - t0
+    vec = np.fromfile(vpath, dtype=np.float32)
+    res = {"workload": "cfg4 application streams", "input_gen_s": round(gen_s, 1)}
+    stream = torch.cuda.Stream()
+    for xname, xf in (("mapped", gfs.XFER_MAPPED), ("pull", gfs.XFER_PULL)):
+        with gfs.Context(cache_bytes=GiB, page_size=512 * KiB, xfer=xf, max_rpc_pages=16, rpc_slots=512) as ctx:
+            fid = ctx.open(mpath)
+            d_vec = torch.from_numpy(vec).cuda()
+            ts = []
+            for r in range(3):
+                ctx.reset_cache(stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out, ssum, shash, status = ctx.rowdot(fid, rows, cols, d_vec, 128, MiB, blocks=296, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            got = out.cpu().numpy().astype(np.float64)
+            rng = np.random.default_rng(4)
+            sample = np.sort(rng.choice(rows, 64, replace=False))
+            worst = 0.0
+            for r in sample:
+                ref, ab = apps.rowdot(mpath, rows, cols, vec, int(r), int(r) + 1)
+                worst = max(worst, abs(got[r] - ref[0]) / (apps.gamma(cols) * ab[0]))
+            res["rowdot_" + xname] = {"gbps": round(rows * cols * 4 / min(ts[1:]) / 1e9, 1), "status": int(status.item()),
+                                      "sampled_rows": 64, "max_err_over_bound": round(worst, 4)}
+            fz = ctx.open(zpath)
+            ts = []
+            for r in range(3):
+                ctx.reset_cache(stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hist, sums, status = ctx.histogram(fz, 1 << 20, MiB, blocks=296, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            h = hist.cpu().numpy().view(np.uint32).astype(np.uint64)
+            res["histogram_" + xname] = {"gbps": round(nz * 4 / min(ts[1:]) / 1e9, 1), "status": int(status.item()),
+                                         "total_count": int(h.sum()), "expected": nz,
+                                         "outside": int(gfs.u64_view(sums)[1]), "top_bin_frac": round(float(h[0]) / nz, 4)}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def _resident_fraction(path):
+    """Fraction of the file's pages in the host page cache (mincore on a read-only mapping)."""
+    import ctypes
+    import mmap
+    size = os.path.getsize(path)
+    if size == 0:
+        return 0.0
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.mmap.restype = ctypes.c_void_p
+    libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long]
+    libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    libc.mincore.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        addr = libc.mmap(None, size, mmap.PROT_READ, mmap.MAP_SHARED, fd, 0)
+        if addr in (None, ctypes.c_void_p(-1).value):
+            return -1.0
+        pg = mmap.PAGESIZE
+        n = (size + pg - 1) // pg
+        vec = (ctypes.c_ubyte * n)()
+        rc = libc.mincore(ctypes.c_void_p(addr), size, vec)
+        libc.munmap(ctypes.c_void_p(addr), size)
+    finally:
+        os.close(fd)
+    if rc != 0:
+        return -1.0
+    return sum(v & 1 for v in vec) / n
+
+
+def run_cold(args):
+    """Config 2 cold: the 8 GiB file on the box's disk, host page cache dropped before every scan."""
+    import torch
+
+    import inputs
+    from paper_2109_05366_gb300 import gfs
+    size, seed, page, cache, blocks, stride = WORKLOADS[DEFAULT_WORKLOAD]
+    d = os.environ.get("GFS_COLD_DIR", tempfile.gettempdir())
+    path = os.path.join(d, "gfs_cold_s%d_%d.bin" % (seed, size))
+    inputs.ensure_file(path, seed, size)
+    fd = os.open(path, os.O_RDONLY)
+    os.fsync(fd)  # written pages must be clean before the cache can drop them
+    os.close(fd)
+    stream = torch.cuda.Stream()
+    res = {"workload": "cfg2 cold: 8 GiB file on disk (%s), page cache dropped (posix_fadvise DONTNEED) "
+                       "before each scan" % d}
+    out = tuple(torch.empty(size // stride, dtype=torch.int64, device="cuda") for _ in range(3))
+    for label, xf, mode in (("pull_readahead", gfs.XFER_PULL, 0), ("pull_ondemand", gfs.XFER_PULL, 1),
+                            ("dma_readahead", gfs.XFER_DMA, 0)):
+        with gfs.Context(cache_bytes=cache, page_size=page, xfer=xf, mode=mode, max_rpc_pages=16,
+                         rpc_slots=512) as ctx:
+            fid = ctx.open(path)
+            ts, resident = [], []
+            for r in range(2):
+                ctx.reset_cache(stream)
+                f = os.open(path, os.O_RDONLY)
+                os.posix_fadvise(f, 0, 0, os.POSIX_FADV_DONTNEED)
+                os.close(f)
+                resident.append(round(_resident_fraction(path), 4))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.scan(fid, stride, blocks=blocks, out=out, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            ok = bool((out[0][:-1] == stride).all().item())
+        res[label] = {"gbps": round(size / min(ts) / 1e9, 2), "resident_before": resident, "counts_ok": ok}
+    # the same host read without the GPU: 16 pread threads after dropping the cache
+    f = os.open(path, os.O_RDONLY)
+    os.posix_fadvise(f, 0, 0, os.POSIX_FADV_DONTNEED)
+    os.close(f)
+    res["pread_16thr_cold_gbps"] = round(gfs.probe_pread(path, 16, 4 * MiB, 1), 2)
+    f = os.open(path, os.O_RDONLY)
+    os.posix_fadvise(f, 0, 0, os.POSIX_FADV_DONTNEED)
+    os.close(f)
+    d_file = torch.empty(size, dtype=torch.uint8, device="cuda")
+    res["cpuio_16thr_cold_gbps"] = round(size / gfs.cpuio_scan(path, stride, stride, 16, 8 * MiB, d_file, out) / 1e9, 2)
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -451,7 +592,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--sweep", choices=["cfg3"], default=None, help="run a sweep instead of the bench line")
+    ap.add_argument("--sweep", choices=["cfg3", "cfg4", "cold"], default=None, help="run a sweep instead of the bench line")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -459,6 +600,10 @@ def main():
         return run_reference(args)
     if args.sweep == "cfg3":
         return run_cfg3(args)
+    if args.sweep == "cfg4":
+        return run_cfg4(args)
+    if args.sweep == "cold":
+        return run_cold(args)
     return run_gfs(args)
 
 
