@@ -58,6 +58,19 @@ Rules (R1-R7) as implemented below:
   R8 data read sequentially is used once (Section 5.1): a readahead window is
      also cut at the first page already fetched since the last cache reset
      (it was read and evicted, or is being read); demand misses always fetch.
+Paper mode (mode="paper"; Sections 4.1 and 5.1 as the paper designs them):
+  P1 every stream (threadblock) has a private buffer; on a miss at page p the
+     stream allocates a frame for p and looks in its buffer: if p is there the
+     page is copied from it (no request); otherwise one request of
+     1 + W pages (PAGE_SIZE + PREFETCH_SIZE, W = ra_cap, static) is sent, page p
+     goes to the frame and pages p+1 .. p+W replace the buffer's contents.
+     No window growth, no asynchronous readahead, no coordination between
+     streams (two streams may prefetch the same pages).
+  P2 replacement "tb_lra": each stream keeps the frames it allocated in
+     allocation order, at most quota = max(1, F // streams) of them; below the
+     quota it takes a never-used frame, at the quota it evicts its own least
+     recently allocated frame and reuses it (remapping it in the page table).
+     replacement "fifo" uses rule R6 instead.
 A demand page that finds no victim at all (every frame belongs to the current
 gread) makes the gread return -ENOMEM; later pages of a demand run just end the
 request early.
@@ -121,6 +134,7 @@ class Stats:
     evictions: int = 0
     unconsumed_evictions: int = 0
     fetch_count: dict = field(default_factory=dict)  # (fid, page) -> times fetched
+    buffer_hits: int = 0                              # paper mode: misses served from the private buffer
 
 
 class PageCacheSim:
@@ -128,11 +142,11 @@ class PageCacheSim:
 
     def __init__(self, page_size: int, n_frames: int, mode: str = "readahead",
                  ra_cap: int = 8, reserve: int = 0, async_ra: bool = True,
-                 read_fn=None, max_rpc_pages: int = 64):
+                 read_fn=None, max_rpc_pages: int = 64, replacement: str = "fifo", streams: int = 1):
         if page_size <= 0 or n_frames <= 0:
             raise ValueError("page_size and n_frames must be positive")
-        if mode not in ("readahead", "ondemand"):
-            raise ValueError("mode must be 'readahead' or 'ondemand'")
+        if mode not in ("readahead", "ondemand", "paper"):
+            raise ValueError("mode must be 'readahead', 'ondemand' or 'paper'")
         self.P = page_size
         self.F = n_frames
         self.mode = mode
@@ -140,6 +154,12 @@ class PageCacheSim:
         self.reserve = reserve
         self.async_ra = async_ra
         self.max_rpc = max_rpc_pages
+        if replacement not in ("fifo", "tb_lra"):
+            raise ValueError("replacement must be 'fifo' or 'tb_lra'")
+        self.replacement = replacement
+        self.quota = max(1, n_frames // max(1, streams))
+        self.lra: dict[int, deque] = {}          # P2: frames each stream allocated, oldest first
+        self.privbuf: dict[int, tuple] = {}      # P1: stream -> (fid, {page: data})
         self.read_fn = read_fn or (lambda fd, off, n: os.pread(fd, n, off))
         self.frames = [Frame() for _ in range(n_frames)]
         self.table: dict[tuple, int] = {}
@@ -174,6 +194,8 @@ class PageCacheSim:
         self.alloc_counter = 0
         self.last_end.clear()
         self.fetched.clear()
+        self.lra.clear()
+        self.privbuf.clear()
 
     def present(self, fid: int, page: int) -> bool:
         return (fid, page) in self.table
@@ -273,10 +295,71 @@ class PageCacheSim:
             taken.append(f)
         return taken
 
+    # ---- paper mode (P1, P2) -----------------------------------------------------
+    def _take_paper(self, stream: int, gread_seq0: int, new_key) -> int:
+        if self.replacement == "fifo":
+            return self._take(False, gread_seq0, new_key)
+        q = self.lra.setdefault(stream, deque())
+        if len(q) < self.quota and self.next_unused < self.F:
+            f = self.next_unused
+            self.next_unused += 1
+            q.append(f)
+            return f
+        for _ in range(len(q)):
+            f = q.popleft()
+            if f == self._pinned or f in self._busy:
+                q.append(f)
+                continue
+            self._evict(f, new_key)
+            q.append(f)
+            return f
+        raise NoFrame("stream has no frame to reuse")
+
+    def _miss_paper(self, stream: int, fi: FileInfo, fid: int, p: int, gread_seq0: int):
+        self.stats.misses += 1
+        f = self._take_paper(stream, gread_seq0, (fid, p))
+        self._install(f, (fid, p))
+        self.fetched.add((fid, p))
+        buf = self.privbuf.get(stream)
+        if buf is not None and buf[0] == fid and p in buf[1]:          # P1: buffer hit
+            fr = self.frames[f]
+            fr.data = buf[1][p]
+            fr.valid = len(fr.data)
+            fr.state = READY
+            self.stats.buffer_hits += 1
+            self._busy.clear()
+            return
+        n = min(1 + self.Wmax, fi.npages - p, self.max_rpc)
+        kind = SYNC_RA if n > 1 else DEMAND
+        self.rpc_log.append((fid, p, n, kind))
+        self.stats.rpcs += 1
+        want = min(n * self.P, fi.size - p * self.P)
+        try:
+            data = self.read_fn(fi.fd, p * self.P, want)
+        except OSError:
+            data = b""
+        pages = {}
+        for i in range(n):
+            q = p + i
+            expect = min(self.P, fi.size - q * self.P)
+            chunk = data[i * self.P:i * self.P + expect]
+            if len(chunk) == expect:
+                pages[q] = chunk
+            self.stats.pages_fetched += 1
+            self.stats.fetch_count[(fid, q)] = self.stats.fetch_count.get((fid, q), 0) + 1
+        fr = self.frames[f]
+        ok = p in pages
+        fr.data = pages.get(p, b"")
+        fr.valid = len(fr.data) if ok else 0
+        fr.state = READY if ok else ERROR
+        self.stats.bytes_fetched += fr.valid
+        self.privbuf[stream] = (fid, {q: d for q, d in pages.items() if q != p})
+        self._busy.clear()
+
     # ---- R1-R3: a miss ----------------------------------------------------------
     def _miss(self, stream: int, fi: FileInfo, fid: int, p: int, p1: int, gread_seq0: int):
         self.stats.misses += 1
-        if self.mode == "ondemand" or not fi.readahead:            # R1 / R7
+        if self.mode != "readahead" or not fi.readahead:            # R1 / R7
             taken = self._request(fi, fid, p, 1, 1, gread_seq0)
             self._fetch(fi, fid, p, taken, DEMAND)
             return
@@ -337,7 +420,10 @@ class PageCacheSim:
                 self.stats.hits += 1
             else:
                 try:
-                    self._miss(stream, fi, fid, p, p1, seq0)
+                    if self.mode == "paper" and fi.readahead:
+                        self._miss_paper(stream, fi, fid, p, seq0)
+                    else:
+                        self._miss(stream, fi, fid, p, p1, seq0)
                 except NoFrame:
                     ret = -ENOMEM
                     break
@@ -383,7 +469,7 @@ def default_reserve(blocks: int, read_len: int, page_size: int) -> int:
 def run_scan(path: str, page_size: int, n_frames: int, stride: int, blocks: int,
              mode: str = "readahead", ra_cap: int = 8, reserve: int | None = None,
              async_ra: bool = True, read_len: int | None = None, keep_data: bool = False,
-             max_rpc_pages: int = 64):
+             max_rpc_pages: int = 64, replacement: str = "fifo"):
     """Run the stride scan through the simulator in canonical order.
 
     Returns (sim, results) with results[s] = (count, sum, hash, data-or-None) per
@@ -394,7 +480,7 @@ def run_scan(path: str, page_size: int, n_frames: int, stride: int, blocks: int,
     if reserve is None:
         reserve = default_reserve(blocks, read_len, page_size)
     sim = PageCacheSim(page_size, n_frames, mode, ra_cap, reserve, async_ra,
-                       max_rpc_pages=max_rpc_pages)
+                       max_rpc_pages=max_rpc_pages, replacement=replacement, streams=blocks)
     sim.open(0, path)
     results = []
     try:

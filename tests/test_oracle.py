@@ -472,3 +472,52 @@ def test_histogram_brute_force(tmp_path):
     assert all(int(counts[k]) == c.get(k, 0) for k in range(1 << 10))
     counts, out = apps.histogram(path, 4)       # values >= 4 are counted as outside
     assert out == sum(v for k, v in c.items() if k >= 4)
+
+
+# ---------------------------------------------------------------- paper mode (Sections 4.1, 5.1)
+def test_golden_paper_private_buffer(tmp_path):
+    params, rows = _parse("policy_paper_private_buffer.txt")
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(tmp_path, "pp", int(params["seed"]), npg * page)
+    sim = policy.PageCacheSim(page, int(params["frames"]), "paper", ra_cap=int(params["prefetch"]), reserve=0,
+                              replacement="tb_lra", streams=1)
+    sim.open(0, path)
+    ref = inputs.xorshift64_bytes(int(params["seed"]), npg * page)
+    for q in range(npg):
+        n, data = sim.gread(0, 0, q * page, page)
+        assert data == ref[q * page:(q + 1) * page]
+    assert [(lo, n) for (_, lo, n, _) in sim.rpc_log] == [(int(r[1]), int(r[2])) for r in rows if r[0] == "rpc"]
+    assert sim.evict_log == [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert sim.stats.buffer_hits == int([r for r in rows if r[0] == "buffer_hits"][0][1])
+    sim.close_all()
+
+
+def test_paper_lra_quota_isolates_streams(tmp_path):
+    # 2 streams, 4 frames: quota 2; a stream only ever reuses frames it allocated
+    path = _file(tmp_path, "pq", 4, 40 * P)
+    sim = policy.PageCacheSim(P, 4, "paper", ra_cap=0, reserve=0, replacement="tb_lra", streams=2)
+    sim.open(0, path)
+    owner = {}
+    for step in range(10):
+        for s in range(2):
+            q = s * 20 + step
+            sim.gread(s, 0, q * P, P)
+    for s, dq in sim.lra.items():
+        assert len(dq) <= sim.quota == 2
+        for f in dq:
+            assert owner.setdefault(f, s) == s
+    for f, old, new in sim.evict_log:
+        assert (old[1] < 20) == (new[1] < 20)       # stream 0 pages stay in stream 0 frames
+    sim.close_all()
+
+
+def test_paper_mode_prefetches_duplicates_and_delivers_plain_bytes(tmp_path):
+    # no coordination between streams (Section 4.3): neighbouring streams may
+    # prefetch the same pages, but every delivered byte is the file's
+    size = 37 * P + 11
+    path = _file(tmp_path, "pd", 5, size)
+    sim, res = policy.run_scan(path, P, 16, 2 * P, 3, mode="paper", ra_cap=3, replacement="tb_lra", keep_data=True)
+    c, s, h = plain.scan_plain(path, 2 * P)
+    assert [r[0] for r in res] == c and [r[1] for r in res] == s and [r[2] for r in res] == h
+    assert max(sim.stats.fetch_count.values()) > 1        # duplicates happen
+    assert sim.stats.buffer_hits > 0
