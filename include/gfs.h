@@ -40,6 +40,13 @@ extern "C" {
 /* Cache policy modes. */
 #define GFS_MODE_READAHEAD 0 /* Section 4.1 prefetcher + Section 2.3 window growth */
 #define GFS_MODE_ONDEMAND 1  /* original GPUfs (Section 2.2): one page per request */
+#define GFS_MODE_PAPER 2     /* the paper's own prefetcher (Section 4.1): per-threadblock private buffer,
+                              * one request of 1 + ra_cap_pages pages on a miss; GFS_XFER_PULL / MAPPED only */
+
+/* Replacement (gfs_config.replacement). */
+#define GFS_REPL_FIFO 0   /* never-used, then consumed FIFO, then least recently allocated (rule R6) */
+#define GFS_REPL_TB_LRA 1 /* Section 5.1: per-threadblock least-recently-allocated queues of F / blocks frames
+                           * (GFS_MODE_PAPER only) */
 
 /* Open flags (Section 4.4, "Page cache coherency": readahead for read-only opens only). */
 #define GFS_RDONLY 0
@@ -85,7 +92,8 @@ typedef struct gfs_config {
   uint32_t debug_counts;   /* 1: keep per-page fetch counts for file id 0 */
   int32_t device;          /* CUDA device ordinal */
   uint32_t latency_capacity; /* greads whose latency (globaltimer ns, entry to exit) is kept; 0 = off */
-  uint32_t reserved[6];
+  uint32_t replacement;    /* GFS_REPL_* */
+  uint32_t reserved[5];
 } gfs_config;
 
 typedef struct gfs_stat {
@@ -107,7 +115,8 @@ typedef struct gfs_stats {
   uint64_t host_ns_pread;     /* host I/O threads: time inside pread, summed over threads */
   uint64_t host_ns_wait_buf;  /* time waiting for a staging buffer to be copied out (pull) */
   uint64_t host_ns_idle;      /* time waiting for a request */
-  uint64_t reserved[5];
+  uint64_t buffer_hits;       /* GFS_MODE_PAPER: misses served from the private buffer */
+  uint64_t reserved[4];
 } gfs_stats;
 
 /* One entry of the RPC trace: a request as the GPU issued it. */

@@ -141,6 +141,7 @@ extern "C" int gfs_rowdot(gfs_ctx* ctx, int fid, uint32_t rows, uint32_t cols, c
   if ((uint64_t)rows * row_bytes > ctx->files[fid].size) return -EINVAL;
   const uint64_t stride = (read_len + 255) / 256 * 256;
   int rc = ensure_scan_buf(ctx, (size_t)blocks * stride);
+  if (!rc) rc = ensure_paper_state(ctx, blocks);
   if (rc) return rc;
   DevHandle g = ctx->dev;
   g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
@@ -160,6 +161,7 @@ extern "C" int gfs_histogram(gfs_ctx* ctx, int fid, uint32_t nbins, uint32_t* d_
   if (nbins == 0 || read_len == 0 || read_len % 16 || blocks == 0) return -EINVAL;
   const uint64_t stride = (read_len + 255) / 256 * 256;
   int rc = ensure_scan_buf(ctx, (size_t)blocks * stride);
+  if (!rc) rc = ensure_paper_state(ctx, blocks);
   if (rc) return rc;
   DevHandle g = ctx->dev;
   g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames

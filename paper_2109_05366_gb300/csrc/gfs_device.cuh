@@ -604,7 +604,7 @@ static __device__ bool block_help(const DevHandle& g, int target, bool any) {
 
 // ---------------------------------------------------------------- request ring
 static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
-                          const uint32_t* s_frames, unsigned long long deadline) {
+                          const uint32_t* s_frames, unsigned long long deadline, unsigned long long* ticket_out = nullptr) {
   const int lane = lane_id();
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(&g.ctrl->ring_tail.v, 1ull);
@@ -628,7 +628,16 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
     __syncwarp();
     if (ns < 2048) ns <<= 1;
   }
-  if (g.xfer != GFS_XFER_DMA) {
+  if (g.xfer != GFS_XFER_DMA && !s_frames) {  // paper mode: the requesting block copies every page itself
+    if (lane == 0) {
+      st_rlx64(&g.dticket[si], t);
+      st_rlx(&g.dnpages[si], 0u);  // helpers skip it
+      st_rlx(&g.dcopied[si], 0u);
+    }
+    __syncwarp();
+    __threadfence();
+    __syncwarp();
+  } else if (g.xfer != GFS_XFER_DMA) {
     for (uint32_t i = lane; i < n; i += 32) g.dframes[(size_t)si * g.max_rpc_pages + i] = s_frames[i];
     if (lane == 0) {
       st_rlx64(&g.dticket[si], t);
@@ -653,6 +662,7 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
   __syncwarp();
   __threadfence_system();
   __syncwarp();
+  if (ticket_out) *ticket_out = t;
   if (lane == 0) {
     st_rel_sys64(&s->seq, t + 1);
     stat_add(g, ST_RPCS, 1);
@@ -825,11 +835,258 @@ static __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, 
   return f0;
 }
 
+// ---------------------------------------------------------------- paper mode (Sections 4.1, 5.1)
+enum : int { PJ_NONE = 0, PJ_BUFFER = 1, PJ_REQUEST = 2 };
+struct PaperJob {
+  int kind;
+  int f;
+  uint32_t slot, n;
+  unsigned long long t, page, src;
+};
+
+// Claim a frame this stream owns for reuse (one thread).  1 claimed, 0 busy, -1 not reusable.
+static __device__ int frame_claim_own(const DevHandle& g, int f) {
+  const uint32_t st = ld_acq(&g.fstate[f]);
+  if (!(st == FR_READY || st == FR_ERROR || (st == FR_EMPTY && ld_rlx64(&g.fkey[f]) == KEY_NONE))) return 0;
+  if (atomicCAS(&g.fstate[f], st, (uint32_t)FR_RECLAIM) != st) return 0;
+  __threadfence();
+  if (ld_rlx(&g.fpins[f]) != 0u) {
+    st_rel(&g.fstate[f], st);
+    return 0;
+  }
+  return 1;
+}
+
+// Section 5.1: the stream's least-recently-allocated queue.  Below the quota a
+// never-used frame joins it; at the quota the oldest frame is reused (its old
+// page unmapped) and becomes the newest (warp).
+static __device__ int take_frame_lra(const DevHandle& g, int stream, unsigned long long seq0, unsigned long long new_key,
+                                     unsigned long long deadline) {
+  const int lane = lane_id();
+  int f = -1, reuse = 0;
+  if (lane == 0) {
+    const uint32_t base = (uint32_t)stream * g.quota;
+    const uint32_t len = g.lra_len[stream], head = g.lra_head[stream];
+    if (len < g.quota && ld_rlx64(&g.ctrl->next_unused.v) < g.n_frames) {
+      const unsigned long long u = atomicAdd(&g.ctrl->next_unused.v, 1ull);
+      if (u < g.n_frames) {
+        f = (int)u;
+        g.lra[base + (head + len) % g.quota] = (uint32_t)f;
+        g.lra_len[stream] = len + 1;
+      }
+    }
+    if (f < 0 && len > 0) {
+      for (;;) {
+        const int cand = (int)g.lra[base + head];
+        if (frame_claim_own(g, cand) == 1) {
+          f = cand;
+          reuse = 1;
+          g.lra_head[stream] = (head + 1) % g.quota;  // the reused frame is now the newest
+          break;
+        }
+        if (now_ns() > deadline) break;
+        __nanosleep(128);
+      }
+    }
+  }
+  f = bcast(f);
+  if (bcast(reuse)) {
+    evict_key(g, f, new_key, deadline);
+    return f;
+  }
+  if (f >= 0) return f;
+  // the stream owns no frame and none is unused: take any victim and adopt it
+  f = take_frame(g, false, seq0, new_key, deadline);
+  if (f >= 0 && lane == 0) {
+    const uint32_t base = (uint32_t)stream * g.quota;
+    const uint32_t len = g.lra_len[stream], head = g.lra_head[stream];
+    if (len < g.quota) {
+      g.lra[base + (head + len) % g.quota] = (uint32_t)f;
+      g.lra_len[stream] = len + 1;
+    }
+  }
+  return f;
+}
+
+// Section 4.1 miss: allocate a frame for p, then serve it from the stream's
+// private buffer or request PAGE_SIZE + PREFETCH_SIZE (warp).  Returns the
+// pinned FILLING frame and the block-level work in *job, -EAGAIN, or -errno.
+static __device__ int handle_miss_paper(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi,
+                                        unsigned long long p, unsigned long long seq0, unsigned long long deadline,
+                                        PaperJob* job) {
+  const int lane = lane_id();
+  const unsigned long long key = make_key(fid, p);
+  if (lane == 0) stat_add(g, ST_MISSES, 1);
+  const bool own = g.repl == GFS_REPL_TB_LRA && stream >= 0 && (uint32_t)stream < g.paper_streams;
+  int f = own ? take_frame_lra(g, stream, seq0, key, deadline) : take_frame(g, false, seq0, key, deadline);
+  while (f < 0) {
+    int late = 0;
+    if (lane == 0) late = now_ns() > deadline;
+    if (bcast(late)) {
+      if (lane == 0) stat_add(g, ST_ENOMEM, 1);
+      return -kENOMEM;
+    }
+    if (!warp_help(g, (uint32_t)(p % g.rpc_slots))) {
+      if (lane == 0) __nanosleep(256);
+      __syncwarp();
+    }
+    f = own ? take_frame_lra(g, stream, seq0, key, deadline) : take_frame(g, false, seq0, key, deadline);
+  }
+  if (lane == 0) {
+    st_rlx64(&g.fkey[f], key);
+    st_rlx(&g.fconsumed[f], 0u);
+    st_rlx(&g.fwindow[f], 0u);
+    st_rlx(&g.fmark[f], 0u);
+    st_rlx(&g.fvalid[f], expected_valid(g, fi, p));
+    st_rlx64(&g.faseq[f], atomicAdd(&g.ctrl->alloc_counter.v, 1ull));
+    st_rlx(&g.fsrc[f], SRC_NONE);
+    __threadfence();
+    atomicAdd(&g.fpins[f], 1u);
+    st_rel(&g.fstate[f], FR_FILLING);
+  }
+  __syncwarp();
+  const int r = tab_insert(g, key, (uint32_t)f, deadline);
+  if (r != f) {  // another stream mapped p meanwhile: keep the frame, unused
+    if (lane == 0) {
+      atomicSub(&g.fpins[f], 1u);
+      st_rlx64(&g.fkey[f], KEY_NONE);
+      st_rel(&g.fstate[f], FR_EMPTY);
+      if (!own) fifo_push(g, (uint32_t)f, deadline);
+    }
+    __syncwarp();
+    return r < 0 ? r : -kEAGAIN;
+  }
+  if (lane == 0) {
+    if (fi.fetched) atomicOr(&fi.fetched[p >> 5], 1u << (p & 31));
+    job->kind = PJ_NONE;
+    job->f = f;
+    job->page = p;
+  }
+  // the stream's private buffer
+  PrivBuf pb{0, 0, 0};
+  if (stream >= 0 && (uint32_t)stream < g.paper_streams) pb = g.pmeta[stream];
+  if (pb.count && pb.fid == fid && p >= pb.first && p < pb.first + pb.count) {
+    if (lane == 0) {
+      job->kind = PJ_BUFFER;
+      job->src = ((unsigned long long)stream * g.ra_cap + (p - pb.first)) << g.page_shift;
+      stat_add(g, ST_BUFHITS, 1);
+    }
+    __syncwarp();
+    return f;
+  }
+  unsigned long long n = 1ull + g.ra_cap;
+  if (n > fi.npages - p) n = fi.npages - p;
+  if (n > g.max_rpc_pages) n = g.max_rpc_pages;
+  if (!(stream >= 0 && (uint32_t)stream < g.paper_streams)) n = 1;  // no buffer for this stream
+  unsigned long long t = 0;
+  const int rc = rpc_submit(g, fid, p, (uint32_t)n, n > 1 ? GFS_KIND_SYNC_RA : GFS_KIND_DEMAND, nullptr, deadline, &t);
+  if (rc < 0) {
+    if (lane == 0) frame_unpin(g, f);
+    return rc;
+  }
+  if (lane == 0) {
+    unsigned long long bytes = 0;
+    for (unsigned long long i = 0; i < n; ++i) {
+      bytes += expected_valid(g, fi, p + i);
+      if (g.fetch_count && fid == 0 && p + i < g.debug_pages) atomicAdd(&g.fetch_count[p + i], 1u);
+    }
+    stat_add(g, ST_PAGES, n);
+    stat_add(g, ST_BYTES, bytes);
+    if (n > 1) stat_add(g, ST_RA_SYNC, n - 1);
+    job->kind = PJ_REQUEST;
+    job->slot = (uint32_t)(t % g.rpc_slots);
+    job->t = t;
+    job->n = (uint32_t)n;
+  }
+  __syncwarp();
+  return f;
+}
+
+// Whole block: finish a paper-mode miss (copy the page from the private buffer,
+// or take every page of the request as the host publishes it: page p into its
+// frame, the rest into the private buffer).  Returns the frame state or -errno.
+static __device__ int block_paper_job(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi,
+                                      const PaperJob& j, unsigned long long deadline) {
+  __shared__ unsigned long long s_src;
+  __shared__ uint32_t s_buf, s_ok;
+  __shared__ int s_late;
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  uint8_t* frame = g.frames + ((size_t)j.f << g.page_shift);
+  if (j.kind == PJ_BUFFER) {
+    copy_in(g.pbuf + j.src, frame, ld_rlx(&g.fvalid[j.f]), tid, nt);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_rel(&g.fstate[j.f], FR_READY);
+    __syncthreads();
+    return FR_READY;
+  }
+  bool first_ok = false;
+  uint32_t good = 0;
+  bool run = true;
+  for (uint32_t i = 0; i < j.n; ++i) {
+    if (tid == 0) {
+      const PullPage* pp = &g.pages[(size_t)j.slot * g.max_rpc_pages + i];
+      int late = 0;
+      while (ld_acq_sys64(&pp->tag) != j.t + 1) {
+        if (now_ns() > deadline) {
+          late = 1;
+          stat_add(g, ST_TIMEOUTS, 1);
+          break;
+        }
+        __nanosleep(256);
+      }
+      s_late = late;
+      if (!late) {
+        s_src = ld_rlx64((const unsigned long long*)&pp->src);
+        s_buf = ld_rlx((const uint32_t*)&pp->buf);
+        s_ok = ld_rlx((const uint32_t*)&pp->ok);
+      }
+    }
+    __syncthreads();
+    if (s_late) {
+      __syncthreads();
+      return -kETIMEDOUT;
+    }
+    const bool ok = s_ok != 0;
+    const uint8_t* src = s_buf == BUF_MAPPED ? (const uint8_t*)s_src : g.staging + s_src;
+    const uint32_t bytes = expected_valid(g, fi, j.page + i);
+    if (ok) {
+      uint8_t* dst = i == 0 ? frame : g.pbuf + (((unsigned long long)stream * g.ra_cap + (i - 1)) << g.page_shift);
+      copy_in(src, dst, bytes, tid, nt);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0 && s_buf != BUF_MAPPED) {
+      __threadfence_system();
+      atomicAdd_system(&g.bcount[s_buf], 0xffffffffu);
+    }
+    if (i == 0) first_ok = ok;
+    else if (run && ok) ++good;
+    else run = false;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (stream >= 0 && (uint32_t)stream < g.paper_streams) {
+      PrivBuf pb;
+      pb.first = j.page + 1;
+      pb.fid = fid;
+      pb.count = good;
+      g.pmeta[stream] = pb;
+    }
+    __threadfence_system();
+    st_rel_sys64(&ring_slot(g, j.slot)->seq, j.t + g.rpc_slots);
+    atomicAdd(&g.ctrl->freed.v, 1ull);
+    st_rel(&g.fstate[j.f], first_ok ? (uint32_t)FR_READY : (uint32_t)FR_ERROR);
+  }
+  __syncthreads();
+  return first_ok ? (int)FR_READY : (int)FR_ERROR;
+}
+
 // Find or install page p and pin its frame for the caller (warp 0); does not
 // wait.  Returns the frame (its state in *state) or -errno.
 static __device__ int acquire_begin(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, unsigned long long p,
                              unsigned long long p1, unsigned long long seq0, unsigned long long deadline,
-                             uint32_t* s_frames, int* state) {
+                             uint32_t* s_frames, int* state, PaperJob* job) {
   const int lane = lane_id();
   const unsigned long long key = make_key(fid, p);
   for (;;) {
@@ -856,7 +1113,9 @@ static __device__ int acquire_begin(const DevHandle& g, int stream, uint32_t fid
       *state = st;
       return f;
     }
-    int r = handle_miss(g, stream, fid, fi, p, p1, seq0, deadline, s_frames);
+    const bool paper = g.mode == GFS_MODE_PAPER && fi.ra && g.xfer != GFS_XFER_DMA;
+    int r = paper ? handle_miss_paper(g, stream, fid, fi, p, seq0, deadline, job)
+                  : handle_miss(g, stream, fid, fi, p, p1, seq0, deadline, s_frames);
     if (r == -kEAGAIN) {
       if (lane == 0) stat_add(g, ST_RETRIES, 1);
       continue;
@@ -904,7 +1163,7 @@ static __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long 
 static __device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDev& fi, int f, unsigned long long seq0,
                            unsigned long long deadline, uint32_t* s_frames) {
   const int lane = lane_id();
-  if (!(g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra)) return;
+  if (!(g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra)) return;  // no marks in the other modes
   uint32_t m = 0, w = 0;
   if (lane == 0) {
     m = atomicExch(&g.fmark[f], 0u);
@@ -921,7 +1180,8 @@ static __device__ void release_page(const DevHandle& g, int f, uint32_t nbytes, 
   uint32_t v = ld_rlx(&g.fvalid[f]);
   bool push = c < v && c + nbytes >= v;
   frame_unpin(g, f);
-  if (push) fifo_push(g, (uint32_t)f, deadline);
+  // per-threadblock LRA queues (Section 5.1) replace the consumed FIFO entirely
+  if (push && g.repl != GFS_REPL_TB_LRA) fifo_push(g, (uint32_t)f, deadline);
 }
 
 // ---------------------------------------------------------------- copy-out
@@ -1037,6 +1297,7 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
                                 unsigned long long len, uint8_t* buf, Sums& acc) {
   __shared__ int s_frame, s_state;
   __shared__ unsigned long long s_seq0;
+  __shared__ PaperJob s_job;
   __shared__ uint32_t s_frames[MAX_RPC_PAGES];
   const uint32_t tid = threadIdx.x;
   if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
@@ -1052,9 +1313,11 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
   const unsigned long long deadline = now_ns() + g.timeout_ns;
   long long err = 0;
   for (unsigned long long p = p0; p <= p1; ++p) {
+    if (tid == 0) s_job.kind = PJ_NONE;
+    __syncthreads();
     if (tid < 32) {
       int st = 0;
-      int r = acquire_begin(g, stream, (uint32_t)fid, fi, p, p1, seq0, deadline, s_frames, &st);
+      int r = acquire_begin(g, stream, (uint32_t)fid, fi, p, p1, seq0, deadline, s_frames, &st, &s_job);
       if (tid == 0) {
         s_frame = r;
         s_state = st;
@@ -1063,12 +1326,14 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
     __syncthreads();
     const int f = s_frame;
     int st = s_state;
+    const PaperJob job = s_job;
     __syncthreads();
     if (f < 0) {
       err = f;
       break;
     }
-    if (st == FR_FILLING || st == FR_COPYING) st = block_wait_ready(g, f, deadline);
+    if (job.kind != PJ_NONE) st = block_paper_job(g, stream, (uint32_t)fid, fi, job, deadline);
+    else if (st == FR_FILLING || st == FR_COPYING) st = block_wait_ready(g, f, deadline);
     if (st != FR_READY) {
       if (tid == 0) {
         frame_unpin(g, f);

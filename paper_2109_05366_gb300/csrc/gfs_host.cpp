@@ -313,6 +313,7 @@ int gfs_shutdown(gfs_ctx* ctx) {
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   if (ctx->d_frames) cudaFree(ctx->d_frames);
   if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
+  if (ctx->d_paper) cudaFree(ctx->d_paper);
   if (ctx->d_out) cudaFree(ctx->d_out);
   if (ctx->h_out) cudaFreeHost(ctx->h_out);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -329,7 +330,9 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   const gfs_config c = *cfg_in;
   if (!is_pow2(c.page_size) || c.page_size < 4096 || c.page_size > (64u << 20)) return -EINVAL;
   if (c.cache_bytes < c.page_size) return -EINVAL;
-  if (c.mode > GFS_MODE_ONDEMAND || c.xfer > GFS_XFER_MAPPED) return -EINVAL;
+  if (c.mode > GFS_MODE_PAPER || c.xfer > GFS_XFER_MAPPED || c.replacement > GFS_REPL_TB_LRA) return -EINVAL;
+  if (c.mode == GFS_MODE_PAPER && c.xfer == GFS_XFER_DMA) return -ENOTSUP;  // the requesting block copies its pages
+  if (c.replacement == GFS_REPL_TB_LRA && c.mode != GFS_MODE_PAPER) return -EINVAL;
   if (c.rpc_slots < 1 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
   if (c.host_threads < 1 || c.host_threads > 256 || c.max_files < 1 || c.max_files > MAX_FILES) return -EINVAL;
   if (c.max_streams < 1 || c.timeout_ns == 0) return -EINVAL;
@@ -370,6 +373,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.slot_stride = slot_stride(c.max_rpc_pages);
   g.fifo_cap = F;
   g.xfer = c.xfer;
+  g.repl = c.replacement;
+  g.paper_streams = 0;
   g.nbufs = nbufs;
   g.chunk_bytes = chunk_bytes;
 
@@ -658,6 +663,11 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
   if (ctx->dev.fetch_count) CK(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, s));
   for (auto& f : ctx->files)
     if (f.open && f.d_fetched) CK(cudaMemsetAsync(f.d_fetched, 0, f.fetched_bytes, s));
+  if (ctx->dev.paper_streams) {  // private buffers and LRA queues start empty
+    CK(cudaMemsetAsync(ctx->dev.pmeta, 0, (size_t)ctx->dev.paper_streams * sizeof(PrivBuf), s));
+    CK(cudaMemsetAsync(ctx->dev.lra_head, 0, (size_t)ctx->dev.paper_streams * 4, s));
+    CK(cudaMemsetAsync(ctx->dev.lra_len, 0, (size_t)ctx->dev.paper_streams * 4, s));
+  }
   int rc = launch_reset(ctx->dev, s);
   if (rc) return rc;
   return cuda_err(cudaStreamSynchronize(s));
@@ -698,6 +708,7 @@ int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
   o->host_ns_pread = ctx->io->stats.ns_pread.load();
   o->host_ns_wait_buf = ctx->io->stats.ns_wait_buf.load();
   o->host_ns_idle = ctx->io->stats.ns_idle.load();
+  o->buffer_hits = st[ST_BUFHITS];
   return 0;
 }
 
@@ -742,6 +753,32 @@ int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* s
 
 }  // extern "C"
 
+int ensure_paper_state(gfs_ctx* ctx, uint32_t streams) {
+  if (ctx->cfg.mode != GFS_MODE_PAPER || streams <= ctx->dev.paper_streams) return 0;
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
+  cudaDeviceSynchronize();  // no kernel may still use the old state
+  if (ctx->d_paper) cudaFree(ctx->d_paper);
+  ctx->d_paper = nullptr;
+  ctx->dev.paper_streams = 0;
+  const uint32_t quota = std::max<uint32_t>(1, ctx->dev.n_frames / streams);
+  const size_t pbuf = std::max<size_t>(256, (size_t)streams * ctx->dev.ra_cap * ctx->cfg.page_size);
+  const size_t o_meta = align_up(pbuf, 256);
+  const size_t o_lra = o_meta + align_up((size_t)streams * sizeof(PrivBuf), 256);
+  const size_t o_head = o_lra + align_up((size_t)streams * quota * 4, 256);
+  const size_t o_len = o_head + align_up((size_t)streams * 4, 256);
+  const size_t total = o_len + align_up((size_t)streams * 4, 256);
+  CK(cudaMalloc((void**)&ctx->d_paper, total));
+  CK(cudaMemset(ctx->d_paper + o_meta, 0, total - o_meta));
+  ctx->dev.pbuf = ctx->d_paper;
+  ctx->dev.pmeta = (PrivBuf*)(ctx->d_paper + o_meta);
+  ctx->dev.lra = (uint32_t*)(ctx->d_paper + o_lra);
+  ctx->dev.lra_head = (uint32_t*)(ctx->d_paper + o_head);
+  ctx->dev.lra_len = (uint32_t*)(ctx->d_paper + o_len);
+  ctx->dev.quota = quota;
+  ctx->dev.paper_streams = streams;
+  return 0;
+}
+
 int ensure_scan_buf(gfs_ctx* ctx, size_t need) {
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
   if (need <= ctx->scan_buf_bytes) return 0;
@@ -772,6 +809,10 @@ static int scan_prepare(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint64_t*
     ctx->scan_buf_bytes = 0;
     CK(cudaMalloc((void**)&ctx->d_scan_buf, need));
     ctx->scan_buf_bytes = need;
+  }
+  {
+    int prc = ensure_paper_state(ctx, a->blocks);
+    if (prc) return prc;
   }
   *g = ctx->dev;
   const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
@@ -891,6 +932,8 @@ int gfs_read_many(gfs_ctx* ctx, int fid, uint32_t n, const uint64_t* d_off, cons
   if (!d_off || !d_len || !d_dst || !d_buf || !d_ret || blocks == 0) return -EINVAL;
   if (threads != 128 && threads != 256 && threads != 512) return -EINVAL;
   CK(cudaSetDevice(ctx->cfg.device));
+  int prc = ensure_paper_state(ctx, blocks);
+  if (prc) return prc;
   DevHandle g = ctx->dev;
   g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames : blocks + 1;
   return launch_read_many(g, fid, n, d_off, d_len, d_dst, d_buf, d_ret, blocks, threads, (cudaStream_t)stream);

@@ -51,6 +51,8 @@ int launch_pull_probe(const uint8_t* src, uint8_t* dst, uint64_t n, cudaStream_t
 struct gfs_ctx;
 // Grow the context's per-block gread buffers to at least `bytes` (before a launch).
 int ensure_scan_buf(gfs_ctx* ctx, size_t bytes);
+// GFS_MODE_PAPER: private buffers and LRA queues for `streams` streams (before a launch).
+int ensure_paper_state(gfs_ctx* ctx, uint32_t streams);
 namespace gfs {
 
 }  // namespace gfs
@@ -76,6 +78,7 @@ struct gfs_ctx {
   size_t scan_buf_bytes = 0;
   cudaGraphExec_t graph = nullptr;  // gfs_scan_graph: cached executable and its key
   unsigned long long graph_key[8] = {};
+  uint8_t* d_paper = nullptr;       // GFS_MODE_PAPER state (private buffers, metadata, LRA queues)
   uint8_t* d_out = nullptr;        // gfs_scan_host results: device side
   uint8_t* h_out = nullptr;        // and a pinned host copy
   size_t out_bytes = 0;

@@ -41,7 +41,7 @@ GFS_HD inline uint64_t key_page(uint64_t key) { return key & 0xffffffffull; }
 // Statistic slots in the device counter block (order = gfs_stats fields).
 enum : int {
   ST_GREADS = 0, ST_HITS, ST_MISSES, ST_COALESCED, ST_RPCS, ST_PAGES, ST_BYTES, ST_RA_SYNC, ST_RA_ASYNC,
-  ST_EVICT, ST_EVICT_UNCONSUMED, ST_RETRIES, ST_TIMEOUTS, ST_EIO, ST_ENOMEM, ST_COUNT
+  ST_EVICT, ST_EVICT_UNCONSUMED, ST_RETRIES, ST_TIMEOUTS, ST_EIO, ST_ENOMEM, ST_BUFHITS, ST_COUNT
 };
 
 // Control counters in device memory (one 128-byte line per hot counter).
@@ -77,6 +77,12 @@ struct PullPage {
   uint32_t buf;            // staging buffer (host thread * buffers per thread + k), or BUF_MAPPED
   uint32_t ok;
   uint32_t pad[2];
+};
+
+// GFS_MODE_PAPER: the pages a stream's private buffer holds ([first, first+count) of fid).
+struct PrivBuf {
+  unsigned long long first;
+  uint32_t fid, count;
 };
 
 // Per-file device state.
@@ -162,6 +168,15 @@ struct DevHandle {
   // gread latency trace (ns), lat_cap entries
   unsigned long long* lat;
   uint32_t lat_cap;
+  // GFS_MODE_PAPER: per-stream private buffers and per-stream LRA queues
+  uint32_t repl;                  // GFS_REPL_*
+  uint32_t paper_streams;         // streams (threadblocks) with state below
+  uint32_t quota;                 // frames per stream LRA queue
+  uint8_t* pbuf;                  // paper_streams * ra_cap pages
+  PrivBuf* pmeta;                 // per stream: which pages the private buffer holds
+  uint32_t* lra;                  // paper_streams * quota frames, ring per stream
+  uint32_t* lra_head;             // per stream: ring position of the oldest frame
+  uint32_t* lra_len;              // per stream: frames in the ring
 };
 
 }  // namespace gfs

@@ -284,6 +284,8 @@ extern "C" int gfs_serve_start(gfs_ctx* ctx, const gfs_serve_config* sc, void* s
     return -EINVAL;
   if ((int)sc->ctas > per_sm * sms) return -EINVAL;  // a persistent kernel must fit at once
   int rc = 0;
+  rc = ensure_paper_state(ctx, sc->ctas);
+  if (rc) return rc;
   gfs_server* s = new (std::nothrow) gfs_server();
   if (!s) return -ENOMEM;
   Handle& h = s->h;

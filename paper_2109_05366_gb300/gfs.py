@@ -16,7 +16,8 @@ import numpy as np
 from . import build as _build
 
 RDONLY, RDWR = 0, 2
-MODE_READAHEAD, MODE_ONDEMAND = 0, 1
+MODE_READAHEAD, MODE_ONDEMAND, MODE_PAPER = 0, 1, 2
+REPL_FIFO, REPL_TB_LRA = 0, 1
 ADV_NORMAL, ADV_SEQUENTIAL, ADV_RANDOM = 0, 1, 2
 XFER_DMA, XFER_PULL, XFER_MAPPED = 0, 1, 2
 KIND_DEMAND, KIND_SYNC_RA, KIND_ASYNC_RA = 0, 1, 2
@@ -30,7 +31,7 @@ class Config(ctypes.Structure):
                 ("ra_cap_pages", u32), ("async_ra", u32), ("reserve_frames", u32), ("rpc_slots", u32),
                 ("max_rpc_pages", u32), ("host_threads", u32), ("staging_bytes", u32), ("max_streams", u32),
                 ("max_files", u32), ("trace_capacity", u32), ("xfer", u32), ("debug_counts", u32),
-                ("device", i32), ("latency_capacity", u32), ("reserved", u32 * 6)]
+                ("device", i32), ("latency_capacity", u32), ("replacement", u32), ("reserved", u32 * 5)]
 
 
 class Stat(ctypes.Structure):
@@ -40,11 +41,12 @@ class Stat(ctypes.Structure):
 STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fetched", "bytes_fetched",
                 "ra_pages_sync", "ra_pages_async", "evictions", "unconsumed_evictions", "retries", "timeouts",
                 "eio", "enomem", "host_requests", "host_preads", "host_bytes", "host_copies", "host_errors",
-                "trace_rpc_count", "trace_evict_count", "host_ns_pread", "host_ns_wait_buf", "host_ns_idle"]
+                "trace_rpc_count", "trace_evict_count", "host_ns_pread", "host_ns_wait_buf", "host_ns_idle",
+                "buffer_hits"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 5)]
+    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 4)]
 
 
 class RpcRec(ctypes.Structure):

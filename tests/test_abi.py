@@ -43,9 +43,9 @@ def test_struct_layouts_match_header(tmp_path):
     # compile a C program against include/gfs.h and compare sizes/offsets with ctypes
     import ctypes
     import subprocess
-    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "reserved"]),
+    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "replacement", "reserved"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
-              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "reserved"]),
+              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
               ("gfs_evict_rec", gfs.EvictRec, ["new_fid", "new_page"]),
               ("gfs_scan_args", gfs.ScanArgs, ["read_len", "fused", "reserved"])]

@@ -299,3 +299,44 @@ def test_pull_partial_requests_are_helped(torch_cuda, gfs, datadir):
         torch_cuda.cuda.synchronize()
         _check_scan(gfs, path, 64 * KiB, *out)
         assert ctx.stats()["timeouts"] == 0
+
+
+# ------------------------------------------------ the paper's own design (Sections 4.1, 5.1)
+@pytest.mark.parametrize("xfer", [1, 2])
+@pytest.mark.parametrize("repl", [0, 1])
+@pytest.mark.parametrize("size,page,frames,blocks,stride,prefetch", [
+    (16 * MiB, 64 * KiB, 64, 4, 256 * KiB, 3),           # file fits
+    (24 * MiB + 999, 256 * KiB, 16, 6, 512 * KiB, 2),    # file 6x the cache
+])
+def test_paper_mode_serialized_logs_match_oracle(torch_cuda, gfs, datadir, xfer, repl, size, page, frames, blocks,
+                                                 stride, prefetch):
+    path = _file(datadir, 10, size)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=2, replacement=repl, ra_cap_pages=prefetch,
+                     trace_capacity=1 << 16, max_rpc_pages=16, xfer=xfer, reserve_frames=1,
+                     timeout_ns=2 * 10**9) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+        st = ctx.stats()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode="paper", ra_cap=prefetch, reserve=1,
+                               max_rpc_pages=16, replacement=("tb_lra" if repl else "fifo"))
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+    assert st["buffer_hits"] == sim.stats.buffer_hits
+
+
+@pytest.mark.parametrize("xfer", [1, 2])
+@pytest.mark.parametrize("repl", [0, 1])
+def test_paper_mode_concurrent_exact(torch_cuda, gfs, datadir, xfer, repl):
+    size = 128 * MiB + 4096
+    path = _file(datadir, 11, size)
+    with gfs.Context(cache_bytes=32 * MiB, page_size=64 * KiB, mode=2, replacement=repl, ra_cap_pages=15,
+                     max_rpc_pages=16, xfer=xfer, timeout_ns=2 * 10**9) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, MiB, blocks=96, threads=256)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, MiB, *out)
+        st = ctx.stats()
+        assert st["timeouts"] == 0 and st["buffer_hits"] > 0
