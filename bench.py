@@ -377,6 +377,74 @@ def run_cold(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's microbenchmarks on GB300 (Section 6.1), pread staging (pull) like its CPU threads.
+
+    E9: 120 blocks x 512 threads read 1 GiB of a 10 GiB file, each block its own strides;
+        original GPUfs (one page per request) at 4 KiB .. 1 MiB pages vs 4 KiB pages with
+        the paper's prefetcher and with this library's readahead.
+    E10: the same reading 4 GiB of the file through a 2 GiB cache: original vs
+        prefetcher only vs prefetcher + per-block LRA replacement vs this library.
+    """
+    import torch
+
+    from paper_2109_05366_gb300 import gfs
+    size = 10 * GiB
+    path = os.path.join(data_dir(), "gfs_paper_s4_%d.bin" % size)
+    ensure_input(path, 4, size)
+    stream = torch.cuda.Stream()
+    res = {"workload": "paper microbenchmarks: 120 blocks x 512 threads, per-block strides, pull transfer"}
+
+    def run(label, read_bytes, cache, page, mode, ra=8, repl=0, reps=2, stride=8 * MiB):
+        cfg = dict(cache_bytes=cache, page_size=page, mode=mode, ra_cap_pages=ra, replacement=repl,
+                   xfer=gfs.XFER_PULL, max_rpc_pages=min(256, ra + stride // page + 1), rpc_slots=512,
+                   max_streams=4096, timeout_ns=5 * 10**9)
+        try:
+            with gfs.Context(**cfg) as ctx:
+                fid = ctx.open(path)
+                # read the first read_bytes of the file: strides of `stride` bytes, block b takes b, b+120, ...
+                ns = read_bytes // stride
+                offs = torch.arange(ns, dtype=torch.int64, device="cuda") * stride
+                lens = torch.full((ns,), stride, dtype=torch.int64, device="cuda")
+                dsts = (torch.arange(ns, dtype=torch.int64, device="cuda") % 120) * stride
+                buf = torch.empty(120 * stride, dtype=torch.uint8, device="cuda")
+                ret = torch.empty(ns, dtype=torch.int64, device="cuda")
+                ts = []
+                for r in range(reps + 1):
+                    ctx.reset_cache(stream)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.read_many(fid, offs, lens, dsts, buf, ret, blocks=120, threads=512, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r:
+                        ts.append(e0.elapsed_time(e1) / 1e3)
+                st = ctx.stats(stream)
+                ok = bool((ret == stride).all().item())
+            res[label] = {"gbps": round(read_bytes / min(ts) / 1e9, 2), "rpcs": st["rpcs"],
+                          "pages_fetched": st["pages_fetched"], "buffer_hits": st["buffer_hits"],
+                          "evictions": st["evictions"], "ok": ok}
+        except Exception as e:  # report and go on
+            res[label] = {"error": str(e)}
+        print(json.dumps({label: res[label]}), flush=True)
+
+    # E9 (files fit: 2 GiB cache, read 1 GiB)
+    for page in (4 * KiB, 64 * KiB, MiB):
+        run("E9_original_page%dK" % (page // KiB), GiB, 2 * GiB, page, gfs.MODE_ONDEMAND)
+    for pf in (15, 255):
+        run("E9_paper_prefetcher_4K_prefetch%dK" % ((pf + 1) * 4), GiB, 2 * GiB, 4 * KiB, gfs.MODE_PAPER, ra=pf)
+        run("E9_readahead_4K_cap%dK" % ((pf + 1) * 4), GiB, 2 * GiB, 4 * KiB, gfs.MODE_READAHEAD, ra=pf)
+    # E10 (4 GiB through a 2 GiB cache)
+    for page in (4 * KiB, 64 * KiB):
+        k = page // KiB
+        run("E10_original_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_ONDEMAND)
+        run("E10_prefetcher_only_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_PAPER, ra=15)
+        run("E10_prefetcher_tb_lra_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_PAPER, ra=15, repl=1)
+        run("E10_readahead_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_READAHEAD, ra=15)
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -592,7 +660,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--sweep", choices=["cfg3", "cfg4", "cold"], default=None, help="run a sweep instead of the bench line")
+    ap.add_argument("--sweep", choices=["cfg3", "cfg4", "cold", "paper"], default=None, help="run a sweep instead of the bench line")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-step-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -604,6 +672,8 @@ def main():
         return run_cfg4(args)
     if args.sweep == "cold":
         return run_cold(args)
+    if args.sweep == "paper":
+        return run_paper(args)
     return run_gfs(args)
 
 
