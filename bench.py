@@ -102,6 +102,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest value of x over the ranks of the default process group (x itself alone)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(bytes_per_rank_step: int, steps: int, world: int, slowest_total_s: float) -> float:
+    """Whole-job GB/s: every rank moves its own bytes; the job takes as long as its slowest rank."""
+    return world * steps * bytes_per_rank_step / slowest_total_s / 1e9
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Weak scaling by file: rank r scans its own file, generated with seed + r."""
+    return seed + rank
+
+
 def ensure_input(path, seed, size):
     import inputs
     t0 = time.time()
@@ -494,8 +514,8 @@ def run_gfs(args):
     if args.blocks:
         blocks = args.blocks
     # weak scaling: every rank scans its own file (seed + rank), no data-path collective
-    path = os.path.join(data_dir(), "gfs_bench_s%d_%d.bin" % (seed + rank, size))
-    gen_s = ensure_input(path, seed + rank, size)
+    path = os.path.join(data_dir(), "gfs_bench_s%d_%d.bin" % (rank_seed(seed, rank), size))
+    gen_s = ensure_input(path, rank_seed(seed, rank), size)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     nstr = (size + stride - 1) // stride
@@ -541,13 +561,8 @@ def run_gfs(args):
             t0 = time.perf_counter()
             ctx.scan_host(fid, stride, blocks=blocks, threads=args.threads, fused=args.fused, stream=stream)
             e2e_t.append(time.perf_counter() - t0)
-    if world > 1:
-        tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = tt.item()
-    else:
-        total = sum(times)
-    value = world * args.steps * size / total / 1e9
+    total = max_over_ranks(sum(times), dist if world > 1 else None, dev)
+    value = job_rate(size, args.steps, world, total)
     res["readahead"] = value
 
     extra = {}

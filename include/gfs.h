@@ -81,7 +81,7 @@ typedef struct gfs_config {
   uint32_t ra_cap_pages;   /* Wmax: readahead pages beyond the demand run (Section 4.1 PREFETCH_SIZE / page) */
   uint32_t async_ra;       /* 1: asynchronous readahead at the readahead mark (Section 2.3); 0: synchronous only (Section 4.1) */
   uint32_t reserve_frames; /* frames readahead must leave for demand misses; 0 = B * ceil(len/P) + 1 per launch */
-  uint32_t rpc_slots;      /* request ring slots (Section 2.2 request queue; 128 in GPUfs) */
+  uint32_t rpc_slots;      /* request ring slots, 2 or more (Section 2.2 request queue; 128 in GPUfs) */
   uint32_t max_rpc_pages;  /* pages per request at most (1 .. 256) */
   uint32_t host_threads;   /* host I/O threads (Section 2.2; 4 in GPUfs) */
   uint32_t staging_bytes;  /* pinned staging per host thread and buffer (rounded up to whole pages) */
@@ -267,7 +267,7 @@ typedef struct gfs_serve_config {
   uint32_t threads;         /* 128, 256 or 512 */
   uint64_t unit_bytes;      /* bytes per unit of work (one gread) */
   uint32_t max_requests;    /* requests active at once */
-  uint32_t queue_slots;     /* submission and completion ring slots */
+  uint32_t queue_slots;     /* submission and completion ring slots (2 or more) */
   uint32_t units_in_flight; /* per-request reservation in units (0 = 16) */
   uint32_t frame_budget;    /* frames admission may reserve (0 = cache frames - ctas * pages per unit) */
   uint32_t idle_exit_ms;    /* the kernel ends after this long with no work (0 = 60 s) */

@@ -333,7 +333,9 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   if (c.mode > GFS_MODE_PAPER || c.xfer > GFS_XFER_MAPPED || c.replacement > GFS_REPL_TB_LRA) return -EINVAL;
   if (c.mode == GFS_MODE_PAPER && c.xfer == GFS_XFER_DMA) return -ENOTSUP;  // the requesting block copies its pages
   if (c.replacement == GFS_REPL_TB_LRA && c.mode != GFS_MODE_PAPER) return -EINVAL;
-  if (c.rpc_slots < 1 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
+  // a Vyukov ring needs 2 slots at least: with one, "published for ticket t" and
+  // "free for ticket t+1" are the same sequence value
+  if (c.rpc_slots < 2 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
   if (c.host_threads < 1 || c.host_threads > 256 || c.max_files < 1 || c.max_files > MAX_FILES) return -EINVAL;
   if (c.max_streams < 1 || c.timeout_ns == 0) return -EINVAL;
   const uint64_t F64 = c.cache_bytes / c.page_size;
@@ -371,7 +373,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.trace_cap = c.trace_capacity;
   g.rpc_slots = c.rpc_slots;
   g.slot_stride = slot_stride(c.max_rpc_pages);
-  g.fifo_cap = F;
+  g.fifo_cap = std::max<uint32_t>(F, 2);  // same sequence rule as the ring
   g.xfer = c.xfer;
   g.repl = c.replacement;
   g.paper_streams = 0;
@@ -389,7 +391,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
                o_fcons = take((size_t)F * 4), o_fvalid = take((size_t)F * 4), o_fwin = take((size_t)F * 4),
                o_fmark = take((size_t)F * 4), o_faseq = take((size_t)F * 8),
                o_tab = take((size_t)g.nbuckets * BUCKET * 8), o_tlock = take((size_t)g.nbuckets * 4),
-               o_tovf = take((size_t)g.nbuckets * 4), o_fifo = take((size_t)F * 8), o_ctrl = take(sizeof(Ctrl)),
+               o_tovf = take((size_t)g.nbuckets * 4), o_fifo = take((size_t)std::max<uint32_t>(F, 2) * 8), o_ctrl = take(sizeof(Ctrl)),
                o_files = take((size_t)c.max_files * sizeof(FileDev)),
                o_last = take((size_t)c.max_streams * c.max_files * 8),
                o_trpc = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_rpc_rec)),
@@ -1132,7 +1134,7 @@ int gfs_probe_pread(const char* path, uint32_t threads, uint64_t chunk, int reps
 int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests, uint32_t max_pages,
                       uint32_t threads, uint32_t slots, uint64_t seed, uint64_t* h_served) {
   if (!path || !is_pow2(page_size) || page_size < 16 || frames == 0 || max_pages == 0 ||
-      max_pages > MAX_RPC_PAGES || threads == 0 || threads > 64 || slots == 0 || seed == 0)
+      max_pages > MAX_RPC_PAGES || threads == 0 || threads > 64 || slots < 2 || seed == 0)
     return -EINVAL;
   int fd = open(path, O_RDONLY | O_CLOEXEC);
   if (fd < 0) return -errno;

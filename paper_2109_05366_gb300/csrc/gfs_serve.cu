@@ -275,7 +275,7 @@ extern "C" int gfs_serve_start(gfs_ctx* ctx, const gfs_serve_config* sc, void* s
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->server) return -EBUSY;
   if (sc->ctas == 0 || (sc->threads != 128 && sc->threads != 256 && sc->threads != 512) || sc->unit_bytes == 0 ||
-      sc->max_requests == 0 || sc->queue_slots == 0)
+      sc->max_requests == 0 || sc->queue_slots < 2)  // ring sequence rule: 2 slots at least
     return -EINVAL;
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
   int per_sm = 0, sms = 0;

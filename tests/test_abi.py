@@ -82,7 +82,7 @@ def test_init_rejects_bad_config_without_gpu():
 @pytest.mark.parametrize("page,frames,requests,max_pages,threads,slots,size", [
     (4096, 512, 2000, 16, 4, 32, (3 << 20) + 12345),
     (65536, 64, 400, 8, 8, 4, (5 << 20) + 1),
-    (4096, 64, 500, 1, 2, 1, 4096 * 10),
+    (4096, 64, 500, 1, 2, 2, 4096 * 10),
     (16384, 256, 300, 64, 16, 128, 7 * 16384 - 5),
 ])
 def test_ring_and_service_selftest(tmp_path, page, frames, requests, max_pages, threads, slots, size):
@@ -98,3 +98,10 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(gfs._build, "LIB", str(tmp_path / "nope.so"))
     with pytest.raises(gfs.GfsError):
         gfs.load(build_if_missing=False)
+
+
+def test_ring_needs_two_slots(tmp_path):
+    path = str(tmp_path / "f.bin")
+    inputs.write_file(path, 3, 4096 * 4)
+    with pytest.raises(gfs.GfsError):
+        gfs.selftest_ring(path, 4096, 16, 10, 1, 1, 1)
