@@ -116,7 +116,8 @@ typedef struct gfs_stats {
   uint64_t host_ns_wait_buf;  /* time waiting for a staging buffer to be copied out (pull) */
   uint64_t host_ns_idle;      /* time waiting for a request */
   uint64_t buffer_hits;       /* GFS_MODE_PAPER: misses served from the private buffer */
-  uint64_t reserved[4];
+  uint64_t host_controls;     /* opens and closes requested by the device (gopen, gclose) */
+  uint64_t reserved[3];
 } gfs_stats;
 
 /* One entry of the RPC trace: a request as the GPU issued it. */
@@ -162,7 +163,11 @@ int gfs_shutdown(gfs_ctx* ctx);
  * Readahead applies only with GFS_RDONLY (Section 4.4). */
 int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid);
 
-/* Close a file id; its cached pages stay until evicted or reset. */
+/* Close a file id and drop its cached pages, so that a file opened later under
+ * the same id never sees them.  Waits for the device and the host I/O threads
+ * to finish the requests in flight (no kernel of the context may be running or
+ * queued).  Also closes a file opened on the device (gopen), whatever its
+ * reference count. */
 int gfs_close(gfs_ctx* ctx, int fid);
 
 /* Set the access hint of a file (Section 4.4): GFS_ADV_RANDOM turns readahead off. */
@@ -243,6 +248,31 @@ int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d
  * and rebuilt when fid, args, reps or outputs change. */
 int gfs_scan_graph(gfs_ctx* ctx, int fid, const gfs_scan_args* args, uint32_t reps, int64_t* d_count,
                    uint64_t* d_sum, uint64_t* d_hash, void* stream);
+
+/* The stride scan with the file opened on the device: every threadblock calls
+ * gopen(path, GFS_RDONLY) (the open travels over the request ring to the host
+ * like a read, Section 2.2), gfstat for the size, greads its strides and calls
+ * gclose.  All threadblocks share one file id (host-side reference count).
+ * Outputs as gfs_scan, sized ceil(size/stride) for the size of `path` at the
+ * time of the call; if a threadblock's gopen fails, every stride of that block
+ * reports the error.  path: host string, at most GFS_PATH_MAX - 1 bytes.
+ * GFS_MODE_PAPER: -ENOTSUP.  A file closed on the device keeps its file id
+ * (and its cached pages) until gfs_reset_cache, or until gfs_open or gopen
+ * needs the id and drops the pages first (gfs_open at a quiet point only). */
+#define GFS_PATH_MAX 1024
+int gfs_scan_path(gfs_ctx* ctx, const char* path, const gfs_scan_args* args, int64_t* d_count,
+                  uint64_t* d_sum, uint64_t* d_hash, void* stream);
+
+/* Copy the context's device handle (the plain-data struct every kernel that
+ * calls the device API receives by value: gfs::DevHandle of
+ * csrc/gfs_internal.h; device functions gread, gopen, gclose, gfstat, gfadvise
+ * in csrc/gfs_device.cuh) into `out`, which holds `cap` bytes.  `blocks` and
+ * `read_len` size the readahead reserve (blocks * ceil(read_len / page) + 1
+ * frames kept free for demand misses) unless gfs_config.reserve_frames is set.
+ * Returns the handle's size in bytes; -ENOSPC (nothing copied) when cap is
+ * smaller.  The handle stays valid until gfs_shutdown; a later gfs_open does
+ * not change it. */
+int gfs_device_handle(gfs_ctx* ctx, uint32_t blocks, uint64_t read_len, void* out, uint64_t cap);
 
 /* n independent greads: request i reads [d_off[i], d_off[i]+d_len[i]) into
  * d_buf + d_dst[i] and writes its return value to d_ret[i]; `blocks`

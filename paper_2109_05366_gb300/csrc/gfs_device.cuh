@@ -33,7 +33,8 @@
 namespace gfs {
 namespace dev {
 
-constexpr int kEIO = 5, kEBADF = 9, kEAGAIN = 11, kENOMEM = 12, kEINVAL = 22, kETIMEDOUT = 110;
+constexpr int kEIO = 5, kEBADF = 9, kEAGAIN = 11, kENOMEM = 12, kEINVAL = 22, kEMFILE = 24, kENAMETOOLONG = 36,
+              kENOTSUP = 95, kETIMEDOUT = 110;
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -79,6 +80,11 @@ __device__ __forceinline__ unsigned long long ld_acq_sys64(const unsigned long l
   asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ uint32_t ld_acq_sys32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_rel_sys64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -110,6 +116,23 @@ __device__ __forceinline__ uint32_t expected_valid(const DevHandle& g, const Fil
   unsigned long long base = page << g.page_shift;
   unsigned long long rem = fi.size - base;
   return rem < g.page_size ? (uint32_t)rem : g.page_size;
+}
+
+// The file's device state, read with relaxed loads (the device API may have
+// rewritten it since this SM last read it).
+__device__ __forceinline__ FileDev load_file(const DevHandle& g, int fid) {
+  const FileDev* p = &g.files[fid];
+  FileDev f;
+  f.size = ld_rlx64(&p->size);
+  f.npages = ld_rlx64(&p->npages);
+  f.open = ld_rlx(&p->open);
+  f.ra = ld_rlx(&p->ra);
+  f.fetched = (uint32_t*)ld_rlx64((const unsigned long long*)&p->fetched);
+  f.flags = ld_rlx(&p->flags);
+  f.advice = ld_rlx(&p->advice);
+  f.mapped = ld_rlx(&p->mapped);
+  f.pad = 0;
+  return f;
 }
 
 // ---------------------------------------------------------------- page table
@@ -603,21 +626,26 @@ static __device__ bool block_help(const DevHandle& g, int target, bool any) {
 }
 
 // ---------------------------------------------------------------- request ring
-static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
-                          const uint32_t* s_frames, unsigned long long deadline, unsigned long long* ticket_out = nullptr) {
+// Take the next ticket of the ring and wait until its slot is free for this
+// lap (one warp).  Returns 0 with *t and *si set, or -ETIMEDOUT; a ticket once
+// taken is always published by the caller.
+static __device__ int ring_acquire(const DevHandle& g, unsigned long long* t_out, uint32_t* si_out,
+                                   unsigned long long deadline) {
   const int lane = lane_id();
   unsigned long long t = 0;
   if (lane == 0) t = atomicAdd(&g.ctrl->ring_tail.v, 1ull);
   t = bcast64(t);
   const uint32_t si = (uint32_t)(t % g.rpc_slots);
   RingSlot* s = ring_slot(g, si);
+  *t_out = t;
+  *si_out = si;
   for (unsigned ns = 64;;) {  // wait until the slot is free for this lap
     int free_ = 0, late = 0;
     if (lane == 0) {
       free_ = ld_acq_sys64(&s->seq) == t;
       late = now_ns() > deadline;
     }
-    if (bcast(free_)) break;
+    if (bcast(free_)) return 0;
     if (bcast(late)) {
       if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
       return -kETIMEDOUT;
@@ -628,6 +656,16 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
     __syncwarp();
     if (ns < 2048) ns <<= 1;
   }
+}
+
+static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
+                          const uint32_t* s_frames, unsigned long long deadline, unsigned long long* ticket_out = nullptr) {
+  const int lane = lane_id();
+  unsigned long long t = 0;
+  uint32_t si = 0;
+  const int arc = ring_acquire(g, &t, &si, deadline);
+  if (arc) return arc;
+  RingSlot* s = ring_slot(g, si);
   if (g.xfer != GFS_XFER_DMA && !s_frames) {  // paper mode: the requesting block copies every page itself
     if (lane == 0) {
       st_rlx64(&g.dticket[si], t);
@@ -656,7 +694,7 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
     st_sys32(&s->npages, n);
     st_sys64(&s->page_lo, page_lo);
     st_sys32(&s->kind, kind);
-    st_sys32(&s->op, 1u);
+    st_sys32(&s->op, OP_READ);
     st_sys64(&s->issue_ns, now_ns());
   }
   __syncwarp();
@@ -1301,7 +1339,7 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
   __shared__ uint32_t s_frames[MAX_RPC_PAGES];
   const uint32_t tid = threadIdx.x;
   if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
-  const FileDev fi = g.files[fid];
+  const FileDev fi = load_file(g, fid);
   if (!fi.open) return -kEBADF;
   if (tid == 0) stat_add(g, ST_GREADS, 1);
   if (off >= fi.size || len == 0) return 0;
@@ -1368,10 +1406,187 @@ __device__ __forceinline__ long long gread(const DevHandle& g, int stream, int f
   return gread_impl<false>(g, stream, fid, off, len, (uint8_t*)buf, unused);
 }
 
-// File size of an open fid, or -EBADF.
+// File size of an open fid, or -EBADF.  Any thread.
 __device__ __forceinline__ long long gfstat_size(const DevHandle& g, int fid) {
-  if (fid < 0 || (uint32_t)fid >= g.max_files || !g.files[fid].open) return -kEBADF;
-  return (long long)g.files[fid].size;
+  if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
+  const FileDev fi = load_file(g, fid);
+  return fi.open ? (long long)fi.size : -kEBADF;
+}
+
+// ---------------------------------------------------------------- open / close / stat / hint
+// Section 2.2: GPUfs gives GPU threads the POSIX-like calls open, read, close
+// and fstat; open and close go to the host over the same queue as reads.  The
+// access hint of Section 4.4 travels the same way.
+
+// One control request over the ring (one warp).  The host answers in the
+// slot's CtlMsg; the warp waits for the answer (helping with served pages in
+// the GPU copy transfers) and then frees the slot itself.  Returns 0 with
+// *status / *last set, or -ETIMEDOUT.
+static __device__ int rpc_control(const DevHandle& g, uint32_t op, uint32_t fid, uint32_t arg, const char* path,
+                                  uint32_t path_len, int* status, uint32_t* last, unsigned long long deadline) {
+  const int lane = lane_id();
+  unsigned long long t = 0;
+  uint32_t si = 0;
+  const int arc = ring_acquire(g, &t, &si, deadline);
+  if (arc) return arc;
+  RingSlot* s = ring_slot(g, si);
+  CtlMsg* m = reinterpret_cast<CtlMsg*>(s->frames);
+  if (op == OP_OPEN) {
+    char* dst = g.paths + (size_t)si * GFS_PATH_MAX;
+    for (uint32_t i = lane; i <= path_len; i += 32) dst[i] = i < path_len ? path[i] : '\0';
+  }
+  if (lane == 0) {
+    if (g.xfer != GFS_XFER_DMA) {  // no pages: helpers skip the slot
+      st_rlx64(&g.dticket[si], t);
+      st_rlx(&g.dnpages[si], 0u);
+      st_rlx(&g.dcopied[si], 0u);
+    }
+    st_sys32(&m->done, 0u);
+    st_sys32(&m->arg, arg);
+    st_sys32(&s->fid, fid);
+    st_sys32(&s->npages, 0u);
+    st_sys64(&s->page_lo, 0ull);
+    st_sys32(&s->kind, 0u);
+    st_sys32(&s->op, op);
+    st_sys64(&s->issue_ns, now_ns());
+  }
+  __syncwarp();
+  __threadfence_system();
+  __syncwarp();
+  if (lane == 0) st_rel_sys64(&s->seq, t + 1);
+  __syncwarp();
+  for (unsigned ns = 256;;) {
+    int done = 0, late = 0;
+    if (lane == 0) {
+      done = ld_acq_sys32(&m->done) == 1u;
+      late = now_ns() > deadline;
+    }
+    if (bcast(done)) break;
+    if (bcast(late)) {  // the slot stays taken: the ring reports the loss through later timeouts
+      if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
+      return -kETIMEDOUT;
+    }
+    if (g.xfer != GFS_XFER_DMA && warp_help(g, si)) continue;
+    if (lane == 0) __nanosleep(ns);
+    __syncwarp();
+    if (ns < 4096) ns <<= 1;
+  }
+  int st = 0;
+  uint32_t ls = 0;
+  if (lane == 0) {
+    const volatile CtlMsg* vm = m;
+    st = vm->status;
+    ls = vm->last;
+    __threadfence_system();
+    st_rel_sys64(&s->seq, t + g.rpc_slots);  // the slot is free for the next lap
+    atomicAdd(&g.ctrl->freed.v, 1ull);
+  }
+  *status = bcast(st);
+  *last = (uint32_t)bcast((int)ls);
+  return 0;
+}
+
+// Threadblock-collective control call: warp 0 runs it, every thread gets the result.
+static __device__ int block_control(const DevHandle& g, uint32_t op, uint32_t fid, uint32_t arg, const char* path,
+                                    uint32_t path_len) {
+  __shared__ int s_ret;
+  if (threadIdx.x < 32) {
+    int st = 0;
+    uint32_t last = 0;
+    int rc = rpc_control(g, op, fid, arg, path, path_len, &st, &last, now_ns() + g.timeout_ns);
+    if (threadIdx.x == 0) s_ret = rc ? rc : st;
+  }
+  __syncthreads();
+  const int ret = s_ret;
+  __syncthreads();
+  return ret;
+}
+
+// Threadblock-collective open (every thread, same arguments).  `path` is a
+// NUL-terminated string the device can read, shorter than GFS_PATH_MAX.
+// Opening a path that blocks already hold open on the device (same flags)
+// returns the same fid and adds a reference.  Returns the fid or -errno
+// (-EINVAL, -ENAMETOOLONG, -EMFILE, -ENOTSUP in GFS_MODE_PAPER, host open
+// errors, -ETIMEDOUT).
+static __device__ int gopen(const DevHandle& g, const char* path, int flags) {
+  if (g.mode == GFS_MODE_PAPER) return -kENOTSUP;
+  if (!path || (flags != GFS_RDONLY && flags != GFS_RDWR)) return -kEINVAL;
+  __shared__ uint32_t s_len;
+  if (threadIdx.x == 0) {  // one reader: the string's allocation may end at its terminator
+    uint32_t len = 0;
+    while (len < GFS_PATH_MAX && path[len] != '\0') ++len;
+    s_len = len;
+  }
+  __syncthreads();
+  const uint32_t len = s_len;
+  __syncthreads();
+  if (len == 0) return -kEINVAL;
+  if (len >= GFS_PATH_MAX) return -kENAMETOOLONG;
+  return block_control(g, OP_OPEN, 0u, (uint32_t)flags, path, len);
+}
+
+// Threadblock-collective close of a fid opened with gopen.  After the last
+// reference the fid reads as closed; its pages stay cached, unreachable, until
+// the host drops them (gfs_reset_cache, or reuse of the fid).  Returns 0 or
+// -errno (-EBADF for a fid not opened on the device).
+static __device__ int gclose(const DevHandle& g, int fid) {
+  if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
+  return block_control(g, OP_CLOSE, (uint32_t)fid, 0u, nullptr, 0u);
+}
+
+// Threadblock-collective access hint (Section 4.4): GFS_ADV_RANDOM turns
+// readahead off for the fid, NORMAL and SEQUENTIAL turn it back on for
+// read-only opens.  Applies to greads that start after the call returns, in
+// every block.  Returns 0 or -errno.
+static __device__ int gfadvise(const DevHandle& g, int fid, int advice) {
+  if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
+  if (advice < GFS_ADV_NORMAL || advice > GFS_ADV_RANDOM) return -kEINVAL;
+  return block_control(g, OP_ADVISE, (uint32_t)fid, (uint32_t)advice, nullptr, 0u);
+}
+
+// fstat of an open fid (any thread).  Returns 0 or -EBADF.
+__device__ __forceinline__ int gfstat(const DevHandle& g, int fid, gfs_stat* st) {
+  if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;
+  const FileDev fi = load_file(g, fid);
+  if (!fi.open) return -kEBADF;
+  st->size = fi.size;
+  st->page_size = g.page_size;
+  st->flags = fi.flags;
+  st->advice = fi.advice;
+  st->mapped = fi.mapped;
+  return 0;
+}
+
+// Drop every cached page of `fid` (host close).  Runs only while no other
+// kernel of the context runs and no request is in flight: nothing is pinned or
+// filling, and a READY frame is in the consumed FIFO exactly when it is fully
+// consumed.  Warp `w` of `nw` takes frames w, w + nw, ...  Dropped frames
+// become keyless EMPTY frames in the consumed FIFO (victim class 2).
+static __device__ void purge_fid(const DevHandle& g, uint32_t fid, uint32_t w, uint32_t nw,
+                                 unsigned long long deadline) {
+  const int lane = lane_id();
+  for (uint32_t f = w; f < g.n_frames; f += nw) {
+    unsigned long long key = 0;
+    if (lane == 0) key = ld_rlx64(&g.fkey[f]);
+    key = bcast64(key);
+    if (key == KEY_NONE || key_fid(key) != fid) continue;
+    tab_remove(g, key, f, deadline);
+    if (lane == 0) {
+      const uint32_t st = ld_rlx(&g.fstate[f]);
+      const uint32_t valid = ld_rlx(&g.fvalid[f]);
+      const bool queued = g.repl == GFS_REPL_FIFO && st == FR_READY && valid > 0 && ld_rlx(&g.fconsumed[f]) >= valid;
+      st_rlx64(&g.fkey[f], KEY_NONE);
+      st_rlx(&g.fconsumed[f], 0u);
+      st_rlx(&g.fvalid[f], 0u);
+      st_rlx(&g.fwindow[f], 0u);
+      st_rlx(&g.fmark[f], 0u);
+      st_rlx64(&g.faseq[f], ~0ull);
+      if (g.fsrc) st_rlx(&g.fsrc[f], SRC_NONE);
+      st_rel(&g.fstate[f], FR_EMPTY);
+      if (!queued) fifo_push(g, f, deadline);
+    }
+    __syncwarp();
+  }
 }
 
 }  // namespace dev

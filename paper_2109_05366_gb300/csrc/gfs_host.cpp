@@ -190,6 +190,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
   if (fid >= ctx->files.size()) return false;
+  std::lock_guard<std::mutex> lk(ctx->files_mu);
   const HostFile& f = ctx->files[fid];
   if (!f.open) return false;
   out->fd = f.fd;
@@ -237,15 +238,228 @@ void unmap_file(HostFile& hf) {
   hf.dev_map = 0;
 }
 
-int push_file(gfs_ctx* ctx, int fid) {
-  const HostFile& hf = ctx->files[fid];
+FileDev make_filedev(gfs_ctx* ctx, const HostFile& hf) {
   FileDev fd{};
   fd.size = hf.size;
   fd.npages = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
   fd.open = hf.open ? 1u : 0u;
   fd.ra = (hf.open && (hf.flags & 3) == GFS_RDONLY && hf.advice != GFS_ADV_RANDOM) ? 1u : 0u;
   fd.fetched = hf.open ? hf.d_fetched : nullptr;
+  fd.flags = (uint32_t)hf.flags;
+  fd.advice = (uint32_t)hf.advice;
+  fd.mapped = hf.open && hf.map ? 1u : 0u;
+  return fd;
+}
+
+// Write a file's device state (host API calls: the device is not waiting).
+int push_file(gfs_ctx* ctx, int fid) {
+  const FileDev fd = make_filedev(ctx, ctx->files[fid]);
   CK(cudaMemcpy(ctx->dev.files + fid, &fd, sizeof(fd), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+// The same from a host I/O thread while kernels run: a copy on the control
+// stream (non-blocking, so it waits for no kernel), finished before the caller
+// answers the device.  Caller holds dev_open_mu (h_ctl_fd is one buffer).
+int push_file_async(gfs_ctx* ctx, int fid) {
+  FileDev fd;
+  {
+    std::lock_guard<std::mutex> lk(ctx->files_mu);
+    fd = make_filedev(ctx, ctx->files[fid]);
+  }
+  cudaSetDevice(ctx->cfg.device);
+  memcpy(ctx->h_ctl_fd, &fd, sizeof(fd));
+  CK(cudaMemcpyAsync(ctx->dev.files + fid, ctx->h_ctl_fd, sizeof(fd), cudaMemcpyHostToDevice, ctx->ctl_stream));
+  return cuda_err(cudaStreamSynchronize(ctx->ctl_stream));
+}
+
+// Free what a file id holds and make it reusable.  No kernel may use it.
+void release_file(gfs_ctx* ctx, int fid) {
+  HostFile& hf = ctx->files[fid];
+  unmap_file(hf);
+  if (hf.d_fetched) {
+    if (hf.fetched_async) {
+      cudaFreeAsync(hf.d_fetched, ctx->ctl_stream);
+      cudaStreamSynchronize(ctx->ctl_stream);
+    } else {
+      cudaFree(hf.d_fetched);
+    }
+  }
+  if (hf.fd >= 0) close(hf.fd);
+  std::lock_guard<std::mutex> lk(ctx->files_mu);
+  hf = HostFile();
+}
+
+// Wait until every request issued so far has been served and (GPU copy
+// transfers) copied out of staging: the cache is quiet afterwards.  The
+// caller has synchronised the kernels that issue requests.
+int quiesce(gfs_ctx* ctx, cudaStream_t s) {
+  unsigned long long tail = 0;
+  CK(cudaMemcpy(&tail, &ctx->dev.ctrl->ring_tail.v, 8, cudaMemcpyDeviceToHost));
+  const double t0 = now_s();
+  while (ctx->io->served() < tail) {
+    if (now_s() - t0 > (double)ctx->cfg.timeout_ns * 1e-9 + 5.0) return -ETIMEDOUT;
+    usleep(50);
+  }
+  ctx->io->drain_sinks();
+  if (ctx->cfg.xfer != GFS_XFER_DMA) {  // copy out what was served but never read
+    int rc = launch_drain(ctx->dev, s);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    unsigned long long freed = 0;
+    CK(cudaMemcpy(&freed, &ctx->dev.ctrl->freed.v, 8, cudaMemcpyDeviceToHost));
+    if (freed < tail) return -ETIMEDOUT;
+  }
+  return 0;
+}
+
+// Drop the cached pages of a file id (device and host quiet).  The paper mode's
+// private buffers and LRA queues are not per file: that mode clears the cache.
+int purge_pages(gfs_ctx* ctx, int fid) {
+  if (ctx->cfg.mode == GFS_MODE_PAPER) return gfs_reset_cache(ctx, nullptr);
+  int rc = launch_purge(ctx->dev, (uint32_t)fid, nullptr);
+  if (rc) return rc;
+  return cuda_err(cudaStreamSynchronize(nullptr));
+}
+
+// Open, close or hint requested by the device (a host I/O thread; Section
+// 2.2).  Blocks holding a path open share one id; an id whose last device
+// reference is gone is retired: its pages may still be cached, so it is not
+// reused until they are dropped at a quiet point.  Every change reaches the
+// file's device state before the answer.
+void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const char* path, CtlMsg* m) {
+  std::lock_guard<std::mutex> dl(ctx->dev_open_mu);
+  m->last = 0;
+  if (op == OP_CLOSE || op == OP_ADVISE) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->files_mu);
+      const bool ok = fid < ctx->files.size() && ctx->files[fid].open &&
+                      (op == OP_ADVISE || (ctx->files[fid].by_device && ctx->files[fid].dev_refs > 0));
+      if (!ok) {
+        m->status = -EBADF;
+        return;
+      }
+      if (op == OP_ADVISE && arg > GFS_ADV_RANDOM) {
+        m->status = -EINVAL;
+        return;
+      }
+      HostFile& hf = ctx->files[fid];
+      if (op == OP_ADVISE) {
+        hf.advice = (int)arg;
+      } else if (--hf.dev_refs == 0) {
+        hf.open = false;
+        hf.retired = true;
+        m->last = 1;
+      }
+    }
+    m->status = (op == OP_ADVISE || m->last) ? push_file_async(ctx, (int)fid) : 0;
+    return;
+  }
+  if (op != OP_OPEN) {
+    m->status = -EINVAL;
+    return;
+  }
+  const uint32_t mode = arg & 3u;
+  if (arg != mode || (mode != GFS_RDONLY && mode != GFS_RDWR)) {
+    m->status = -EINVAL;
+    return;
+  }
+  const uint32_t P = ctx->cfg.page_size;
+  int slot = -1;
+  {
+    std::lock_guard<std::mutex> lk(ctx->files_mu);
+    for (size_t i = 0; i < ctx->files.size(); ++i) {
+      HostFile& hf = ctx->files[i];
+      if (hf.open && hf.by_device && hf.path == path && (uint32_t)hf.flags == arg) {
+        ++hf.dev_refs;
+        m->status = (int32_t)i;
+        return;
+      }
+    }
+    for (size_t i = 0; i < ctx->files.size(); ++i) {
+      HostFile& hf = ctx->files[i];
+      if (!hf.open && !hf.retired && !hf.opening) {
+        hf.opening = true;
+        slot = (int)i;
+        break;
+      }
+    }
+  }
+  if (slot < 0) {
+    m->status = -EMFILE;
+    return;
+  }
+  auto give_back = [&](int err) {
+    std::lock_guard<std::mutex> lk(ctx->files_mu);
+    ctx->files[slot].opening = false;
+    m->status = err;
+  };
+  const int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return give_back(-errno);
+  struct stat st;
+  if (fstat(fd, &st) != 0) {
+    const int e = errno;
+    close(fd);
+    return give_back(-e);
+  }
+  const uint64_t size = (uint64_t)st.st_size;
+  const uint64_t np = (size + P - 1) >> ctx->dev.page_shift;
+  const size_t fbytes = (size_t)((np + 31) / 32) * 4;
+  uint32_t* bits = nullptr;
+  if (fbytes) {  // stream-ordered on the control stream: nothing waits for the running kernels
+    cudaSetDevice(ctx->cfg.device);
+    if (cudaMallocAsync((void**)&bits, fbytes, ctx->ctl_stream) != cudaSuccess ||
+        cudaMemsetAsync(bits, 0, fbytes, ctx->ctl_stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->ctl_stream) != cudaSuccess) {
+      cudaGetLastError();
+      if (bits) {
+        cudaFreeAsync(bits, ctx->ctl_stream);
+        cudaStreamSynchronize(ctx->ctl_stream);
+      }
+      close(fd);
+      return give_back(-ENOMEM);
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->files_mu);
+    HostFile& hf = ctx->files[slot];
+    hf.fd = fd;
+    hf.size = size;
+    hf.flags = (int)arg;
+    hf.advice = GFS_ADV_NORMAL;
+    hf.path = path;
+    hf.d_fetched = bits;
+    hf.fetched_bytes = fbytes;
+    hf.fetched_async = true;
+    hf.by_device = true;
+    hf.dev_refs = 1;
+    hf.opening = false;
+    hf.open = true;
+  }
+  const int rc = push_file_async(ctx, slot);
+  if (rc) {  // the id stays retired: its device state is unknown
+    std::lock_guard<std::mutex> lk(ctx->files_mu);
+    ctx->files[slot].open = false;
+    ctx->files[slot].retired = true;
+    m->status = rc;
+    return;
+  }
+  m->status = slot;
+}
+
+// Drop the pages of every retired id and make the ids reusable (quiet point;
+// `cleared`: the whole cache was just reset, nothing to drop).
+int reclaim_retired(gfs_ctx* ctx, bool cleared) {
+  for (size_t i = 0; i < ctx->files.size(); ++i) {
+    if (!ctx->files[i].retired) continue;
+    if (!cleared) {
+      int rc = purge_pages(ctx, (int)i);
+      if (rc) return rc;
+    }
+    release_file(ctx, (int)i);
+    int rc = push_file(ctx, (int)i);
+    if (rc) return rc;
+  }
   return 0;
 }
 
@@ -267,7 +481,9 @@ const char* gfs_strerror(int err) {
     case ENOSYS: return "stream memory operations unavailable";
     case EMFILE: return "too many open files";
     case EAGAIN: return "resource temporarily unavailable";
-    case ENOTSUP: return "not supported with this transfer";
+    case ENOTSUP: return "not supported with this transfer or mode";
+    case ENOSPC: return "does not fit the fixed-size buffer";
+    case ENAMETOOLONG: return "path too long";
     default: return strerror(-err);
   }
 }
@@ -305,11 +521,10 @@ int gfs_shutdown(gfs_ctx* ctx) {
     ctx->io = nullptr;
   }
   cudaDeviceSynchronize();
-  for (auto& f : ctx->files) {
-    unmap_file(f);
-    if (f.d_fetched) cudaFree(f.d_fetched);
-    if (f.fd >= 0) close(f.fd);
-  }
+  for (size_t i = 0; i < ctx->files.size(); ++i) release_file(ctx, (int)i);
+  if (ctx->ctl_stream) cudaStreamDestroy(ctx->ctl_stream);
+  if (ctx->h_paths) cudaFreeHost(ctx->h_paths);
+  if (ctx->h_ctl_fd) cudaFreeHost(ctx->h_ctl_fd);
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   if (ctx->d_frames) cudaFree(ctx->d_frames);
   if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
@@ -483,6 +698,19 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
     return rc;
   }
   g.ring = (uint8_t*)d_ring;
+  // path buffers of device opens (one per slot) and the stream their allocations use
+  rc = cuda_err(cudaHostAlloc((void**)&ctx->h_paths, (size_t)c.rpc_slots * GFS_PATH_MAX,
+                              cudaHostAllocMapped | cudaHostAllocPortable));
+  void* d_paths = nullptr;
+  if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&d_paths, ctx->h_paths, 0));
+  if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&ctx->ctl_stream, cudaStreamNonBlocking));
+  if (!rc) rc = cuda_err(cudaHostAlloc((void**)&ctx->h_ctl_fd, sizeof(FileDev), cudaHostAllocPortable));
+  if (rc) {
+    gfs_shutdown(ctx);
+    return rc;
+  }
+  memset(ctx->h_paths, 0, (size_t)c.rpc_slots * GFS_PATH_MAX);
+  g.paths = (char*)d_paths;
 
   ctx->files.resize(c.max_files);
   rc = launch_reset(g, 0);
@@ -501,6 +729,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.staging_pages = std::max<uint32_t>(1, c.staging_bytes / c.page_size);
   sc.threads = c.host_threads;
   sc.n_frames = F;
+  sc.paths = ctx->h_paths;
   if (c.xfer != GFS_XFER_DMA) {
     sc.pull_arena = ctx->h_staging;
     sc.pull_done = ctx->h_done;
@@ -522,7 +751,10 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
         }
         return s;
       },
-      [ctx](uint32_t fid, FileView* fv) { return file_lookup(ctx, fid, fv); });
+      [ctx](uint32_t fid, FileView* fv) { return file_lookup(ctx, fid, fv); },
+      [ctx](uint32_t op, uint32_t fid, uint32_t arg, const char* path, CtlMsg* m) {
+        device_control(ctx, op, fid, arg, path, m);
+      });
   rc = ctx->io->start();
   if (rc) {
     gfs_shutdown(ctx);
@@ -542,29 +774,54 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
   if (!ctx || !path || !fid) return -EINVAL;
   if ((flags & 3) != GFS_RDONLY && (flags & 3) != GFS_RDWR) return -EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  int slot = -1;
-  for (size_t i = 0; i < ctx->files.size(); ++i)
-    if (!ctx->files[i].open) {
-      slot = (int)i;
-      break;
+  CK(cudaSetDevice(ctx->cfg.device));
+  auto pick = [ctx]() {
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    for (size_t i = 0; i < ctx->files.size(); ++i) {
+      HostFile& f = ctx->files[i];
+      if (!f.open && !f.retired && !f.opening) {
+        f.opening = true;
+        return (int)i;
+      }
     }
-  if (slot < 0) return -EMFILE;
+    return -1;
+  };
+  int slot = pick();
+  if (slot < 0) {  // ids closed on the device: drop their pages now and reuse them
+    bool any = false;
+    for (auto& f : ctx->files) any = any || f.retired;
+    if (!any) return -EMFILE;
+    CK(cudaDeviceSynchronize());
+    int rc = quiesce(ctx, nullptr);
+    if (!rc) rc = reclaim_retired(ctx, false);
+    if (rc) return rc;
+    slot = pick();
+    if (slot < 0) return -EMFILE;
+  }
   int fd = open(path, O_RDONLY | O_CLOEXEC);
-  if (fd < 0) return -errno;
+  if (fd < 0) {
+    const int e = errno;
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    ctx->files[slot].opening = false;
+    return -e;
+  }
   struct stat st;
   if (fstat(fd, &st) != 0) {
     int e = errno;
     close(fd);
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    ctx->files[slot].opening = false;
     return -e;
   }
   HostFile& hf = ctx->files[slot];
-  hf.fd = fd;
-  hf.size = (uint64_t)st.st_size;
-  hf.flags = flags;
-  hf.advice = GFS_ADV_NORMAL;
-  hf.open = true;
-  hf.path = path;
-  CK(cudaSetDevice(ctx->cfg.device));
+  {
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    hf.fd = fd;
+    hf.size = (uint64_t)st.st_size;
+    hf.flags = flags;
+    hf.advice = GFS_ADV_NORMAL;
+    hf.path = path;
+  }
   if (ctx->cfg.xfer == GFS_XFER_MAPPED) map_file(hf);  // falls back to pread staging when it fails
   {
     const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
@@ -572,10 +829,7 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
     if (hf.fetched_bytes) {
       if (cudaMalloc((void**)&hf.d_fetched, hf.fetched_bytes) != cudaSuccess ||
           cudaMemset(hf.d_fetched, 0, hf.fetched_bytes) != cudaSuccess) {
-        if (hf.d_fetched) cudaFree(hf.d_fetched);
-        unmap_file(hf);
-        close(fd);
-        hf = HostFile();
+        release_file(ctx, slot);
         return -ENOMEM;
       }
     }
@@ -591,12 +845,14 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
       ctx->dev.debug_pages = (uint32_t)std::min<uint64_t>(np, 0xffffffffull);
     }
   }
+  {
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    hf.opening = false;
+    hf.open = true;
+  }
   int rc = push_file(ctx, slot);
   if (rc) {
-    if (hf.d_fetched) cudaFree(hf.d_fetched);
-    unmap_file(hf);
-    close(fd);
-    hf = HostFile();
+    release_file(ctx, slot);
     return rc;
   }
   *fid = slot;
@@ -607,15 +863,18 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
 int gfs_close(gfs_ctx* ctx, int fid) {
   if (!ctx || fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  HostFile& hf = ctx->files[fid];
-  hf.open = false;
   CK(cudaSetDevice(ctx->cfg.device));
-  int rc = push_file(ctx, fid);
-  cudaDeviceSynchronize();  // no kernel may still read the mapping or the fetched bits
-  unmap_file(hf);
-  if (hf.d_fetched) cudaFree(hf.d_fetched);
-  close(hf.fd);
-  hf = HostFile();
+  // nothing may still read the file: no kernel, no request in flight
+  CK(cudaDeviceSynchronize());
+  int rc = quiesce(ctx, nullptr);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    ctx->files[fid].open = false;
+  }
+  rc = push_file(ctx, fid);
+  if (!rc) rc = purge_pages(ctx, fid);
+  release_file(ctx, fid);
   return rc;
 }
 
@@ -623,7 +882,10 @@ int gfs_fadvise(gfs_ctx* ctx, int fid, int advice) {
   if (!ctx || fid < 0 || (size_t)fid >= ctx->files.size() || !ctx->files[fid].open) return -EBADF;
   if (advice < GFS_ADV_NORMAL || advice > GFS_ADV_RANDOM) return -EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->files[fid].advice = advice;
+  {
+    std::lock_guard<std::mutex> fl(ctx->files_mu);
+    ctx->files[fid].advice = advice;
+  }
   CK(cudaSetDevice(ctx->cfg.device));
   return push_file(ctx, fid);
 }
@@ -645,22 +907,8 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
   CK(cudaSetDevice(ctx->cfg.device));
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaStreamSynchronize(s));
-  unsigned long long tail = 0;
-  CK(cudaMemcpy(&tail, &ctx->dev.ctrl->ring_tail.v, 8, cudaMemcpyDeviceToHost));
-  const double t0 = now_s();
-  while (ctx->io->served() < tail) {
-    if (now_s() - t0 > (double)ctx->cfg.timeout_ns * 1e-9 + 5.0) return -ETIMEDOUT;
-    usleep(50);
-  }
-  ctx->io->drain_sinks();
-  if (ctx->cfg.xfer != GFS_XFER_DMA) {  // copy out what was served but never read
-    int rc = launch_drain(ctx->dev, s);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(s));
-    unsigned long long freed = 0;
-    CK(cudaMemcpy(&freed, &ctx->dev.ctrl->freed.v, 8, cudaMemcpyDeviceToHost));
-    if (freed < tail) return -ETIMEDOUT;
-  }
+  int qrc = quiesce(ctx, s);
+  if (qrc) return qrc;
   ctx->io->stats.clear();
   if (ctx->dev.fetch_count) CK(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, s));
   for (auto& f : ctx->files)
@@ -672,7 +920,8 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
   }
   int rc = launch_reset(ctx->dev, s);
   if (rc) return rc;
-  return cuda_err(cudaStreamSynchronize(s));
+  CK(cudaStreamSynchronize(s));
+  return reclaim_retired(ctx, true);  // ids closed on the device: their pages are gone now
 }
 
 int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
@@ -711,6 +960,7 @@ int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
   o->host_ns_wait_buf = ctx->io->stats.ns_wait_buf.load();
   o->host_ns_idle = ctx->io->stats.ns_idle.load();
   o->buffer_hits = st[ST_BUFHITS];
+  o->host_controls = ctx->io->stats.controls.load();
   return 0;
 }
 
@@ -840,6 +1090,46 @@ int gfs_scan(gfs_ctx* ctx, int fid, const gfs_scan_args* a, int64_t* d_count, ui
   cudaStream_t s = (cudaStream_t)stream;
   if (a->serialize) CK(cudaMemsetAsync(&g.ctrl->ticket.v, 0, 8, s));
   return launch_scan(g, fid, *a, ns, ctx->d_scan_buf, bs, d_count, d_sum, d_hash, s);
+}
+
+int gfs_scan_path(gfs_ctx* ctx, const char* path, const gfs_scan_args* a, int64_t* d_count, uint64_t* d_sum,
+                  uint64_t* d_hash, void* stream) {
+  if (!ctx || !path || !a) return -EINVAL;
+  const size_t len = strnlen(path, GFS_PATH_MAX);
+  if (len == 0) return -EINVAL;
+  if (len >= GFS_PATH_MAX) return -ENAMETOOLONG;
+  if (ctx->cfg.mode == GFS_MODE_PAPER) return -ENOTSUP;
+  if (a->stride == 0 || a->read_len == 0 || a->blocks == 0 || a->serialize) return -EINVAL;
+  if (a->threads != 128 && a->threads != 256 && a->threads != 512) return -EINVAL;
+  struct stat st;
+  if (stat(path, &st) != 0) return -errno;
+  const uint64_t size = (uint64_t)st.st_size;
+  const uint64_t ns = size ? (size + a->stride - 1) / a->stride : 0;
+  if (ns == 0) return 0;
+  if (!d_count || !d_sum || !d_hash) return -EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  const uint64_t bs = align_up(a->read_len, 256);
+  int rc = ensure_scan_buf(ctx, (size_t)a->blocks * bs);
+  if (rc) return rc;
+  DevHandle g = ctx->dev;
+  const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
+                                      : (uint32_t)std::min<uint64_t>(0xffffffffull, a->blocks * pages_per_read + 1);
+  PathArg pa;
+  memset(pa.s, 0, sizeof(pa.s));
+  memcpy(pa.s, path, len);
+  return launch_scan_path(g, pa, *a, ns, ctx->d_scan_buf, bs, d_count, d_sum, d_hash, (cudaStream_t)stream);
+}
+
+int gfs_device_handle(gfs_ctx* ctx, uint32_t blocks, uint64_t read_len, void* out, uint64_t cap) {
+  if (!ctx || !out || blocks == 0 || read_len == 0) return -EINVAL;
+  if (cap < sizeof(DevHandle)) return -ENOSPC;
+  DevHandle g = ctx->dev;
+  const uint64_t pages_per_read = (read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
+                                      : (uint32_t)std::min<uint64_t>(0xffffffffull, blocks * pages_per_read + 1);
+  memcpy(out, &g, sizeof(g));
+  return (int)sizeof(DevHandle);
 }
 
 int gfs_scan_host(gfs_ctx* ctx, int fid, const gfs_scan_args* a, int64_t* h_count, uint64_t* h_sum, uint64_t* h_hash,

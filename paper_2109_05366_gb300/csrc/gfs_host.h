@@ -31,6 +31,14 @@ struct HostFile {
   int advice = GFS_ADV_NORMAL;
   bool open = false;
   std::string path;
+  // opened on the device (gopen): reference count of the blocks holding it
+  bool by_device = false;
+  uint32_t dev_refs = 0;
+  bool opening = false;        // a device open is setting the id up
+  bool fetched_async = false;  // d_fetched came from cudaMallocAsync on the control stream
+  // closed on the device: the id keeps its cached pages (and its descriptor)
+  // until they are dropped at a quiet point
+  bool retired = false;
 };
 
 class IoService;
@@ -40,6 +48,14 @@ int launch_reset(const DevHandle& g, cudaStream_t s);
 int launch_drain(const DevHandle& g, cudaStream_t s);
 int launch_scan(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
                 uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
+// A path passed by value as a kernel parameter (readable through a pointer).
+struct PathArg {
+  char s[GFS_PATH_MAX];
+};
+int launch_scan_path(const DevHandle& g, const PathArg& path, const gfs_scan_args& a, unsigned long long nstrides,
+                     uint8_t* bufs, uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash,
+                     cudaStream_t s);
+int launch_purge(const DevHandle& g, uint32_t fid, cudaStream_t s);
 int launch_read_many(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
                      const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
                      cudaStream_t s);
@@ -82,5 +98,10 @@ struct gfs_ctx {
   uint8_t* d_out = nullptr;        // gfs_scan_host results: device side
   uint8_t* h_out = nullptr;        // and a pinned host copy
   size_t out_bytes = 0;
+  char* h_paths = nullptr;         // per-slot path buffers of device opens (mapped pinned)
+  cudaStream_t ctl_stream = nullptr;  // device control requests: allocations and file-state copies
+  void* h_ctl_fd = nullptr;           // pinned FileDev staging of those copies
   std::mutex mu;
+  std::mutex files_mu;             // HostFile fields read by the host I/O threads
+  std::mutex dev_open_mu;          // device opens and closes, one at a time
 };

@@ -86,13 +86,20 @@ struct PrivBuf {
 };
 
 // Per-file device state.
+// Written only by the host (also for the device's gopen, gfadvise and gclose,
+// before it answers them); read with relaxed loads at the start of each gread.
 struct FileDev {
   unsigned long long size;
   unsigned long long npages;
   uint32_t open;     // 1 if the fid is open
   uint32_t ra;       // readahead enabled (read-only, not ADV_RANDOM)
   uint32_t* fetched; // one bit per page: fetched since the last reset (readahead skips those)
+  uint32_t flags;    // open flags
+  uint32_t advice;   // GFS_ADV_*
+  uint32_t mapped;   // 1 if the file's page cache is mapped for the GPU
+  uint32_t pad;
 };
+static_assert(sizeof(FileDev) == 48, "FileDev");
 
 // One request-ring slot in mapped pinned memory (64-byte header + frame list).
 // Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; the GPU
@@ -105,11 +112,28 @@ struct RingSlot {
   uint32_t npages;
   unsigned long long page_lo;
   uint32_t kind;
-  uint32_t op;
+  uint32_t op;         // OP_READ, OP_OPEN, OP_CLOSE
   unsigned long long issue_ns;
   uint32_t pad[6];
   uint32_t frames[1];  // npages entries follow (slot stride covers max_rpc_pages)
 };
+
+// Request kinds of a ring slot.  OPEN, CLOSE and ADVISE carry no frames: their
+// payload (where the frame list of a read would be) is a CtlMsg, the path of an
+// OPEN sits in the slot's GFS_PATH_MAX-byte path buffer, and the requesting
+// warp frees the slot after it has read the host's answer.  The host makes
+// every change to a file's FileDev itself (a copy on a stream of its own) before
+// it answers, so the device sees one order of opens, closes and hints.
+enum : uint32_t { OP_READ = 1, OP_OPEN = 2, OP_CLOSE = 3, OP_ADVISE = 4 };
+
+// Payload of an OPEN / CLOSE / ADVISE slot.
+struct CtlMsg {
+  uint32_t done;    // host: 1 once the answer is written (release)
+  int32_t status;   // host: fid (OPEN) or 0, else -errno
+  uint32_t arg;     // GPU: open flags (OPEN) or advice (ADVISE)
+  uint32_t last;    // host: 1 if the CLOSE dropped the last device reference
+};
+static_assert(sizeof(CtlMsg) == 16, "CtlMsg");
 static_assert(sizeof(unsigned long long) == 8, "u64");
 
 GFS_HD inline uint32_t slot_stride(uint32_t max_pages) {
@@ -145,8 +169,9 @@ struct DevHandle {
   Ctrl* ctrl;
   FileDev* files;
   unsigned long long* last_end;  // per stream: (fid << 32 | end page), ~0 = none
-  // request ring (device view of mapped pinned memory)
+  // request ring (device view of mapped pinned memory) and its per-slot path buffers
   uint8_t* ring;
+  char* paths;                   // rpc_slots * GFS_PATH_MAX bytes, mapped pinned
   // traces
   gfs_rpc_rec* trace_rpc;
   gfs_evict_rec* trace_evict;

@@ -111,6 +111,42 @@ __global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_
   block_help_drain(g);
 }
 
+// The stride scan with the file opened on the device (Section 2.2: GPU threads
+// open, read and close files through GPUfs calls): every block gopens `path`,
+// reads its strides with the fused checksum, and gcloses.  A block whose gopen
+// fails reports the error for each of its strides.
+__global__ void __launch_bounds__(512) k_scan_path(DevHandle g, const __grid_constant__ PathArg path,
+                                                    unsigned long long stride,
+                                                    unsigned long long read_len, unsigned long long nstrides,
+                                                    uint8_t* bufs, unsigned long long buf_stride, long long* cnt,
+                                                    unsigned long long* sum, unsigned long long* hash) {
+  const uint32_t b = blockIdx.x, tid = threadIdx.x;
+  uint8_t* buf = bufs + (size_t)b * buf_stride;
+  const int fid = dev::gopen(g, path.s, GFS_RDONLY);
+  const long long size = fid >= 0 ? dev::gfstat_size(g, fid) : (long long)fid;
+  for (unsigned long long s = b; s < nstrides; s += gridDim.x) {
+    Sums acc{0ull, 0ull};
+    const long long r = size < 0 ? size : dev::gread_impl<true>(g, (int)b, fid, s * stride, read_len, buf, acc);
+    dev::block_sum2(acc.sum, acc.hash);
+    if (tid == 0) {
+      cnt[s] = r;
+      sum[s] = r > 0 ? acc.sum : 0ull;
+      hash[s] = r > 0 ? acc.hash : 0ull;
+    }
+    __syncthreads();
+  }
+  if (fid >= 0) dev::gclose(g, fid);
+  block_help_drain(g);
+}
+
+// Host close: drop the cached pages and the sequential contexts of `fid` (the
+// device is otherwise idle).
+__global__ void __launch_bounds__(256) k_purge(DevHandle g, uint32_t fid) {
+  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  dev::purge_fid(g, fid, gt >> 5, nt >> 5, dev::now_ns() + g.timeout_ns);
+  for (uint32_t i = gt; i < g.max_streams; i += nt) g.last_end[(size_t)i * g.max_files + fid] = 0;
+}
+
 // GFS_XFER_PULL: copy out every request in flight (cache reset, end of use).
 __global__ void __launch_bounds__(512) k_drain(DevHandle g) {
   if (g.xfer == GFS_XFER_DMA) return;
@@ -225,6 +261,20 @@ int launch_scan(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned lo
     k_scan<false><<<a.blocks, a.threads, 0, s>>>(g, fid, a.stride, a.read_len, nstrides, (int)a.serialize, bufs,
                                                  buf_stride, (long long*)d_count, (unsigned long long*)d_sum,
                                                  (unsigned long long*)d_hash);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_scan_path(const DevHandle& g, const PathArg& path, const gfs_scan_args& a, unsigned long long nstrides,
+                     uint8_t* bufs, uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash,
+                     cudaStream_t s) {
+  k_scan_path<<<a.blocks, a.threads, 0, s>>>(g, path, a.stride, a.read_len, nstrides, bufs, buf_stride,
+                                             (long long*)d_count, (unsigned long long*)d_sum,
+                                             (unsigned long long*)d_hash);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_purge(const DevHandle& g, uint32_t fid, cudaStream_t s) {
+  k_purge<<<152, 256, 0, s>>>(g, fid);
   return cuda_err(cudaGetLastError());
 }
 

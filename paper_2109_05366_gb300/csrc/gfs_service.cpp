@@ -19,8 +19,8 @@ static inline uint64_t mono_ns() {
       .count();
 }
 
-IoService::IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files)
-    : cfg_(cfg), make_sink_(std::move(make_sink)), files_(std::move(files)) {}
+IoService::IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files, Control control)
+    : cfg_(cfg), make_sink_(std::move(make_sink)), files_(std::move(files)), control_(std::move(control)) {}
 
 IoService::~IoService() { stop(); }
 
@@ -227,6 +227,27 @@ void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticke
   __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);
 }
 
+// Answer a control request from the device in the slot's payload.  The slot
+// stays taken: the requesting warp frees it once it has read the answer.
+void IoService::control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid) {
+  CtlMsg* m = reinterpret_cast<CtlMsg*>(s->frames);
+  CtlMsg ans{};
+  ans.arg = ((volatile CtlMsg*)m)->arg;
+  ans.status = -ENOTSUP;
+  if (control_) {
+    char path[GFS_PATH_MAX];
+    path[0] = '\0';
+    if (op == OP_OPEN && cfg_.paths) {
+      memcpy(path, cfg_.paths + (size_t)slot * GFS_PATH_MAX, GFS_PATH_MAX);
+      path[GFS_PATH_MAX - 1] = '\0';
+    }
+    control_(op, fid, ans.arg, path, &ans);
+  }
+  m->status = ans.status;
+  m->last = ans.last;
+  __atomic_store_n(&m->done, 1u, __ATOMIC_RELEASE);
+}
+
 void IoService::run(int idx) {
   Sink* sink = sinks_[idx];
   sink->thread_init();
@@ -252,7 +273,14 @@ void IoService::run(int idx) {
     const uint32_t fid = vs->fid;
     const uint32_t npages = vs->npages;
     const uint64_t page_lo = vs->page_lo;
+    const uint32_t op = vs->op;
     const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
+    if (op == OP_OPEN || op == OP_CLOSE || op == OP_ADVISE) {
+      control(s, (uint32_t)(h % cfg_.slots), op, fid);
+      stats.controls.fetch_add(1, std::memory_order_relaxed);
+      served_.fetch_add(1, std::memory_order_release);
+      continue;
+    }
     stats.requests.fetch_add(1, std::memory_order_relaxed);
     if (cfg_.pull_arena) {  // the GPU frees the slot once it has copied the pages
       serve_pull(idx, pull_cur, (uint32_t)(h % cfg_.slots), h, fid, page_lo,

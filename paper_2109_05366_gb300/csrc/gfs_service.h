@@ -61,14 +61,17 @@ struct ServiceConfig {
   uint64_t chunk_bytes = 0;
   uint32_t bufs_per_thread = 0;
   uint32_t max_pages = 0;
+  // device opens: per-slot path buffers (host view), GFS_PATH_MAX bytes each
+  const char* paths = nullptr;
 };
 
 struct ServiceStats {
   std::atomic<uint64_t> requests{0}, preads{0}, bytes{0}, copies{0}, errors{0};
   std::atomic<uint64_t> ns_pread{0}, ns_wait_buf{0}, ns_idle{0};
+  std::atomic<uint64_t> controls{0};  // device opens and closes answered
   void clear() {
     requests = 0; preads = 0; bytes = 0; copies = 0; errors = 0;
-    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0;
+    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0; controls = 0;
   }
 };
 
@@ -76,8 +79,11 @@ class IoService {
  public:
   using SinkFactory = std::function<Sink*(int thread_index)>;
   using FileLookup = std::function<bool(uint32_t fid, FileView* out)>;
+  // OP_OPEN / OP_CLOSE / OP_ADVISE from the device: fill msg->status (and
+  // msg->last); the service then publishes the answer.
+  using Control = std::function<void(uint32_t op, uint32_t fid, uint32_t arg, const char* path, CtlMsg* msg)>;
 
-  IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files);
+  IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files, Control control = nullptr);
   ~IoService();
   int start();
   void stop();
@@ -90,6 +96,7 @@ class IoService {
 
  private:
   void run(int idx);
+  void control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid);
   void serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
   void serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
                   uint32_t npages);
@@ -98,6 +105,7 @@ class IoService {
   ServiceConfig cfg_;
   SinkFactory make_sink_;
   FileLookup files_;
+  Control control_;
   std::vector<std::thread> threads_;
   std::vector<Sink*> sinks_;
   std::atomic<bool> stop_{false};

@@ -21,6 +21,7 @@ REPL_FIFO, REPL_TB_LRA = 0, 1
 ADV_NORMAL, ADV_SEQUENTIAL, ADV_RANDOM = 0, 1, 2
 XFER_DMA, XFER_PULL, XFER_MAPPED = 0, 1, 2
 KIND_DEMAND, KIND_SYNC_RA, KIND_ASYNC_RA = 0, 1, 2
+PATH_MAX = 1024
 
 u32, u64, i32, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
 vp = ctypes.c_void_p
@@ -42,11 +43,11 @@ STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fe
                 "ra_pages_sync", "ra_pages_async", "evictions", "unconsumed_evictions", "retries", "timeouts",
                 "eio", "enomem", "host_requests", "host_preads", "host_bytes", "host_copies", "host_errors",
                 "trace_rpc_count", "trace_evict_count", "host_ns_pread", "host_ns_wait_buf", "host_ns_idle",
-                "buffer_hits"]
+                "buffer_hits", "host_controls"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 4)]
+    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 3)]
 
 
 class RpcRec(ctypes.Structure):
@@ -92,6 +93,8 @@ SIGNATURES = {
     "gfs_scan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_host": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
+    "gfs_scan_path": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
+    "gfs_device_handle": (ctypes.c_int, [vp, u32, u64, vp, u64]),
     "gfs_read_many": (ctypes.c_int, [vp, ctypes.c_int, u32, vp, vp, vp, vp, vp, u32, u32, vp]),
     "gfs_scan_graph": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), u32, vp, vp, vp, vp]),
     "gfs_cpuio_scan": (ctypes.c_int, [ctypes.c_char_p, u64, u64, u32, u64, vp, vp, vp, vp, vp,
@@ -279,6 +282,29 @@ class Context:
         _check(load().gfs_scan(self.handle, fid, ctypes.byref(a), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
                                _stream(stream)), "gfs_scan")
         return out
+
+    def scan_path(self, path: str, stride: int, read_len: int | None = None, blocks: int = 64, threads: int = 256,
+                  out=None, stream=None):
+        """Stride scan whose threadblocks open `path` on the device (gopen / gclose); device tensors as scan()."""
+        import torch
+        try:
+            size = os.path.getsize(path)
+        except OSError:  # the library reports the error
+            size = 0
+        ns = (size + stride - 1) // stride if size else 0
+        if out is None:
+            out = tuple(torch.empty(max(ns, 1), dtype=torch.int64, device="cuda") for _ in range(3))
+        a = self._args(stride, read_len, blocks, threads, False, True)
+        _check(load().gfs_scan_path(self.handle, path.encode(), ctypes.byref(a), _ptr(out[0]), _ptr(out[1]),
+                                    _ptr(out[2]), _stream(stream)), "gfs_scan_path(%s)" % path)
+        return out
+
+    def device_handle(self, blocks: int, read_len: int) -> bytes:
+        """The plain-data device handle that kernels calling the device API take by value."""
+        buf = ctypes.create_string_buffer(4096)
+        n = load().gfs_device_handle(self.handle, blocks, read_len, buf, len(buf))
+        _check(n if n < 0 else 0, "gfs_device_handle")
+        return buf.raw[:n]
 
     def scan_graph(self, fid: int, stride: int, reps: int, read_len: int | None = None, blocks: int = 64,
                    threads: int = 256, serialize: bool = False, fused: bool = False, out=None, stream=None):

@@ -1,0 +1,17 @@
+"""Compile tests/devapi_user.cu (a user's kernel calling the device API) with nvcc."""
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "devapi_user.cu")
+
+
+def build_user_kernel(outdir: str) -> str:
+    nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    out = os.path.join(outdir, "devapi_user.so")
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-shared",
+                           "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "paper_2109_05366_gb300", "csrc"),
+                           "-I", os.path.join(ROOT, "include"), SRC, "-o", out])
+    return out

@@ -1,0 +1,75 @@
+// A kernel written the way a user of the library writes one: it includes the
+// device runtime and calls the device API itself.  Every threadblock opens the
+// file (gopen), optionally sets an access hint (gfadvise), checks gfstat, reads
+// its strides with gread into its own buffer, sums the bytes, and closes the
+// file (gclose).  Built by tests/test_gpu_devapi.py with nvcc.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "gfs_device.cuh"
+
+namespace {
+
+struct UserPath {
+  char s[GFS_PATH_MAX];
+};
+
+__global__ void __launch_bounds__(256) k_user(gfs::DevHandle g, const __grid_constant__ UserPath path, int advice,
+                                              unsigned long long stride, unsigned long long nstrides, uint8_t* bufs,
+                                              long long* cnt, unsigned long long* sum, long long* info) {
+  using namespace gfs;
+  uint8_t* buf = bufs + (size_t)blockIdx.x * stride;
+  const int fid = dev::gopen(g, path.s, GFS_RDONLY);
+  int arc = 0;
+  if (fid >= 0 && advice >= 0) arc = dev::gfadvise(g, fid, advice);
+  gfs_stat st{};
+  const int src = fid >= 0 ? dev::gfstat(g, fid, &st) : fid;
+  for (unsigned long long s = blockIdx.x; s < nstrides; s += gridDim.x) {
+    const long long r = fid >= 0 ? dev::gread(g, (int)blockIdx.x, fid, s * stride, stride, buf) : fid;
+    unsigned long long acc = 0;
+    for (long long i = threadIdx.x; i < r; i += blockDim.x) acc += buf[i];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ unsigned long long s_part[8];
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+      cnt[s] = r;
+      sum[s] = t;
+    }
+    __syncthreads();
+  }
+  const int crc = fid >= 0 ? dev::gclose(g, fid) : 0;
+  if (threadIdx.x == 0) {
+    long long* mine = info + 8 * blockIdx.x;
+    mine[0] = fid;
+    mine[1] = arc;
+    mine[2] = src;
+    mine[3] = (long long)st.size;
+    mine[4] = st.page_size;
+    mine[5] = st.advice;
+    mine[6] = st.flags;
+    mine[7] = crc;
+  }
+}
+
+}  // namespace
+
+// handle: the bytes gfs_device_handle wrote; bufs: blocks * stride bytes;
+// cnt, sum: nstrides entries; info: 8 * blocks entries.  Returns a cudaError_t.
+extern "C" int user_scan(const void* handle, uint64_t handle_bytes, const char* path, int advice, uint64_t stride,
+                         uint64_t nstrides, uint32_t blocks, void* bufs, void* cnt, void* sum, void* info,
+                         void* stream) {
+  if (handle_bytes != sizeof(gfs::DevHandle)) return (int)cudaErrorInvalidValue;
+  if (strlen(path) >= GFS_PATH_MAX) return (int)cudaErrorInvalidValue;
+  gfs::DevHandle g;
+  memcpy(&g, handle, sizeof(g));
+  UserPath p;
+  memset(p.s, 0, sizeof(p.s));
+  strcpy(p.s, path);
+  k_user<<<blocks, 256, 0, (cudaStream_t)stream>>>(g, p, advice, stride, nstrides, (uint8_t*)bufs, (long long*)cnt,
+                                                   (unsigned long long*)sum, (long long*)info);
+  return (int)cudaGetLastError();
+}

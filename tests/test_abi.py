@@ -45,7 +45,7 @@ def test_struct_layouts_match_header(tmp_path):
     import subprocess
     checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "replacement", "reserved"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
-              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "reserved"]),
+              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "host_controls", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
               ("gfs_evict_rec", gfs.EvictRec, ["new_fid", "new_page"]),
               ("gfs_scan_args", gfs.ScanArgs, ["read_len", "fused", "reserved"])]
@@ -105,3 +105,14 @@ def test_ring_needs_two_slots(tmp_path):
     inputs.write_file(path, 3, 4096 * 4)
     with pytest.raises(gfs.GfsError):
         gfs.selftest_ring(path, 4096, 16, 10, 1, 1, 1)
+
+
+def test_user_kernel_builds_against_device_api(tmp_path):
+    """A user's kernel that includes the device runtime and calls gopen / gfadvise /
+    gfstat / gread / gclose compiles for sm_103a and exports its launcher."""
+    import subprocess
+
+    from tests.devapi_build import build_user_kernel
+    so = build_user_kernel(str(tmp_path))
+    syms = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    assert " user_scan" in syms
