@@ -37,6 +37,18 @@ constexpr int kEIO = 5, kEBADF = 9, kEAGAIN = 11, kENOMEM = 12, kEINVAL = 22, kE
               kENOTSUP = 95, kETIMEDOUT = 110;
 constexpr unsigned kFull = 0xffffffffu;
 
+// A gread's allocation context and every frame's allocation record share one
+// encoding: (allocation sequence << kOwnerBits) | owner, owner = stream + 1
+// (0 = no stream).  Ordering by the value orders by allocation sequence.
+constexpr uint32_t kOwnerBits = 20;
+constexpr unsigned long long kOwnerMask = (1ull << kOwnerBits) - 1;
+__device__ __forceinline__ unsigned long long owner_of(int stream) {
+  return stream >= 0 ? ((unsigned long long)stream + 1) & kOwnerMask : 0ull;
+}
+// Frames the demand fallback scans per attempt; a cache of at most this many
+// frames is scanned whole (exact least recently allocated).
+constexpr uint32_t kLraWindow = 1024;
+
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -399,17 +411,34 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
     }
   }
   if (for_ra) return -1;
-  // (3) demand only: the least recently allocated unconsumed frame not
-  //     allocated during this gread
-  for (int attempt = 0; attempt < 8; ++attempt) {
+  // (3) demand only: the least recently allocated unconsumed frame that this
+  //     gread did not allocate.  A cache of at most kLraWindow frames is scanned
+  //     whole.  A larger one is scanned a window of kLraWindow frames at a time,
+  //     from a place that depends on the gread, and the oldest frame of the first
+  //     window that has one is taken: concurrent greads then pick different
+  //     victims instead of all racing for the single oldest frame.
+  const uint32_t W = g.n_frames < kLraWindow ? g.n_frames : kLraWindow;
+  const uint32_t nwin = (g.n_frames + W - 1) / W;
+  uint32_t base = 0;
+  if (nwin > 1) {
+    unsigned long long z = seq0 + 0x9e3779b97f4a7c15ull * (1ull + blockIdx.x);
+    z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ull;
+    base = (uint32_t)((z ^ (z >> 29)) % g.n_frames);
+  }
+  const unsigned long long my_seq = seq0 >> kOwnerBits, my_owner = seq0 & kOwnerMask;
+  uint32_t empty_windows = 0;
+  for (uint32_t attempt = 0; attempt < nwin + 8; ++attempt) {
+    const uint32_t start = nwin > 1 ? (uint32_t)((base + (unsigned long long)attempt * W) % g.n_frames) : 0u;
     unsigned long long best = ~0ull;
     int bf = -1;
-    for (uint32_t i = lane; i < g.n_frames; i += 32) {
+    for (uint32_t k = lane; k < W; k += 32) {
+      uint32_t i = start + k;
+      if (i >= g.n_frames) i -= g.n_frames;
       uint32_t st = ld_rlx(&g.fstate[i]);
       if (st != FR_READY && st != FR_ERROR) continue;
       if (ld_rlx(&g.fpins[i]) != 0u) continue;
       unsigned long long a = ld_rlx64(&g.faseq[i]);
-      if (a >= seq0) continue;
+      if ((a >> kOwnerBits) >= my_seq && (a & kOwnerMask) == my_owner) continue;  // allocated by this gread
       if (st == FR_READY && ld_rlx(&g.fconsumed[i]) >= ld_rlx(&g.fvalid[i])) continue;  // belongs to the FIFO
       if (a < best) { best = a; bf = (int)i; }
     }
@@ -418,7 +447,11 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
       int of = __shfl_xor_sync(kFull, bf, o);
       if (ob < best || (ob == best && of >= 0 && (bf < 0 || of < bf))) { best = ob; bf = of; }
     }
-    if (bf < 0) return -kENOMEM;
+    if (bf < 0) {
+      if (++empty_windows >= nwin) return -kENOMEM;  // no candidate anywhere
+      continue;
+    }
+    empty_windows = 0;
     int claimed = 0;
     if (lane == 0) claimed = frame_claim(g, bf, false);
     if (bcast(claimed) == 1) {
@@ -763,7 +796,7 @@ static __device__ int request_range(const DevHandle& g, uint32_t fid, const File
       st_rlx(&g.fwindow[f], 0u);
       st_rlx(&g.fmark[f], 0u);
       st_rlx(&g.fvalid[f], expected_valid(g, fi, q));
-      st_rlx64(&g.faseq[f], atomicAdd(&g.ctrl->alloc_counter.v, 1ull));
+      st_rlx64(&g.faseq[f], (atomicAdd(&g.ctrl->alloc_counter.v, 1ull) << kOwnerBits) | (seq0 & kOwnerMask));
       if (g.fsrc) st_rlx(&g.fsrc[f], SRC_NONE);
       __threadfence();
       if (pin) atomicAdd(&g.fpins[f], 1u);
@@ -976,7 +1009,7 @@ static __device__ int handle_miss_paper(const DevHandle& g, int stream, uint32_t
     st_rlx(&g.fwindow[f], 0u);
     st_rlx(&g.fmark[f], 0u);
     st_rlx(&g.fvalid[f], expected_valid(g, fi, p));
-    st_rlx64(&g.faseq[f], atomicAdd(&g.ctrl->alloc_counter.v, 1ull));
+    st_rlx64(&g.faseq[f], (atomicAdd(&g.ctrl->alloc_counter.v, 1ull) << kOwnerBits) | (seq0 & kOwnerMask));
     st_rlx(&g.fsrc[f], SRC_NONE);
     __threadfence();
     atomicAdd(&g.fpins[f], 1u);
@@ -1173,7 +1206,7 @@ static __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long 
   for (uint32_t it = 0;; ++it) {
     if (threadIdx.x == 0) {
       int st = (int)ld_acq(&g.fstate[f]);
-      if ((st == FR_FILLING || st == FR_COPYING) && now_ns() > deadline) {
+      if ((st == FR_FILLING || st == FR_COPYING || st == FR_RECLAIM) && now_ns() > deadline) {
         stat_add(g, ST_TIMEOUTS, 1);
         st = -kETIMEDOUT;
       }
@@ -1182,7 +1215,9 @@ static __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long 
     __syncthreads();
     const int st = s_st;
     __syncthreads();
-    if (st != FR_FILLING && st != FR_COPYING) return st;
+    // RECLAIM is transient here: an evictor that claimed the frame finds this
+    // block's pin and puts the state back
+    if (st != FR_FILLING && st != FR_COPYING && st != FR_RECLAIM) return st;
     if (g.xfer != GFS_XFER_DMA) {
       // the page itself first; other served pages only now and then (their
       // completion records are read over the host link)
@@ -1345,7 +1380,7 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
   if (off >= fi.size || len == 0) return 0;
   const unsigned long long end = (len > fi.size - off) ? fi.size : off + len;
   const unsigned long long p0 = off >> g.page_shift, p1 = (end - 1) >> g.page_shift;
-  if (tid == 0) s_seq0 = ld_rlx64(&g.ctrl->alloc_counter.v);
+  if (tid == 0) s_seq0 = (ld_rlx64(&g.ctrl->alloc_counter.v) << kOwnerBits) | owner_of(stream);
   __syncthreads();
   const unsigned long long seq0 = s_seq0;
   const unsigned long long deadline = now_ns() + g.timeout_ns;
