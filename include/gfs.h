@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define GFS_ABI_VERSION 1
+#define GFS_ABI_VERSION 2
 
 /* Cache policy modes. */
 #define GFS_MODE_READAHEAD 0 /* Section 4.1 prefetcher + Section 2.3 window growth */
@@ -65,6 +65,14 @@ extern "C" {
                            * GPU copies them into frames over the host link.  Files that cannot be mapped
                            * read-write (permissions, file system) fall back to GFS_XFER_PULL. */
 
+/* How requests are placed in the ring and how host threads find them (gfs_config.queue). */
+#define GFS_QUEUE_SHARED 0 /* one shared ring: the GPU takes the next ticket, any host thread serves any
+                            * ticket (every thread busy while requests wait) */
+#define GFS_QUEUE_STATIC 1 /* GPUfs as Section 3.2 describes it: a threadblock uses slot
+                            * (block index mod rpc_slots) and host thread k polls only its contiguous
+                            * share of the slots, so threads whose slots belong to blocks that are not
+                            * running stay idle */
+
 /* Request kinds in the RPC trace. */
 #define GFS_KIND_DEMAND 0
 #define GFS_KIND_SYNC_RA 1
@@ -93,7 +101,8 @@ typedef struct gfs_config {
   int32_t device;          /* CUDA device ordinal */
   uint32_t latency_capacity; /* greads whose latency (globaltimer ns, entry to exit) is kept; 0 = off */
   uint32_t replacement;    /* GFS_REPL_* */
-  uint32_t reserved[5];
+  uint32_t queue;          /* GFS_QUEUE_* */
+  uint32_t reserved[4];
 } gfs_config;
 
 typedef struct gfs_stat {
@@ -119,6 +128,25 @@ typedef struct gfs_stats {
   uint64_t host_controls;     /* opens and closes requested by the device (gopen, gclose) */
   uint64_t reserved[3];
 } gfs_stats;
+
+/* Per host I/O thread counters since the last gfs_reset_cache (Section 3.2: the
+ * GPUfs host threads' polling before their first request). */
+typedef struct gfs_thread_stat {
+  uint64_t requests;           /* requests this thread served (reads, opens, closes, hints) */
+  uint64_t polls_before_first; /* empty polls (of its ticket or of its slots) before its first request */
+  uint64_t first_request_ns;   /* from the reset (or start) to its first request; 0 if none */
+  uint64_t idle_ns;            /* time spent waiting for requests */
+  uint64_t pread_ns;           /* time spent in pread */
+  uint64_t bytes;              /* file bytes it delivered */
+} gfs_thread_stat;
+
+/* One entry of the host I/O trace: a file range a host thread served (read with
+ * pread in the staging transfers, published for the GPU in the mapped one). */
+typedef struct gfs_io_rec {
+  uint64_t offset, bytes;
+  uint32_t fid, thread;
+  uint64_t t_ns; /* when the thread took the request (CLOCK_MONOTONIC) */
+} gfs_io_rec;
 
 /* One entry of the RPC trace: a request as the GPU issued it. */
 typedef struct gfs_rpc_rec {
@@ -197,6 +225,22 @@ int gfs_get_trace(gfs_ctx* ctx, gfs_rpc_rec* h_rpc, gfs_evict_rec* h_evict, uint
  * > 0): copies min(cap, recorded) values to h_ns; *n receives the number of
  * greads that finished (may exceed the capacity). */
 int gfs_get_latencies(gfs_ctx* ctx, uint64_t* h_ns, uint64_t cap, uint64_t* n, void* stream);
+
+/* Per host I/O thread counters; copies min(cap, host_threads) entries and
+ * returns host_threads. */
+int gfs_get_thread_stats(gfs_ctx* ctx, gfs_thread_stat* h_out, uint32_t cap);
+
+/* Host I/O trace (trace_capacity > 0): copies min(cap, recorded, trace_capacity)
+ * entries in the order the host threads took the requests; *n = ranges recorded. */
+int gfs_get_io_trace(gfs_ctx* ctx, gfs_io_rec* h_out, uint64_t cap, uint64_t* n);
+
+/* Replay a host I/O trace on the CPU without the GPU (Section 3.2: the GPU I/O
+ * trace replayed by CPU threads isolates the file access pattern from the
+ * CPU-GPU interaction): `threads` threads take the records in order and pread
+ * each range of `path` into a private buffer.  *seconds = wall time, *bytes =
+ * bytes read. */
+int gfs_replay_io(const char* path, const gfs_io_rec* recs, uint64_t n, uint32_t threads, double* seconds,
+                  uint64_t* bytes);
 
 /* Per-page fetch counts of file id 0 (debug_counts=1); copies min(cap, pages). */
 int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* stream);
@@ -361,10 +405,15 @@ int gfs_probe_pull(uint64_t bytes, int reps, double* gbps);
 
 /* Self-test of the request ring and the host I/O service without a GPU: a host
  * thread plays the device client (same slot protocol), the service preads the
- * file into host frames; returns 0 when every page matches pread. */
+ * file into host frames; returns 0 when every page matches pread.  queue:
+ * GFS_QUEUE_*; with GFS_QUEUE_STATIC request i comes from client block
+ * i mod client_blocks and uses that block's slot.  *h_served = requests the
+ * service handed to its sinks; h_thread_requests (threads entries, or NULL)
+ * gets each host thread's request count. */
 int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests,
-                      uint32_t max_pages, uint32_t threads, uint32_t slots, uint64_t seed,
-                      uint64_t* h_served);
+                      uint32_t max_pages, uint32_t threads, uint32_t slots, uint32_t queue,
+                      uint32_t client_blocks, uint64_t seed, uint64_t* h_served,
+                      uint64_t* h_thread_requests);
 
 /* Library ABI version (GFS_ABI_VERSION). */
 int gfs_abi_version(void);

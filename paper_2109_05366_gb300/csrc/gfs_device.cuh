@@ -666,7 +666,15 @@ static __device__ int ring_acquire(const DevHandle& g, unsigned long long* t_out
                                    unsigned long long deadline) {
   const int lane = lane_id();
   unsigned long long t = 0;
-  if (lane == 0) t = atomicAdd(&g.ctrl->ring_tail.v, 1ull);
+  if (lane == 0) {
+    const unsigned long long k = atomicAdd(&g.ctrl->ring_tail.v, 1ull);  // requests issued (drain counts them)
+    if (g.queue == GFS_QUEUE_STATIC) {  // Section 3.2: the threadblock's own slot
+      const uint32_t slot = blockIdx.x % g.rpc_slots;
+      t = atomicAdd(&g.slot_lap[slot], 1ull) * g.rpc_slots + slot;
+    } else {
+      t = k;
+    }
+  }
   t = bcast64(t);
   const uint32_t si = (uint32_t)(t % g.rpc_slots);
   RingSlot* s = ring_slot(g, si);

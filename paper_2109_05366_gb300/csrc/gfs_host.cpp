@@ -548,6 +548,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   if (c.mode > GFS_MODE_PAPER || c.xfer > GFS_XFER_MAPPED || c.replacement > GFS_REPL_TB_LRA) return -EINVAL;
   if (c.mode == GFS_MODE_PAPER && c.xfer == GFS_XFER_DMA) return -ENOTSUP;  // the requesting block copies its pages
   if (c.replacement == GFS_REPL_TB_LRA && c.mode != GFS_MODE_PAPER) return -EINVAL;
+  if (c.queue > GFS_QUEUE_STATIC) return -EINVAL;
   // a Vyukov ring needs 2 slots at least: with one, "published for ticket t" and
   // "free for ticket t+1" are the same sequence value
   if (c.rpc_slots < 2 || c.max_rpc_pages < 1 || c.max_rpc_pages > MAX_RPC_PAGES) return -EINVAL;
@@ -613,7 +614,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
                o_tev = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_evict_rec)),
                o_dtick = take((size_t)c.rpc_slots * 8), o_dnp = take((size_t)c.rpc_slots * 4),
                o_dcop = take((size_t)c.rpc_slots * 4), o_dfr = take((size_t)c.rpc_slots * c.max_rpc_pages * 4),
-               o_fsrc = take((size_t)F * 4), o_lat = take((size_t)std::max<uint32_t>(1, c.latency_capacity) * 8);
+               o_fsrc = take((size_t)F * 4), o_lat = take((size_t)std::max<uint32_t>(1, c.latency_capacity) * 8),
+               o_lap = take((size_t)c.rpc_slots * 8);
   ctx->arena_bytes = off;
   rc = cuda_err(cudaMalloc(&ctx->d_arena, off));
   if (!rc) rc = cuda_err(cudaMemset(ctx->d_arena, 0, off));
@@ -650,6 +652,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.fsrc = (uint32_t*)(a + o_fsrc);
   g.lat = (unsigned long long*)(a + o_lat);
   g.lat_cap = c.latency_capacity;
+  g.queue = c.queue;
+  g.slot_lap = (unsigned long long*)(a + o_lap);  // zero: every slot at lap 0, for the life of the context
   g.staging = nullptr;
   g.done = nullptr;
   g.pages = nullptr;
@@ -730,6 +734,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.threads = c.host_threads;
   sc.n_frames = F;
   sc.paths = ctx->h_paths;
+  sc.queue = c.queue;
+  sc.io_trace_cap = c.trace_capacity;
   if (c.xfer != GFS_XFER_DMA) {
     sc.pull_arena = ctx->h_staging;
     sc.pull_done = ctx->h_done;
@@ -909,7 +915,7 @@ int gfs_reset_cache(gfs_ctx* ctx, void* stream) {
   CK(cudaStreamSynchronize(s));
   int qrc = quiesce(ctx, s);
   if (qrc) return qrc;
-  ctx->io->stats.clear();
+  ctx->io->clear_stats();
   if (ctx->dev.fetch_count) CK(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, s));
   for (auto& f : ctx->files)
     if (f.open && f.d_fetched) CK(cudaMemsetAsync(f.d_fetched, 0, f.fetched_bytes, s));
@@ -989,6 +995,31 @@ int gfs_get_latencies(gfs_ctx* ctx, uint64_t* h_ns, uint64_t cap, uint64_t* n, v
   CK(cudaMemcpy(&k, &ctx->dev.ctrl->lat_n.v, 8, cudaMemcpyDeviceToHost));
   const uint64_t c = std::min<uint64_t>({k, cap, (uint64_t)ctx->dev.lat_cap});
   if (h_ns && c) CK(cudaMemcpy(h_ns, ctx->dev.lat, c * 8, cudaMemcpyDeviceToHost));
+  if (n) *n = k;
+  return 0;
+}
+
+int gfs_get_thread_stats(gfs_ctx* ctx, gfs_thread_stat* h_out, uint32_t cap) {
+  if (!ctx || !ctx->io || (cap && !h_out)) return -EINVAL;
+  const uint32_t T = ctx->io->threads();
+  for (uint32_t i = 0; i < T && i < cap; ++i) {
+    const ThreadCounters& c = ctx->io->thread_counters(i);
+    gfs_thread_stat& o = h_out[i];
+    o.requests = c.requests.load();
+    o.polls_before_first = c.polls_before_first.load();
+    o.first_request_ns = c.first_ns.load();
+    o.idle_ns = c.idle_ns.load();
+    o.pread_ns = c.pread_ns.load();
+    o.bytes = c.bytes.load();
+  }
+  return (int)T;
+}
+
+int gfs_get_io_trace(gfs_ctx* ctx, gfs_io_rec* h_out, uint64_t cap, uint64_t* n) {
+  if (!ctx || !ctx->io || (cap && !h_out)) return -EINVAL;
+  const uint64_t k = ctx->io->io_trace_count();
+  const uint64_t c = std::min<uint64_t>({k, cap, (uint64_t)ctx->cfg.trace_capacity});
+  if (c) memcpy(h_out, ctx->io->io_trace(), c * sizeof(gfs_io_rec));
   if (n) *n = k;
   return 0;
 }
@@ -1420,11 +1451,53 @@ int gfs_probe_pread(const char* path, uint32_t threads, uint64_t chunk, int reps
   return rc;
 }
 
+// ---------------------------------------------------------------- trace replay (Section 3.2)
+int gfs_replay_io(const char* path, const gfs_io_rec* recs, uint64_t n, uint32_t threads, double* seconds,
+                  uint64_t* bytes) {
+  if (!path || (n && !recs) || threads == 0 || threads > 256 || !seconds) return -EINVAL;
+  uint64_t maxb = 0;
+  for (uint64_t i = 0; i < n; ++i) maxb = std::max<uint64_t>(maxb, recs[i].bytes);
+  if (maxb > (1ull << 32)) return -EINVAL;
+  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return -errno;
+  std::atomic<uint64_t> next{0}, total{0};
+  std::atomic<int> err{0};
+  const double t0 = now_s();
+  std::vector<std::thread> th;
+  for (uint32_t t = 0; t < threads; ++t)
+    th.emplace_back([&] {
+      std::vector<uint8_t> buf((size_t)std::max<uint64_t>(maxb, 1));
+      for (;;) {
+        const uint64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        uint64_t got = 0;
+        while (got < recs[i].bytes) {
+          const ssize_t r = pread(fd, buf.data() + got, (size_t)(recs[i].bytes - got), (off_t)(recs[i].offset + got));
+          if (r < 0 && errno == EINTR) continue;
+          if (r < 0) {
+            err.store(-errno);
+            break;
+          }
+          if (r == 0) break;
+          got += (uint64_t)r;
+        }
+        total.fetch_add(got);
+      }
+    });
+  for (auto& x : th) x.join();
+  *seconds = now_s() - t0;
+  close(fd);
+  if (bytes) *bytes = total.load();
+  return err.load();
+}
+
 // ---------------------------------------------------------------- CPU self-test
 int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests, uint32_t max_pages,
-                      uint32_t threads, uint32_t slots, uint64_t seed, uint64_t* h_served) {
+                      uint32_t threads, uint32_t slots, uint32_t queue, uint32_t client_blocks, uint64_t seed,
+                      uint64_t* h_served, uint64_t* h_thread_requests) {
   if (!path || !is_pow2(page_size) || page_size < 16 || frames == 0 || max_pages == 0 ||
-      max_pages > MAX_RPC_PAGES || threads == 0 || threads > 64 || slots < 2 || seed == 0)
+      max_pages > MAX_RPC_PAGES || threads == 0 || threads > 64 || slots < 2 || seed == 0 ||
+      queue > GFS_QUEUE_STATIC || (queue == GFS_QUEUE_STATIC && client_blocks == 0))
     return -EINVAL;
   int fd = open(path, O_RDONLY | O_CLOEXEC);
   if (fd < 0) return -errno;
@@ -1448,6 +1521,7 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
   sc.staging_pages = std::max<uint32_t>(1, (uint32_t)std::min<uint64_t>(4, max_pages));
   sc.threads = threads;
   sc.n_frames = frames;
+  sc.queue = queue;
   const size_t stg = (size_t)sc.staging_pages * page_size;
   IoService io(
       sc, [&](int) -> Sink* { return new HostSink(fr.data(), state.data(), shift, stg); },
@@ -1475,7 +1549,8 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
     uint64_t page_lo;
     uint32_t n, frame0;
   };
-  uint32_t done = 0;
+  uint32_t done = 0, issued = 0;
+  std::vector<uint64_t> lap(slots, 0);
   const uint32_t batch_max = std::max<uint32_t>(1, std::min<uint32_t>(slots, frames / max_pages));
   while (done < requests && !bad && npages) {
     std::vector<Pending> batch;
@@ -1488,6 +1563,11 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
       if (next_frame + p.n > frames) break;
       next_frame += p.n;
       for (uint32_t i = 0; i < p.n; ++i) __atomic_store_n(&state[p.frame0 + i], (uint32_t)FR_FILLING, __ATOMIC_RELAXED);
+      if (queue == GFS_QUEUE_STATIC) {  // the client block's own slot, numbered by its uses
+        const uint32_t si = (issued % client_blocks) % slots;
+        ticket = lap[si]++ * slots + si;
+      }
+      ++issued;
       RingSlot* s = (RingSlot*)(rb + (size_t)(ticket % slots) * stride);
       const double t0 = now_s();
       while (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != ticket)
@@ -1539,6 +1619,8 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
   io.stop();
   close(fd);
   if (h_served) *h_served = io.stats.requests.load();
+  if (h_thread_requests)
+    for (uint32_t i = 0; i < threads; ++i) h_thread_requests[i] = io.thread_counters(i).requests.load();
   return bad ? -(int)(1000 + bad) : 0;
 }
 

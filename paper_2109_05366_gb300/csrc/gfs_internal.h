@@ -105,7 +105,10 @@ static_assert(sizeof(FileDev) == 48, "FileDev");
 // Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; the GPU
 // producer with ticket t waits for seq == t, fills the slot and publishes
 // seq = t + 1; the host consumer with ticket h waits for seq == h + 1, copies the
-// request out and frees the slot with seq = h + R.
+// request out and frees the slot with seq = h + R.  Tickets of slot i are
+// i, i + R, i + 2R, ...: GFS_QUEUE_SHARED hands out tickets in order from one
+// counter (slot = ticket mod R); GFS_QUEUE_STATIC picks the slot from the
+// threadblock and numbers that slot's uses (ticket = lap * R + slot).
 struct RingSlot {
   unsigned long long seq;
   uint32_t fid;
@@ -172,6 +175,8 @@ struct DevHandle {
   // request ring (device view of mapped pinned memory) and its per-slot path buffers
   uint8_t* ring;
   char* paths;                   // rpc_slots * GFS_PATH_MAX bytes, mapped pinned
+  uint32_t queue;                // GFS_QUEUE_*
+  unsigned long long* slot_lap;  // GFS_QUEUE_STATIC: per slot, requests placed in it so far
   // traces
   gfs_rpc_rec* trace_rpc;
   gfs_evict_rec* trace_evict;

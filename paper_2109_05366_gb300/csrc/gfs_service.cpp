@@ -20,7 +20,11 @@ static inline uint64_t mono_ns() {
 }
 
 IoService::IoService(const ServiceConfig& cfg, SinkFactory make_sink, FileLookup files, Control control)
-    : cfg_(cfg), make_sink_(std::move(make_sink)), files_(std::move(files)), control_(std::move(control)) {}
+    : cfg_(cfg), make_sink_(std::move(make_sink)), files_(std::move(files)), control_(std::move(control)) {
+  tstats_.reset(new ThreadCounters[cfg_.threads ? cfg_.threads : 1]);
+  io_trace_.resize(cfg_.io_trace_cap);
+  t0_ns_.store(mono_ns());
+}
 
 IoService::~IoService() { stop(); }
 
@@ -65,7 +69,51 @@ void IoService::set_faults(uint32_t eio_every, uint32_t short_every, uint32_t de
   delay_us_.store(delay_us);
 }
 
-ssize_t IoService::do_pread(int fd, uint8_t* buf, size_t n, uint64_t off) {
+void IoService::clear_stats() {
+  stats.clear();
+  for (uint32_t i = 0; i < cfg_.threads; ++i) {
+    ThreadCounters& c = tstats_[i];
+    c.got_first.store(false, std::memory_order_relaxed);
+    c.requests = 0;
+    c.polls_before_first = 0;
+    c.first_ns = 0;
+    c.idle_ns = 0;
+    c.pread_ns = 0;
+    c.bytes = 0;
+  }
+  io_n_.store(0, std::memory_order_release);
+  t0_ns_.store(mono_ns(), std::memory_order_release);
+}
+
+void IoService::polled_empty(int idx, uint64_t idle_ns) {
+  ThreadCounters& c = tstats_[idx];
+  if (!c.got_first.load(std::memory_order_relaxed)) c.polls_before_first.fetch_add(1, std::memory_order_relaxed);
+  if (idle_ns) c.idle_ns.fetch_add(idle_ns, std::memory_order_relaxed);
+}
+
+void IoService::took_request(int idx) {
+  ThreadCounters& c = tstats_[idx];
+  c.requests.fetch_add(1, std::memory_order_relaxed);
+  if (!c.got_first.load(std::memory_order_relaxed)) {
+    const uint64_t t0 = t0_ns_.load(std::memory_order_relaxed), now = mono_ns();
+    c.first_ns.store(now > t0 ? now - t0 : 1, std::memory_order_relaxed);
+    c.got_first.store(true, std::memory_order_relaxed);
+  }
+}
+
+void IoService::record_io(int idx, uint32_t fid, uint64_t off, uint64_t bytes, uint64_t t_ns) {
+  if (io_trace_.empty()) return;
+  const uint64_t i = io_n_.fetch_add(1, std::memory_order_relaxed);
+  if (i >= io_trace_.size()) return;
+  gfs_io_rec& r = io_trace_[i];
+  r.offset = off;
+  r.bytes = bytes;
+  r.fid = fid;
+  r.thread = (uint32_t)idx;
+  r.t_ns = t_ns;
+}
+
+ssize_t IoService::do_pread(int idx, int fd, uint8_t* buf, size_t n, uint64_t off) {
   const uint64_t k = pread_count_.fetch_add(1, std::memory_order_relaxed);
   const uint32_t eio = eio_every_.load(std::memory_order_relaxed);
   const uint32_t sh = short_every_.load(std::memory_order_relaxed);
@@ -76,9 +124,14 @@ ssize_t IoService::do_pread(int fd, uint8_t* buf, size_t n, uint64_t off) {
   const uint64_t t0 = mono_ns();
   struct Acc {
     std::atomic<uint64_t>& a;
+    std::atomic<uint64_t>& b;
     uint64_t t0;
-    ~Acc() { a.fetch_add(mono_ns() - t0, std::memory_order_relaxed); }
-  } acc{stats.ns_pread, t0};
+    ~Acc() {
+      const uint64_t d = mono_ns() - t0;
+      a.fetch_add(d, std::memory_order_relaxed);
+      b.fetch_add(d, std::memory_order_relaxed);
+    }
+  } acc{stats.ns_pread, tstats_[idx].pread_ns, t0};
   size_t got = 0;
   while (got < n) {
     ssize_t r = ::pread(fd, buf + got, n - got, (off_t)(off + got));
@@ -92,11 +145,15 @@ ssize_t IoService::do_pread(int fd, uint8_t* buf, size_t n, uint64_t off) {
   return (ssize_t)got;
 }
 
-void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames) {
+void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames) {
+  Sink* sink = w.sink;
+  int& cur = w.cur;
   FileView fv{-1, 0, 0};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
   const uint64_t off0 = page_lo << cfg_.page_shift;
+  if (have && off0 < fv.size)
+    record_io(w.idx, fid, off0, std::min<uint64_t>((uint64_t)npages * P, fv.size - off0), mono_ns());
   bool full[MAX_RPC_PAGES];
   for (uint32_t c0 = 0; c0 < npages; c0 += cfg_.staging_pages) {
     const uint32_t cn = std::min(cfg_.staging_pages, npages - c0);
@@ -108,13 +165,14 @@ void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint
     if (have && coff < fv.size) want = (size_t)std::min<uint64_t>((uint64_t)cn * P, fv.size - coff);
     ssize_t got = 0;
     if (want) {
-      got = do_pread(fv.fd, buf, want, coff);
+      got = do_pread(w.idx, fv.fd, buf, want, coff);
       stats.preads.fetch_add(1, std::memory_order_relaxed);
       if (got < 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);
         got = 0;
       } else {
         stats.bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
+        tstats_[w.idx].bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
       }
     }
     // Section 4.1: the returned size decides which pages are delivered.
@@ -146,12 +204,16 @@ void IoService::serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint
   }
 }
 
-void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
+void IoService::serve_pull(Worker& w, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
                            uint32_t npages) {
+  const int idx = w.idx;
+  uint32_t& cur = w.pull_cur;
   FileView fv{-1, 0, 0};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
   const uint64_t off0 = page_lo << cfg_.page_shift;
+  if (have && off0 < fv.size)
+    record_io(idx, fid, off0, std::min<uint64_t>((uint64_t)npages * P, fv.size - off0), mono_ns());
   const uint32_t cpages = (uint32_t)(cfg_.chunk_bytes >> cfg_.page_shift);
   long long total = have ? 0 : -EBADF;
   if (have && fv.dev_map) {  // mapped file: the pages are already in host memory the GPU can read
@@ -172,7 +234,10 @@ void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticke
       if (!fail && base < fv.size) total += (long long)std::min<uint64_t>(P, fv.size - base);
       __atomic_store_n(&pp->tag, ticket + 1, __ATOMIC_RELEASE);
     }
-    if (total > 0) stats.bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
+    if (total > 0) {
+      stats.bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
+      tstats_[idx].bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
+    }
     PullDone* d = cfg_.pull_done + slot;
     __atomic_store_n(&d->result, total, __ATOMIC_RELAXED);
     __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);
@@ -200,7 +265,7 @@ void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticke
     if (have && coff < fv.size) want = (size_t)std::min<uint64_t>((uint64_t)cn * P, fv.size - coff);
     ssize_t got = 0;
     if (want) {
-      got = do_pread(fv.fd, buf, want, coff);
+      got = do_pread(idx, fv.fd, buf, want, coff);
       stats.preads.fetch_add(1, std::memory_order_relaxed);
       if (got < 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);
@@ -208,6 +273,7 @@ void IoService::serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticke
         got = 0;
       } else {
         stats.bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
+        tstats_[idx].bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
         if (total >= 0) total += got;
       }
     }
@@ -249,12 +315,15 @@ void IoService::control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid) {
 }
 
 void IoService::run(int idx) {
-  Sink* sink = sinks_[idx];
-  sink->thread_init();
+  Worker w{idx, sinks_[idx], 0, 0u};
+  w.sink->thread_init();
   prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);  // short sleeps while polling the ring
-  int cur = 0;
-  uint32_t pull_cur = 0;
-  uint32_t frames[MAX_RPC_PAGES];
+  if (cfg_.queue == GFS_QUEUE_STATIC) run_static(w);
+  else run_shared(w);
+}
+
+// GFS_QUEUE_SHARED: take the next ticket and wait for its request.
+void IoService::run_shared(Worker& w) {
   while (!stop_.load(std::memory_order_relaxed)) {
     const uint64_t h = head_.fetch_add(1, std::memory_order_relaxed);
     RingSlot* s = (RingSlot*)(cfg_.ring + (size_t)(h % cfg_.slots) * cfg_.slot_stride);
@@ -263,42 +332,84 @@ void IoService::run(int idx) {
     while (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) {
       if (stop_.load(std::memory_order_relaxed)) return;
       ++spins;
+      polled_empty(w.idx, 0);
       if (spins > 20000) {
         struct timespec ts = {0, spins > 2000000 ? 50000 : 2000};
         nanosleep(&ts, nullptr);
       }
     }
-    stats.ns_idle.fetch_add(mono_ns() - i0, std::memory_order_relaxed);
-    const volatile RingSlot* vs = s;
-    const uint32_t fid = vs->fid;
-    const uint32_t npages = vs->npages;
-    const uint64_t page_lo = vs->page_lo;
-    const uint32_t op = vs->op;
-    const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
-    if (op == OP_OPEN || op == OP_CLOSE || op == OP_ADVISE) {
-      control(s, (uint32_t)(h % cfg_.slots), op, fid);
-      stats.controls.fetch_add(1, std::memory_order_relaxed);
-      served_.fetch_add(1, std::memory_order_release);
-      continue;
-    }
-    stats.requests.fetch_add(1, std::memory_order_relaxed);
-    if (cfg_.pull_arena) {  // the GPU frees the slot once it has copied the pages
-      serve_pull(idx, pull_cur, (uint32_t)(h % cfg_.slots), h, fid, page_lo,
-                 std::min<uint32_t>(npages, cfg_.max_pages));
-      served_.fetch_add(1, std::memory_order_release);
-      continue;
-    }
-    for (uint32_t i = 0; i < n; ++i) frames[i] = vs->frames[i];
-    __atomic_store_n(&s->seq, h + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
-    bool bad = npages == 0 || npages > MAX_RPC_PAGES;
-    for (uint32_t i = 0; i < n && !bad; ++i) bad = frames[i] >= cfg_.n_frames;
-    if (bad) {
-      stats.errors.fetch_add(1, std::memory_order_relaxed);
-    } else {
-      serve(sink, cur, fid, page_lo, n, frames);
-    }
-    served_.fetch_add(1, std::memory_order_release);
+    const uint64_t idle = mono_ns() - i0;
+    stats.ns_idle.fetch_add(idle, std::memory_order_relaxed);
+    tstats_[w.idx].idle_ns.fetch_add(idle, std::memory_order_relaxed);
+    handle(w, h, s);
   }
+}
+
+// GFS_QUEUE_STATIC (Section 3.2): thread k owns slots [k R / T, (k+1) R / T)
+// and sweeps them in turn; slot i's uses have tickets i, i + R, i + 2R, ...
+void IoService::run_static(Worker& w) {
+  const uint32_t T = cfg_.threads, R = cfg_.slots;
+  const uint32_t lo = (uint32_t)((uint64_t)w.idx * R / T), hi = (uint32_t)((uint64_t)(w.idx + 1) * R / T);
+  std::vector<uint64_t> lap(hi > lo ? hi - lo : 0, 0);
+  uint64_t sweeps = 0;
+  uint64_t i0 = mono_ns();
+  while (!stop_.load(std::memory_order_relaxed)) {
+    bool any = false;
+    for (uint32_t si = lo; si < hi; ++si) {
+      const uint64_t h = lap[si - lo] * R + si;
+      RingSlot* s = (RingSlot*)(cfg_.ring + (size_t)si * cfg_.slot_stride);
+      if (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) continue;
+      const uint64_t idle = mono_ns() - i0;
+      stats.ns_idle.fetch_add(idle, std::memory_order_relaxed);
+      tstats_[w.idx].idle_ns.fetch_add(idle, std::memory_order_relaxed);
+      ++lap[si - lo];
+      any = true;
+      handle(w, h, s);
+      i0 = mono_ns();
+    }
+    if (any) {
+      sweeps = 0;
+      continue;
+    }
+    polled_empty(w.idx, 0);
+    if (++sweeps > 20000) {
+      struct timespec ts = {0, sweeps > 2000000 ? 50000 : 2000};
+      nanosleep(&ts, nullptr);
+    }
+  }
+}
+
+void IoService::handle(Worker& w, uint64_t h, RingSlot* s) {
+  uint32_t frames[MAX_RPC_PAGES];
+  took_request(w.idx);
+  const volatile RingSlot* vs = s;
+  const uint32_t fid = vs->fid;
+  const uint32_t npages = vs->npages;
+  const uint64_t page_lo = vs->page_lo;
+  const uint32_t op = vs->op;
+  const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
+  if (op == OP_OPEN || op == OP_CLOSE || op == OP_ADVISE) {
+    control(s, (uint32_t)(h % cfg_.slots), op, fid);
+    stats.controls.fetch_add(1, std::memory_order_relaxed);
+    served_.fetch_add(1, std::memory_order_release);
+    return;
+  }
+  stats.requests.fetch_add(1, std::memory_order_relaxed);
+  if (cfg_.pull_arena) {  // the GPU frees the slot once it has copied the pages
+    serve_pull(w, (uint32_t)(h % cfg_.slots), h, fid, page_lo, std::min<uint32_t>(npages, cfg_.max_pages));
+    served_.fetch_add(1, std::memory_order_release);
+    return;
+  }
+  for (uint32_t i = 0; i < n; ++i) frames[i] = vs->frames[i];
+  __atomic_store_n(&s->seq, h + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
+  bool bad = npages == 0 || npages > MAX_RPC_PAGES;
+  for (uint32_t i = 0; i < n && !bad; ++i) bad = frames[i] >= cfg_.n_frames;
+  if (bad) {
+    stats.errors.fetch_add(1, std::memory_order_relaxed);
+  } else {
+    serve(w, fid, page_lo, n, frames);
+  }
+  served_.fetch_add(1, std::memory_order_release);
 }
 
 }  // namespace gfs

@@ -3,14 +3,16 @@
 // Section 4.1: one pread serves every page of a readahead request, and the
 // returned size decides which pages are delivered).
 //
-// Unlike GPUfs, which gives each host thread a fixed slice of the queue and so
-// leaves threads idle when the running threadblocks map to one slice
-// (Section 3.2), every thread takes the next ticket of one shared ring.
+// GFS_QUEUE_SHARED (default): every thread takes the next ticket of one shared
+// ring.  GFS_QUEUE_STATIC is GPUfs as Section 3.2 describes it: each thread
+// polls a fixed slice of the slots, which leaves threads idle when the running
+// threadblocks map to other slices.
 #pragma once
 
 #include <atomic>
 #include <cstdint>
 #include <functional>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -63,6 +65,14 @@ struct ServiceConfig {
   uint32_t max_pages = 0;
   // device opens: per-slot path buffers (host view), GFS_PATH_MAX bytes each
   const char* paths = nullptr;
+  uint32_t queue = GFS_QUEUE_SHARED;  // GFS_QUEUE_*: how a thread finds its requests
+  uint64_t io_trace_cap = 0;          // host I/O trace entries kept (0 = off)
+};
+
+// Counters of one host thread (gfs_thread_stat).
+struct ThreadCounters {
+  std::atomic<uint64_t> requests{0}, polls_before_first{0}, first_ns{0}, idle_ns{0}, pread_ns{0}, bytes{0};
+  std::atomic<bool> got_first{false};
 };
 
 struct ServiceStats {
@@ -92,15 +102,34 @@ class IoService {
   // Wait for all sinks' queued work.
   void drain_sinks();
   void set_faults(uint32_t eio_every, uint32_t short_every, uint32_t delay_us);
+  // Zero the service and per-thread counters and the I/O trace (a quiet point).
+  void clear_stats();
+  uint32_t threads() const { return cfg_.threads; }
+  const ThreadCounters& thread_counters(uint32_t i) const { return tstats_[i]; }
+  // I/O trace: ranges recorded so far (may exceed the capacity) and the records kept.
+  uint64_t io_trace_count() const { return io_n_.load(std::memory_order_acquire); }
+  const gfs_io_rec* io_trace() const { return io_trace_.data(); }
   ServiceStats stats;
 
  private:
+  struct Worker {  // one host thread's serving state
+    int idx;
+    Sink* sink;
+    int cur;
+    uint32_t pull_cur;
+  };
   void run(int idx);
+  void run_shared(Worker& w);
+  void run_static(Worker& w);
+  // Serve the published request with ticket h in slot s.
+  void handle(Worker& w, uint64_t h, RingSlot* s);
   void control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid);
-  void serve(Sink* sink, int& cur, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
-  void serve_pull(int idx, uint32_t& cur, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
-                  uint32_t npages);
-  ssize_t do_pread(int fd, uint8_t* buf, size_t n, uint64_t off);
+  void serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
+  void serve_pull(Worker& w, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages);
+  ssize_t do_pread(int idx, int fd, uint8_t* buf, size_t n, uint64_t off);
+  void record_io(int idx, uint32_t fid, uint64_t off, uint64_t bytes, uint64_t t_ns);
+  void polled_empty(int idx, uint64_t idle_ns);
+  void took_request(int idx);
 
   ServiceConfig cfg_;
   SinkFactory make_sink_;
@@ -113,6 +142,10 @@ class IoService {
   std::atomic<uint64_t> served_{0};
   std::atomic<uint64_t> pread_count_{0};
   std::atomic<uint32_t> eio_every_{0}, short_every_{0}, delay_us_{0};
+  std::unique_ptr<ThreadCounters[]> tstats_;
+  std::atomic<uint64_t> t0_ns_{0};  // start of the current counting period
+  std::vector<gfs_io_rec> io_trace_;
+  std::atomic<uint64_t> io_n_{0};
 };
 
 }  // namespace gfs

@@ -20,6 +20,7 @@ MODE_READAHEAD, MODE_ONDEMAND, MODE_PAPER = 0, 1, 2
 REPL_FIFO, REPL_TB_LRA = 0, 1
 ADV_NORMAL, ADV_SEQUENTIAL, ADV_RANDOM = 0, 1, 2
 XFER_DMA, XFER_PULL, XFER_MAPPED = 0, 1, 2
+QUEUE_SHARED, QUEUE_STATIC = 0, 1
 KIND_DEMAND, KIND_SYNC_RA, KIND_ASYNC_RA = 0, 1, 2
 PATH_MAX = 1024
 
@@ -32,7 +33,8 @@ class Config(ctypes.Structure):
                 ("ra_cap_pages", u32), ("async_ra", u32), ("reserve_frames", u32), ("rpc_slots", u32),
                 ("max_rpc_pages", u32), ("host_threads", u32), ("staging_bytes", u32), ("max_streams", u32),
                 ("max_files", u32), ("trace_capacity", u32), ("xfer", u32), ("debug_counts", u32),
-                ("device", i32), ("latency_capacity", u32), ("replacement", u32), ("reserved", u32 * 5)]
+                ("device", i32), ("latency_capacity", u32), ("replacement", u32), ("queue", u32),
+                ("reserved", u32 * 4)]
 
 
 class Stat(ctypes.Structure):
@@ -48,6 +50,15 @@ STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fe
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 3)]
+
+
+class ThreadStat(ctypes.Structure):
+    _fields_ = [("requests", u64), ("polls_before_first", u64), ("first_request_ns", u64), ("idle_ns", u64),
+                ("pread_ns", u64), ("bytes", u64)]
+
+
+class IoRec(ctypes.Structure):
+    _fields_ = [("offset", u64), ("bytes", u64), ("fid", u32), ("thread", u32), ("t_ns", u64)]
 
 
 class RpcRec(ctypes.Structure):
@@ -89,6 +100,10 @@ SIGNATURES = {
     "gfs_get_trace": (ctypes.c_int, [vp, ctypes.POINTER(RpcRec), ctypes.POINTER(EvictRec), u32,
                                      ctypes.POINTER(u64), ctypes.POINTER(u64), vp]),
     "gfs_get_fetch_counts": (ctypes.c_int, [vp, vp, u64, vp]),
+    "gfs_get_thread_stats": (ctypes.c_int, [vp, ctypes.POINTER(ThreadStat), u32]),
+    "gfs_get_io_trace": (ctypes.c_int, [vp, ctypes.POINTER(IoRec), u64, ctypes.POINTER(u64)]),
+    "gfs_replay_io": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(IoRec), u64, u32,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)]),
     "gfs_get_latencies": (ctypes.c_int, [vp, vp, u64, ctypes.POINTER(u64), vp]),
     "gfs_scan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
     "gfs_scan_host": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), vp, vp, vp, vp]),
@@ -102,7 +117,8 @@ SIGNATURES = {
     "gfs_probe_h2d": (ctypes.c_int, [u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pread": (ctypes.c_int, [ctypes.c_char_p, u32, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pull": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
-    "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u64, ctypes.POINTER(u64)]),
+    "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u32, u32, u64,
+                                         ctypes.POINTER(u64), vp]),
     "gfs_rowdot": (ctypes.c_int, [vp, ctypes.c_int, u32, u32, vp, vp, u32, u64, u32, vp, vp, vp, vp]),
     "gfs_histogram": (ctypes.c_int, [vp, ctypes.c_int, u32, vp, u64, u32, vp, vp, vp]),
     "gfs_serve_start": (ctypes.c_int, [vp, ctypes.POINTER(ServeConfig), vp]),
@@ -252,6 +268,20 @@ class Context:
         _check(load().gfs_get_latencies(self.handle, out.ctypes.data, cap, ctypes.byref(n), _stream(stream)),
                "gfs_get_latencies")
         return out[:min(cap, n.value)]
+
+    def thread_stats(self) -> list[dict]:
+        """Per host I/O thread counters since the last reset."""
+        arr = (ThreadStat * 256)()
+        n = _check(load().gfs_get_thread_stats(self.handle, arr, 256), "gfs_get_thread_stats")
+        return [{f: int(getattr(arr[i], f)) for f, _ in ThreadStat._fields_} for i in range(min(n, 256))]
+
+    def io_trace(self) -> list:
+        """Host I/O trace (IoRec records) since the last reset."""
+        cap = int(self.cfg.trace_capacity)
+        arr = (IoRec * max(cap, 1))()
+        n = u64()
+        _check(load().gfs_get_io_trace(self.handle, arr, cap, ctypes.byref(n)), "gfs_get_io_trace")
+        return list(arr[:min(cap, n.value)])
 
     def fetch_counts(self, n: int, stream=None) -> np.ndarray:
         out = np.zeros(n, dtype=np.uint32)
@@ -420,11 +450,29 @@ def probe_pread(path: str, threads: int, chunk: int, reps: int = 2) -> float:
 
 
 def selftest_ring(path: str, page_size: int = 4096, frames: int = 256, requests: int = 500, max_pages: int = 8,
-                  threads: int = 4, slots: int = 16, seed: int = 1) -> int:
+                  threads: int = 4, slots: int = 16, seed: int = 1, queue: int = QUEUE_SHARED,
+                  client_blocks: int = 0, per_thread: bool = False):
+    """Requests served (and, with per_thread, each host thread's request count)."""
     served = u64()
-    _check(load().gfs_selftest_ring(path.encode(), page_size, frames, requests, max_pages, threads, slots, seed,
-                                    ctypes.byref(served)), "gfs_selftest_ring")
-    return served.value
+    counts = np.zeros(threads, dtype=np.uint64)
+    _check(load().gfs_selftest_ring(path.encode(), page_size, frames, requests, max_pages, threads, slots, queue,
+                                    client_blocks, seed, ctypes.byref(served), counts.ctypes.data),
+           "gfs_selftest_ring")
+    return (served.value, counts.tolist()) if per_thread else served.value
+
+
+def replay_io(path: str, recs, threads: int):
+    """CPU replay of a host I/O trace (list of IoRec or (offset, bytes) pairs): (seconds, bytes)."""
+    arr = (IoRec * max(len(recs), 1))()
+    for i, r in enumerate(recs):
+        if isinstance(r, IoRec):
+            arr[i] = r
+        else:
+            arr[i].offset, arr[i].bytes = r
+    secs, nbytes = ctypes.c_double(), u64()
+    _check(load().gfs_replay_io(path.encode(), arr, len(recs), threads, ctypes.byref(secs), ctypes.byref(nbytes)),
+           "gfs_replay_io")
+    return secs.value, nbytes.value
 
 
 def u64_view(t) -> np.ndarray:

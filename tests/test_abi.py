@@ -27,7 +27,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_abi_version_and_errors():
     lib = gfs.load()
-    assert lib.gfs_abi_version() == 1
+    assert lib.gfs_abi_version() == 2
     assert lib.gfs_strerror(-22) == b"invalid argument"
     assert lib.gfs_strerror(-110) == b"device wait timed out"
 
@@ -43,7 +43,10 @@ def test_struct_layouts_match_header(tmp_path):
     # compile a C program against include/gfs.h and compare sizes/offsets with ctypes
     import ctypes
     import subprocess
-    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "replacement", "reserved"]),
+    checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "replacement",
+                                          "queue", "reserved"]),
+              ("gfs_thread_stat", gfs.ThreadStat, ["requests", "first_request_ns", "bytes"]),
+              ("gfs_io_rec", gfs.IoRec, ["offset", "bytes", "fid", "thread", "t_ns"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
               ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "host_controls", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
@@ -90,6 +93,36 @@ def test_ring_and_service_selftest(tmp_path, page, frames, requests, max_pages, 
     inputs.write_file(path, 3, size)
     served = gfs.selftest_ring(path, page, frames, requests, max_pages, threads, slots, seed=7)
     assert served == requests
+
+
+@pytest.mark.parametrize("threads,slots,blocks", [(4, 64, 16), (4, 64, 48), (8, 16, 40), (3, 10, 7)])
+def test_static_queue_selftest_leaves_unowned_threads_idle(tmp_path, threads, slots, blocks):
+    """Section 3.2: with slot = block index and each host thread polling a fixed
+    contiguous share of the slots, only the threads whose share holds a client
+    block's slot ever serve; every request is still served exactly."""
+    path = str(tmp_path / "f.bin")
+    inputs.write_file(path, 3, (2 << 20) + 77)
+    served, per = gfs.selftest_ring(path, 4096, 512, 1500, 8, threads, slots, seed=5, queue=gfs.QUEUE_STATIC,
+                                    client_blocks=blocks, per_thread=True)
+    assert served == 1500 and sum(per) == 1500
+    used = {b % slots for b in range(blocks)}
+    for k in range(threads):
+        lo, hi = k * slots // threads, (k + 1) * slots // threads
+        owns = any(lo <= s < hi for s in used)
+        assert (per[k] > 0) == owns, (k, per)
+    served, per = gfs.selftest_ring(path, 4096, 512, 1500, 8, threads, slots, seed=5, per_thread=True)
+    assert served == 1500 and sum(per) == 1500
+
+
+def test_replay_reads_the_recorded_ranges(tmp_path):
+    path = str(tmp_path / "f.bin")
+    size = (3 << 20) + 5
+    inputs.write_file(path, 4, size)
+    recs = [(0, 1 << 20), (1 << 20, 1 << 20), (3 << 20, 5), (size - 100, 100), (4096, 0)]
+    secs, nbytes = gfs.replay_io(path, recs, 3)
+    assert nbytes == sum(b for _, b in recs) and secs >= 0
+    secs, nbytes = gfs.replay_io(path, [(size, 4096)], 2)  # past EOF: nothing read, no error
+    assert nbytes == 0
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
