@@ -140,6 +140,14 @@ def data_dir():
     return tempfile.gettempdir()
 
 
+# DRAM bytes per scanned file byte of k_scan, from the ncu capture summarised in
+# profiles/k_scan_cfg2s_2GiB_sol.md (2 GiB case; traffic grows with the bytes scanned),
+# valid only for the library build it was taken on.
+NCU_DRAM = {"build_digest": "95cef848c1136f46e5d18853ada37397e8baf30cb5f232b12be7dafdb89a0cf0",
+            "bytes_per_file_byte": (2.247664e9 + 4.322181e9) / (2 * GiB),
+            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 2 GiB case scaled by bytes scanned"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -815,8 +823,13 @@ def run_gfs(args):
                                     "p99": round(float(np.percentile(lat, 99)) / 1e3, 1),
                                     "greads": int(len(lat)), "read_len": stride}
     if binding:
+        from paper_2109_05366_gb300 import build as _b
+        traffic = None
+        if _b._digest() == NCU_DRAM["build_digest"] and args.xfer == "mapped" and not args.fused:
+            traffic = int(NCU_DRAM["bytes_per_file_byte"] * size)  # DRAM bytes per launch
         line["roofline"] = {"bound": "link", "achieved": round(value / world, 2), "peak": round(binding, 1),
-                            "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": None,
+                            "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": traffic,
+                            "traffic_source": NCU_DRAM["source"] if traffic else None,
                             "peak_source": "measured in this run: " + binding_src}
         hbm = peaks.get("hbm_gbs", 6800.0)
         line["hbm_roofline"] = {"bound": "hbm", "achieved": round(nbytes_hbm / kt / 1e9, 1), "peak": hbm,
