@@ -800,7 +800,8 @@ def run_gfs(args):
     kt = sum(times) / len(times)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(1e3 * kt, 3), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * kt, 3), "step_ms": [round(1e3 * t, 2) for t in times],
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded xorshift64 file, warm host page cache)",
         "config": {"workload": args.workload, "file_bytes": size, "page_bytes": page, "cache_bytes": cache,

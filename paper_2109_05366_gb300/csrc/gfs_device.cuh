@@ -614,8 +614,11 @@ __device__ __forceinline__ void pull_finish(const DevHandle& g, const PullJob& j
     __threadfence_system();
     atomicAdd_system(&g.bcount[j.buf], 0xffffffffu);  // -1: the host may reuse the buffer once 0
   }
+  // the page count is read while this page's claim still keeps the slot from
+  // being freed: after the increment a later request may own the slot
+  const uint32_t np = ld_rlx(&g.dnpages[j.s]);
   const uint32_t c = atomicAdd(&g.dcopied[j.s], 1u) + 1;
-  if (c == ld_rlx(&g.dnpages[j.s])) {
+  if (c == np) {
     __threadfence_system();
     st_rel_sys64(&ring_slot(g, j.s)->seq, j.t + g.rpc_slots);
     atomicAdd(&g.ctrl->freed.v, 1ull);
@@ -633,11 +636,62 @@ static __device__ bool warp_help(const DevHandle& g, uint32_t start) {
   return true;
 }
 
+// One warp, after claiming page j.i of request (j.s, ticket j.t): claim up to
+// `want` more published pages of the same request (their frames FILLING ->
+// COPYING, as one claim each).  Claimed pages go to out[0 .. count).
+static __device__ int pull_claim_more(const DevHandle& g, const PullJob& j, int want, PullJob* out) {
+  const int lane = lane_id();
+  const uint32_t np = ld_rlx(&g.dnpages[j.s]);
+  int got = 0;
+  for (uint32_t base = 0; base < np && got < want; base += 32) {
+    const uint32_t i = base + (uint32_t)lane;
+    int f = -1;
+    if (i < np && i != j.i) {
+      f = (int)ld_rlx(&g.dframes[(size_t)j.s * g.max_rpc_pages + i]);
+      if (f >= (int)g.n_frames || ld_rlx(&g.fstate[f]) != FR_FILLING ||
+          ld_acq(&g.fsrc[f]) != j.s * g.max_rpc_pages + i ||
+          ld_acq_sys64(&g.pages[(size_t)j.s * g.max_rpc_pages + i].tag) != j.t + 1)
+        f = -1;
+    }
+    const unsigned cm = __ballot_sync(kFull, f >= 0);
+    const int rank = __popc(cm & ((1u << lane) - 1u));
+    bool mine = false;
+    if (f >= 0 && rank < want - got &&
+        atomicCAS(&g.fstate[f], (uint32_t)FR_FILLING, (uint32_t)FR_COPYING) == FR_FILLING) {
+      __threadfence();
+      mine = ld_rlx64(&g.dticket[j.s]) == j.t;  // the claim stands for the request that was checked
+      if (!mine) st_rel(&g.fstate[f], (uint32_t)FR_FILLING);
+    }
+    const unsigned mm = __ballot_sync(kFull, mine);
+    if (mine) {
+      PullJob k{f, j.s, i, 0, 0, j.t, 0};
+      pull_read_page(g, k);
+      out[got + __popc(mm & ((1u << lane) - 1u))] = k;
+    }
+    got += __popc(mm);
+  }
+  return got;
+}
+
+// Pages of one request a helping block copies in one pass: small pages are
+// copied a warp per page, many at once, so their claim, descriptor and copy
+// round trips overlap; large pages keep one page per pass, the whole block on it.
+__device__ __forceinline__ int help_batch(const DevHandle& g) {
+  if (g.page_size <= (16u << 10)) return 32;
+  if (g.page_size <= (64u << 10)) return 4;
+  return 1;
+}
+
 // Whole block: copy frame f if served (target >= 0), else help with any served
-// page.  Returns true if the block copied a page.  Block-uniform.
+// page; with small pages, also further served pages of the same request.
+// Returns true if the block copied a page.  Block-uniform.
 static __device__ bool block_help(const DevHandle& g, int target, bool any) {
   __shared__ PullJob s_job;
+  __shared__ PullJob s_more[31];
+  __shared__ int s_nmore;
+  __shared__ uint32_t s_ok[32];
   const uint32_t tid = threadIdx.x;
+  const int batch = help_batch(g);
   if (tid < 32) {
     PullJob j{-1, 0, 0, 0, 0, 0, 0};
     if (target >= 0 && tid == 0) j = pull_claim_frame(g, target);
@@ -646,15 +700,51 @@ static __device__ bool block_help(const DevHandle& g, int target, bool any) {
       const uint32_t start = (uint32_t)((blockIdx.x * 37u + (uint32_t)(now_ns() >> 10)) % g.rpc_slots);
       j = pull_claim_any(g, start);
     }
-    if (tid == 0) s_job = j;
+    int nmore = 0;
+    if (j.f >= 0 && batch > 1) {
+      // every lane needs the claimed job (lane 0 or the claiming lane filled it)
+      PullJob b;
+      b.f = __shfl_sync(kFull, j.f, 0);
+      b.s = __shfl_sync(kFull, j.s, 0);
+      b.i = __shfl_sync(kFull, j.i, 0);
+      b.t = __shfl_sync(kFull, j.t, 0);
+      b.buf = 0;
+      b.ok = 0;
+      b.src = 0;
+      nmore = pull_claim_more(g, b, batch - 1, s_more);
+    }
+    if (tid == 0) {
+      s_job = j;
+      s_nmore = nmore;
+    }
   }
   __syncthreads();
   const PullJob j = s_job;
+  const int nmore = s_nmore;
   __syncthreads();
   if (j.f < 0) return false;
-  const bool ok = pull_copy(g, j, tid, blockDim.x);
+  if (nmore == 0) {
+    const bool ok = pull_copy(g, j, tid, blockDim.x);
+    __syncthreads();
+    if (tid == 0) pull_finish(g, j, ok);
+    return true;
+  }
+  const uint32_t nw = blockDim.x >> 5, w = tid >> 5, lane = tid & 31u;
+  if (g.page_size <= (16u << 10)) {  // a warp per page
+    for (int k = (int)w; k <= nmore; k += (int)nw) {
+      const PullJob jk = k == 0 ? j : s_more[k - 1];
+      const bool ok = pull_copy(g, jk, lane, 32);
+      if (lane == 0) s_ok[k] = ok ? 1u : 0u;
+    }
+  } else {  // the whole block on each page in turn
+    for (int k = 0; k <= nmore; ++k) {
+      const PullJob jk = k == 0 ? j : s_more[k - 1];
+      const bool ok = pull_copy(g, jk, tid, blockDim.x);
+      if (tid == 0) s_ok[k] = ok ? 1u : 0u;
+    }
+  }
   __syncthreads();
-  if (tid == 0) pull_finish(g, j, ok);
+  if (tid <= (uint32_t)nmore) pull_finish(g, tid == 0 ? j : s_more[tid - 1], s_ok[tid] != 0u);
   return true;
 }
 
