@@ -4,7 +4,7 @@
 //   * one device arena (cudaMalloc): cache frames, per-frame metadata, the page
 //     table, the consumed FIFO, control counters, traces;
 //   * the request ring in mapped pinned host memory, written by the GPU and
-//     served by the host I/O threads (Section 2.2 "shared CPU-GPU request queue").
+//     served by the host I/O threads (Section 2.2: the request queue GPU and host share).
 #pragma once
 
 #include <stdint.h>
