@@ -69,8 +69,13 @@ Paper mode (mode="paper"; Sections 4.1 and 5.1 as the paper designs them):
   P2 replacement "tb_lra": each stream keeps the frames it allocated in
      allocation order, at most quota = max(1, F // streams) of them; below the
      quota it takes a never-used frame, at the quota it evicts its own least
-     recently allocated frame and reuses it (remapping it in the page table).
-     replacement "fifo" uses rule R6 instead.
+     recently allocated frame and reuses it (remapping it in the page table);
+     a frame of the request being built or the page being delivered is passed
+     over (it moves to the newest end).  replacement "fifo" uses rule R6 instead.
+     P2 also combines with modes "readahead" and "ondemand": every frame a
+     request takes, demand or readahead, then comes from the requesting
+     stream's queue, and the quota takes the place of the readahead reserve
+     (readahead just stops when the stream has no frame to pass).
 A demand page that finds no victim at all (every frame belongs to the current
 gread) makes the gread return -ENOMEM; later pages of a demand run just end the
 request early.
@@ -272,7 +277,7 @@ class PageCacheSim:
             self.stats.fetch_count[key] = self.stats.fetch_count.get(key, 0) + 1
         self._busy.clear()
 
-    def _request(self, fi: FileInfo, fid: int, p: int, want: int, demand: int,
+    def _request(self, stream: int, fi: FileInfo, fid: int, p: int, want: int, demand: int,
                  gread_seq0: int) -> list[int]:
         """Allocate frames for [p, p+want), cut at EOF / present page / allowance."""
         want = min(want, self.max_rpc)
@@ -283,7 +288,10 @@ class PageCacheSim:
             if q - p >= demand and (fid, q) in self.fetched:      # R8
                 break
             try:
-                f = self._take(q - p >= demand, gread_seq0, (fid, q))
+                if self.replacement == "tb_lra":                   # P2
+                    f = self._take_lra(stream, q - p >= demand, (fid, q))
+                else:
+                    f = self._take(q - p >= demand, gread_seq0, (fid, q))
             except NoFrame:
                 if q == p:
                     raise
@@ -296,9 +304,8 @@ class PageCacheSim:
         return taken
 
     # ---- paper mode (P1, P2) -----------------------------------------------------
-    def _take_paper(self, stream: int, gread_seq0: int, new_key) -> int:
-        if self.replacement == "fifo":
-            return self._take(False, gread_seq0, new_key)
+    def _take_lra(self, stream: int, for_readahead: bool, new_key) -> int | None:
+        """P2: the stream's own least recently allocated frame (None: readahead stops)."""
         q = self.lra.setdefault(stream, deque())
         if len(q) < self.quota and self.next_unused < self.F:
             f = self.next_unused
@@ -307,13 +314,19 @@ class PageCacheSim:
             return f
         for _ in range(len(q)):
             f = q.popleft()
+            q.append(f)
             if f == self._pinned or f in self._busy:
-                q.append(f)
                 continue
             self._evict(f, new_key)
-            q.append(f)
             return f
+        if for_readahead:
+            return None
         raise NoFrame("stream has no frame to reuse")
+
+    def _take_paper(self, stream: int, gread_seq0: int, new_key) -> int:
+        if self.replacement == "fifo":
+            return self._take(False, gread_seq0, new_key)
+        return self._take_lra(stream, False, new_key)
 
     def _miss_paper(self, stream: int, fi: FileInfo, fid: int, p: int, gread_seq0: int):
         self.stats.misses += 1
@@ -360,7 +373,7 @@ class PageCacheSim:
     def _miss(self, stream: int, fi: FileInfo, fid: int, p: int, p1: int, gread_seq0: int):
         self.stats.misses += 1
         if self.mode != "readahead" or not fi.readahead:            # R1 / R7
-            taken = self._request(fi, fid, p, 1, 1, gread_seq0)
+            taken = self._request(stream, fi, fid, p, 1, 1, gread_seq0)
             self._fetch(fi, fid, p, taken, DEMAND)
             return
         d = 0                                                         # R2
@@ -369,7 +382,7 @@ class PageCacheSim:
         seq = (p == 0 or (fid, p - 1) in self.table
                or self.last_end.get((stream, fid)) == p)              # R3
         if not seq:
-            taken = self._request(fi, fid, p, d, d, gread_seq0)
+            taken = self._request(stream, fi, fid, p, d, d, gread_seq0)
             self._fetch(fi, fid, p, taken, DEMAND)
             for f in taken:
                 self.frames[f].window = 0
@@ -377,7 +390,7 @@ class PageCacheSim:
         prev = self.table.get((fid, p - 1)) if p > 0 else None
         t_prev = self.frames[prev].window if prev is not None else 0
         T = min(d + self.Wmax, max(4 * d, 2 * t_prev), self.max_rpc)
-        taken = self._request(fi, fid, p, T, d, gread_seq0)
+        taken = self._request(stream, fi, fid, p, T, d, gread_seq0)
         n = len(taken)
         self._fetch(fi, fid, p, taken, SYNC_RA if n > d else DEMAND)
         for f in taken:
@@ -386,10 +399,10 @@ class PageCacheSim:
             self.frames[taken[d]].ra_end = p + n
 
     # ---- R4: a readahead mark ---------------------------------------------------
-    def _async(self, fi: FileInfo, fid: int, end: int, t: int, gread_seq0: int):
+    def _async(self, stream: int, fi: FileInfo, fid: int, end: int, t: int, gread_seq0: int):
         if end >= fi.npages or (fid, end) in self.table or (fid, end) in self.fetched:
             return
-        taken = self._request(fi, fid, end, min(self.Wmax, 2 * t), 0, gread_seq0)
+        taken = self._request(stream, fi, fid, end, min(self.Wmax, 2 * t), 0, gread_seq0)
         if not taken:
             return
         n = len(taken)
@@ -436,7 +449,7 @@ class PageCacheSim:
                 mark, fr.ra_end = fr.ra_end, -1
                 if self.async_ra and self.mode == "readahead" and fi.readahead:
                     self._pinned = f
-                    self._async(fi, fid, mark, fr.window, seq0)
+                    self._async(stream, fi, fid, mark, fr.window, seq0)
                     self._pinned = None
             base = p * self.P
             lo = max(off, base) - base

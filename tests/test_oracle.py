@@ -492,6 +492,44 @@ def test_golden_paper_private_buffer(tmp_path):
     sim.close_all()
 
 
+def test_golden_readahead_with_per_block_lra(tmp_path):
+    params, rows = _parse("policy_readahead_tb_lra.txt")
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(tmp_path, "rl", int(params["seed"]), npg * page)
+    sim = policy.PageCacheSim(page, int(params["frames"]), "readahead", ra_cap=int(params["wmax"]), reserve=0,
+                              async_ra=False, replacement="tb_lra", streams=int(params["streams"]))
+    sim.open(0, path)
+    ref = inputs.xorshift64_bytes(int(params["seed"]), npg * page)
+    for stream, fid, off, ln in policy.canonical_scan_trace(npg * page, page, int(params["streams"])):
+        n, data = sim.gread(stream, fid, off, ln)
+        assert n == ln and data == ref[off:off + ln]
+    assert [(lo, n) for (_, lo, n, _) in sim.rpc_log] == [(int(r[1]), int(r[2])) for r in rows if r[0] == "rpc"]
+    assert all(k == policy.SYNC_RA for (_, _, _, k) in sim.rpc_log)
+    assert sim.evict_log == [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert sim.next_unused == 2
+    sim.close_all()
+
+
+@pytest.mark.parametrize("mode", ["readahead", "ondemand"])
+def test_per_block_lra_with_readahead_keeps_streams_apart(tmp_path, mode):
+    # 3 streams, 12 frames: quota 4; every frame a stream takes (demand or
+    # readahead) is one it allocated, and it never holds more than its quota
+    path = _file(tmp_path, "rq", 6, 90 * P + 17)
+    sim = policy.PageCacheSim(P, 12, mode, ra_cap=3, reserve=0, replacement="tb_lra", streams=3)
+    sim.open(0, path)
+    ref = open(path, "rb").read()
+    owner = {}
+    for stream, fid, off, ln in policy.canonical_scan_trace(len(ref), 2 * P, 3):
+        n, data = sim.gread(stream, fid, off, ln)
+        assert data == ref[off:off + ln]
+        for s_, dq in sim.lra.items():
+            assert len(dq) <= sim.quota == 4
+            for f in dq:
+                assert owner.setdefault(f, s_) == s_
+    assert sim.stats.evictions > 0 and sim.next_unused == 12
+    sim.close_all()
+
+
 def test_paper_lra_quota_isolates_streams(tmp_path):
     # 2 streams, 4 frames: quota 2; a stream only ever reuses frames it allocated
     path = _file(tmp_path, "pq", 4, 40 * P)
