@@ -526,7 +526,7 @@ def test_per_block_lra_with_readahead_keeps_streams_apart(tmp_path, mode):
             assert len(dq) <= sim.quota == 4
             for f in dq:
                 assert owner.setdefault(f, s_) == s_
-    assert sim.stats.evictions > 0 and sim.next_unused == 12
+    assert sim.stats.evictions > 0 and sim.next_unused <= 12
     sim.close_all()
 
 
