@@ -469,6 +469,7 @@ def run_paper(args):
         run("E10_prefetcher_only_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_PAPER, ra=15)
         run("E10_prefetcher_tb_lra_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_PAPER, ra=15, repl=1)
         run("E10_readahead_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_READAHEAD, ra=15)
+        run("E10_readahead_tb_lra_page%dK" % k, 4 * GiB, 2 * GiB, page, gfs.MODE_READAHEAD, ra=15, repl=1)
     print(json.dumps(res), flush=True)
     return 0
 

@@ -45,8 +45,9 @@ extern "C" {
 
 /* Replacement (gfs_config.replacement). */
 #define GFS_REPL_FIFO 0   /* never-used, then consumed FIFO, then least recently allocated (rule R6) */
-#define GFS_REPL_TB_LRA 1 /* Section 5.1: per-threadblock least-recently-allocated queues of F / blocks frames
-                           * (GFS_MODE_PAPER only) */
+#define GFS_REPL_TB_LRA 1 /* Section 5.1: per-threadblock least-recently-allocated queues of F / blocks frames;
+                           * with GFS_MODE_READAHEAD every frame a request takes, demand or readahead, comes
+                           * from the requesting block's queue (the quota replaces the readahead reserve) */
 
 /* Open flags (Section 4.4, "Page cache coherency": readahead for read-only opens only). */
 #define GFS_RDONLY 0

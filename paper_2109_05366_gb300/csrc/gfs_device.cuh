@@ -857,7 +857,20 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
 // when no readahead victim is allowed.  Frames go to s_frames; the first is
 // pinned when pin_first.  Returns the page count, -EAGAIN when page p was
 // inserted by someone else meanwhile, or a negative errno.
-static __device__ int request_range(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t want,
+static __device__ int take_frame_lra(const DevHandle& g, int stream, bool for_ra, unsigned long long seq0,
+                                     unsigned long long new_key, unsigned long long deadline);
+
+// A frame for a request of `stream`: with GFS_REPL_TB_LRA from the stream's own
+// queue (Section 5.1), else by victim classes 1-3.
+static __device__ int take_for(const DevHandle& g, int stream, bool for_ra, unsigned long long seq0,
+                               unsigned long long new_key, unsigned long long deadline) {
+  if (g.repl == GFS_REPL_TB_LRA && stream >= 0 && (uint32_t)stream < g.paper_streams)
+    return take_frame_lra(g, stream, for_ra, seq0, new_key, deadline);
+  return take_frame(g, for_ra, seq0, new_key, deadline);
+}
+
+static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi,
+                                    unsigned long long p, uint32_t want,
                              uint32_t demand, bool pin_first, unsigned long long seq0, unsigned long long deadline,
                              uint32_t* s_frames) {
   const int lane = lane_id();
@@ -871,7 +884,7 @@ static __device__ int request_range(const DevHandle& g, uint32_t fid, const File
     const bool is_ra = i >= demand;
     // R8: readahead does not fetch a page again once fetched (sequential data is used once)
     if (is_ra && fi.fetched && (ld_rlx(&fi.fetched[q >> 5]) >> (q & 31)) & 1u) break;
-    int f = take_frame(g, is_ra, seq0, key, deadline);
+    int f = take_for(g, stream, is_ra, seq0, key, deadline);
     while (f < 0 && !is_ra && i == 0) {  // the first demand page waits for a victim
       int late = 0;
       if (lane == 0) late = now_ns() > deadline;
@@ -884,7 +897,7 @@ static __device__ int request_range(const DevHandle& g, uint32_t fid, const File
         if (lane == 0) __nanosleep(256);
         __syncwarp();
       }
-      f = take_frame(g, false, seq0, key, deadline);
+      f = take_for(g, stream, false, seq0, key, deadline);
     }
     if (f < 0) break;
     const bool pin = pin_first && i == 0;
@@ -940,14 +953,15 @@ static __device__ int finish_request(const DevHandle& g, uint32_t fid, const Fil
 }
 
 // R4: asynchronous readahead of [end, end + min(Wmax, 2T)) from a readahead mark.
-static __device__ void async_readahead(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long end, uint32_t t,
-                                unsigned long long seq0, unsigned long long deadline, uint32_t* s_frames) {
+static __device__ void async_readahead(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi,
+                                       unsigned long long end, uint32_t t, unsigned long long seq0,
+                                       unsigned long long deadline, uint32_t* s_frames) {
   if (end >= fi.npages) return;
   if (fi.fetched && (ld_rlx(&fi.fetched[end >> 5]) >> (end & 31)) & 1u) return;  // R8
   if (tab_lookup(g, make_key(fid, end)) >= 0) return;
   uint32_t want = 2 * t < g.ra_cap ? 2 * t : g.ra_cap;
   if (want == 0) return;
-  int n = request_range(g, fid, fi, end, want, 0, false, seq0, deadline, s_frames);
+  int n = request_range(g, stream, fid, fi, end, want, 0, false, seq0, deadline, s_frames);
   if (n <= 0) return;
   finish_request(g, fid, fi, end, (uint32_t)n, 0, (uint32_t)n, GFS_KIND_ASYNC_RA, end + (uint32_t)n, 0, s_frames,
                  deadline);
@@ -988,7 +1002,7 @@ static __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, 
     if (T > g.max_rpc_pages) T = g.max_rpc_pages;
     if (d > T) d = T;
   }
-  int n = request_range(g, fid, fi, p, T, d, true, seq0, deadline, s_frames);
+  int n = request_range(g, stream, fid, fi, p, T, d, true, seq0, deadline, s_frames);
   if (n < 0) return n;
   const uint32_t kind = (uint32_t)n > d ? GFS_KIND_SYNC_RA : GFS_KIND_DEMAND;
   const uint32_t window = (ra && seq) ? (uint32_t)n : 0u;
@@ -1026,16 +1040,21 @@ static __device__ int frame_claim_own(const DevHandle& g, int f) {
   return 1;
 }
 
-// Section 5.1: the stream's least-recently-allocated queue.  Below the quota a
-// never-used frame joins it; at the quota the oldest frame is reused (its old
-// page unmapped) and becomes the newest (warp).
-static __device__ int take_frame_lra(const DevHandle& g, int stream, unsigned long long seq0, unsigned long long new_key,
-                                     unsigned long long deadline) {
+// Section 5.1: the stream's least-recently-allocated queue (warp).  Below the
+// quota a never-used frame joins it; otherwise its frames are tried oldest
+// first: the first one not in use (pinned, being filled, or in the request being
+// built) is reused, its old page unmapped; every frame tried moves to the newest
+// end.  Returns a frame, or -1 when none can be passed (a demand page retries
+// until its deadline; readahead stops).  A stream that owns no frame when none
+// is unused adopts a victim of classes 1-3.
+static __device__ int take_frame_lra(const DevHandle& g, int stream, bool for_ra, unsigned long long seq0,
+                                     unsigned long long new_key, unsigned long long deadline) {
   const int lane = lane_id();
-  int f = -1, reuse = 0;
+  int f = -1, reuse = 0, adopt = 0;
   if (lane == 0) {
     const uint32_t base = (uint32_t)stream * g.quota;
-    const uint32_t len = g.lra_len[stream], head = g.lra_head[stream];
+    const uint32_t len = g.lra_len[stream];
+    uint32_t head = g.lra_head[stream];
     if (len < g.quota && ld_rlx64(&g.ctrl->next_unused.v) < g.n_frames) {
       const unsigned long long u = atomicAdd(&g.ctrl->next_unused.v, 1ull);
       if (u < g.n_frames) {
@@ -1044,18 +1063,20 @@ static __device__ int take_frame_lra(const DevHandle& g, int stream, unsigned lo
         g.lra_len[stream] = len + 1;
       }
     }
-    if (f < 0 && len > 0) {
-      for (;;) {
+    if (f < 0) {
+      for (uint32_t k = 0; k < len; ++k) {
         const int cand = (int)g.lra[base + head];
-        if (frame_claim_own(g, cand) == 1) {
+        const int r = frame_claim_own(g, cand);
+        g.lra[base + (head + len) % g.quota] = (uint32_t)cand;  // oldest -> newest
+        head = (head + 1) % g.quota;
+        if (r == 1) {
           f = cand;
           reuse = 1;
-          g.lra_head[stream] = (head + 1) % g.quota;  // the reused frame is now the newest
           break;
         }
-        if (now_ns() > deadline) break;
-        __nanosleep(128);
       }
+      g.lra_head[stream] = head;
+      adopt = f < 0 && len == 0;
     }
   }
   f = bcast(f);
@@ -1063,14 +1084,13 @@ static __device__ int take_frame_lra(const DevHandle& g, int stream, unsigned lo
     evict_key(g, f, new_key, deadline);
     return f;
   }
-  if (f >= 0) return f;
-  // the stream owns no frame and none is unused: take any victim and adopt it
-  f = take_frame(g, false, seq0, new_key, deadline);
+  if (f >= 0 || !bcast(adopt)) return f;
+  f = take_frame(g, for_ra, seq0, new_key, deadline);
   if (f >= 0 && lane == 0) {
-    const uint32_t base = (uint32_t)stream * g.quota;
+    const uint32_t b2 = (uint32_t)stream * g.quota;
     const uint32_t len = g.lra_len[stream], head = g.lra_head[stream];
     if (len < g.quota) {
-      g.lra[base + (head + len) % g.quota] = (uint32_t)f;
+      g.lra[b2 + (head + len) % g.quota] = (uint32_t)f;
       g.lra_len[stream] = len + 1;
     }
   }
@@ -1087,7 +1107,7 @@ static __device__ int handle_miss_paper(const DevHandle& g, int stream, uint32_t
   const unsigned long long key = make_key(fid, p);
   if (lane == 0) stat_add(g, ST_MISSES, 1);
   const bool own = g.repl == GFS_REPL_TB_LRA && stream >= 0 && (uint32_t)stream < g.paper_streams;
-  int f = own ? take_frame_lra(g, stream, seq0, key, deadline) : take_frame(g, false, seq0, key, deadline);
+  int f = own ? take_frame_lra(g, stream, false, seq0, key, deadline) : take_frame(g, false, seq0, key, deadline);
   while (f < 0) {
     int late = 0;
     if (lane == 0) late = now_ns() > deadline;
@@ -1099,7 +1119,7 @@ static __device__ int handle_miss_paper(const DevHandle& g, int stream, uint32_t
       if (lane == 0) __nanosleep(256);
       __syncwarp();
     }
-    f = own ? take_frame_lra(g, stream, seq0, key, deadline) : take_frame(g, false, seq0, key, deadline);
+    f = own ? take_frame_lra(g, stream, false, seq0, key, deadline) : take_frame(g, false, seq0, key, deadline);
   }
   if (lane == 0) {
     st_rlx64(&g.fkey[f], key);
@@ -1331,8 +1351,8 @@ static __device__ int block_wait_ready(const DevHandle& g, int f, unsigned long 
 
 // R4 for a READY page just acquired: the first reader of a marked page issues
 // the asynchronous window (warp 0).
-static __device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDev& fi, int f, unsigned long long seq0,
-                           unsigned long long deadline, uint32_t* s_frames) {
+static __device__ void check_mark(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi, int f,
+                                  unsigned long long seq0, unsigned long long deadline, uint32_t* s_frames) {
   const int lane = lane_id();
   if (!(g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra)) return;  // no marks in the other modes
   uint32_t m = 0, w = 0;
@@ -1342,7 +1362,7 @@ static __device__ void check_mark(const DevHandle& g, uint32_t fid, const FileDe
   }
   m = (uint32_t)bcast((int)m);
   w = (uint32_t)bcast((int)w);
-  if (m) async_readahead(g, fid, fi, (unsigned long long)m - 1, w, seq0, deadline, s_frames);
+  if (m) async_readahead(g, stream, fid, fi, (unsigned long long)m - 1, w, seq0, deadline, s_frames);
 }
 
 // R5: account the delivered bytes, unpin, and queue the frame once fully consumed.
@@ -1514,7 +1534,7 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
       __syncthreads();
       break;
     }
-    if (tid < 32) check_mark(g, (uint32_t)fid, fi, f, seq0, deadline, s_frames);
+    if (tid < 32) check_mark(g, stream, (uint32_t)fid, fi, f, seq0, deadline, s_frames);
     const unsigned long long base = p << g.page_shift;
     const unsigned long long lo = (off > base ? off : base) - base;
     const unsigned long long hi = (end < base + g.page_size ? end : base + g.page_size) - base;

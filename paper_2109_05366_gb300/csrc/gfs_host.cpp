@@ -314,9 +314,10 @@ int quiesce(gfs_ctx* ctx, cudaStream_t s) {
 }
 
 // Drop the cached pages of a file id (device and host quiet).  The paper mode's
-// private buffers and LRA queues are not per file: that mode clears the cache.
+// private buffers and the per-block LRA queues are not per file: with either
+// the cache is cleared.
 int purge_pages(gfs_ctx* ctx, int fid) {
-  if (ctx->cfg.mode == GFS_MODE_PAPER) return gfs_reset_cache(ctx, nullptr);
+  if (ctx->cfg.mode == GFS_MODE_PAPER || ctx->cfg.replacement == GFS_REPL_TB_LRA) return gfs_reset_cache(ctx, nullptr);
   int rc = launch_purge(ctx->dev, (uint32_t)fid, nullptr);
   if (rc) return rc;
   return cuda_err(cudaStreamSynchronize(nullptr));
@@ -547,7 +548,6 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   if (c.cache_bytes < c.page_size) return -EINVAL;
   if (c.mode > GFS_MODE_PAPER || c.xfer > GFS_XFER_MAPPED || c.replacement > GFS_REPL_TB_LRA) return -EINVAL;
   if (c.mode == GFS_MODE_PAPER && c.xfer == GFS_XFER_DMA) return -ENOTSUP;  // the requesting block copies its pages
-  if (c.replacement == GFS_REPL_TB_LRA && c.mode != GFS_MODE_PAPER) return -EINVAL;
   if (c.queue > GFS_QUEUE_STATIC) return -EINVAL;
   // a Vyukov ring needs 2 slots at least: with one, "published for ticket t" and
   // "free for ticket t+1" are the same sequence value
@@ -1037,14 +1037,16 @@ int gfs_get_fetch_counts(gfs_ctx* ctx, uint32_t* h_counts, uint64_t cap, void* s
 }  // extern "C"
 
 int ensure_paper_state(gfs_ctx* ctx, uint32_t streams) {
-  if (ctx->cfg.mode != GFS_MODE_PAPER || streams <= ctx->dev.paper_streams) return 0;
+  const bool paper = ctx->cfg.mode == GFS_MODE_PAPER;
+  if ((!paper && ctx->cfg.replacement != GFS_REPL_TB_LRA) || streams <= ctx->dev.paper_streams) return 0;
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
   cudaDeviceSynchronize();  // no kernel may still use the old state
   if (ctx->d_paper) cudaFree(ctx->d_paper);
   ctx->d_paper = nullptr;
   ctx->dev.paper_streams = 0;
   const uint32_t quota = std::max<uint32_t>(1, ctx->dev.n_frames / streams);
-  const size_t pbuf = std::max<size_t>(256, (size_t)streams * ctx->dev.ra_cap * ctx->cfg.page_size);
+  // private buffers only for the paper's prefetcher; the LRA queues for GFS_REPL_TB_LRA
+  const size_t pbuf = paper ? std::max<size_t>(256, (size_t)streams * ctx->dev.ra_cap * ctx->cfg.page_size) : 256;
   const size_t o_meta = align_up(pbuf, 256);
   const size_t o_lra = o_meta + align_up((size_t)streams * sizeof(PrivBuf), 256);
   const size_t o_head = o_lra + align_up((size_t)streams * quota * 4, 256);
@@ -1141,6 +1143,7 @@ int gfs_scan_path(gfs_ctx* ctx, const char* path, const gfs_scan_args* a, int64_
   CK(cudaSetDevice(ctx->cfg.device));
   const uint64_t bs = align_up(a->read_len, 256);
   int rc = ensure_scan_buf(ctx, (size_t)a->blocks * bs);
+  if (!rc) rc = ensure_paper_state(ctx, a->blocks);
   if (rc) return rc;
   DevHandle g = ctx->dev;
   const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;

@@ -357,7 +357,9 @@ extern "C" int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* a, in
   if (nstrides == 0) return 0;
   if (!d_count || !d_sum || !d_hash) return -EINVAL;
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
-  if (ctx->cfg.mode == GFS_MODE_PAPER && ctx->dev.paper_streams < a->blocks) return -ENOTSUP;  // would allocate
+  if ((ctx->cfg.mode == GFS_MODE_PAPER || ctx->cfg.replacement == GFS_REPL_TB_LRA) &&
+      ctx->dev.paper_streams < a->blocks)
+    return -ENOTSUP;  // would allocate
   void* scratch = nullptr;
   int rc = static_scratch(ctx->cfg.device, &scratch);
   if (rc) return rc;

@@ -301,6 +301,46 @@ def test_pull_partial_requests_are_helped(torch_cuda, gfs, datadir):
         assert ctx.stats()["timeouts"] == 0
 
 
+# ------------------------------------------------ readahead with the per-block LRA of Section 5.1
+@pytest.mark.parametrize("xfer", XFERS)
+@pytest.mark.parametrize("size,page,frames,blocks,stride,ra_cap,async_ra", [
+    (24 * MiB + 999, 256 * KiB, 24, 6, 512 * KiB, 2, 1),     # file 4x the cache, quota 4
+    (16 * MiB + 7, 64 * KiB, 40, 4, 192 * KiB, 8, 0),        # sync readahead only, quota 10
+    (8 * MiB, 128 * KiB, 64, 2, 128 * KiB, 8, 1),            # file as large as the cache, quota 32 each
+])
+def test_readahead_per_block_lra_serialized_logs_match_oracle(torch_cuda, gfs, datadir, xfer, size, page, frames,
+                                                               blocks, stride, ra_cap, async_ra):
+    path = _file(datadir, 12, size)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=0, replacement=1, ra_cap_pages=ra_cap,
+                     async_ra=async_ra, trace_capacity=1 << 16, max_rpc_pages=16, xfer=xfer,
+                     timeout_ns=2 * 10**9) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode="readahead", ra_cap=ra_cap, reserve=0,
+                               async_ra=bool(async_ra), max_rpc_pages=16, replacement="tb_lra")
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
+@pytest.mark.parametrize("xfer", XFERS)
+def test_readahead_per_block_lra_concurrent_exact(torch_cuda, gfs, datadir, xfer):
+    size = 128 * MiB + 4096
+    path = _file(datadir, 11, size)
+    with gfs.Context(cache_bytes=32 * MiB, page_size=64 * KiB, mode=0, replacement=1, ra_cap_pages=15,
+                     max_rpc_pages=32, xfer=xfer, timeout_ns=5 * 10**9) as ctx:
+        fid = ctx.open(path)
+        for _ in range(2):
+            out = ctx.scan(fid, MiB, blocks=96, threads=256)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            assert st["timeouts"] == 0 and st["enomem"] == 0 and st["evictions"] > 0
+            ctx.reset_cache()
+
+
 # ------------------------------------------------ the paper's own design (Sections 4.1, 5.1)
 @pytest.mark.parametrize("xfer", [1, 2])
 @pytest.mark.parametrize("repl", [0, 1])
