@@ -143,8 +143,8 @@ def data_dir():
 # DRAM bytes per scanned file byte of k_scan, from the ncu capture summarised in
 # profiles/k_scan_cfg2s_2GiB_sol.md (2 GiB case; traffic grows with the bytes scanned),
 # valid only for the library build it was taken on.
-NCU_DRAM = {"build_digest": "95cef848c1136f46e5d18853ada37397e8baf30cb5f232b12be7dafdb89a0cf0",
-            "bytes_per_file_byte": (2.247664e9 + 4.322181e9) / (2 * GiB),
+NCU_DRAM = {"build_digest": "1006b98120dda8bf5526d9baf7a690d8783dbaf189d42274433498072afcd1c2",
+            "bytes_per_file_byte": (2.960236e9 + 4.321291e9) / (2 * GiB),
             "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 2 GiB case scaled by bytes scanned"}
 
 

@@ -1357,7 +1357,10 @@ static __device__ void check_mark(const DevHandle& g, int stream, uint32_t fid, 
   if (!(g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra)) return;  // no marks in the other modes
   uint32_t m = 0, w = 0;
   if (lane == 0) {
-    m = atomicExch(&g.fmark[f], 0u);
+    // a READY page's mark only ever goes from set to clear, and it was set
+    // before the page was published: most pages carry none, and only a set
+    // mark needs the exchange that lets exactly one reader claim it
+    m = ld_rlx(&g.fmark[f]) ? atomicExch(&g.fmark[f], 0u) : 0u;
     if (m) w = ld_rlx(&g.fwindow[f]);
   }
   m = (uint32_t)bcast((int)m);
@@ -1367,12 +1370,16 @@ static __device__ void check_mark(const DevHandle& g, int stream, uint32_t fid, 
 
 // R5: account the delivered bytes, unpin, and queue the frame once fully consumed.
 static __device__ void release_page(const DevHandle& g, int f, uint32_t nbytes, unsigned long long deadline) {  // one thread
+  if (g.repl == GFS_REPL_TB_LRA) {  // per-threadblock LRA queues (Section 5.1) replace the consumed FIFO
+    atomicAdd(&g.fconsumed[f], nbytes);  // nothing waits for the old count
+    frame_unpin(g, f);
+    return;
+  }
   uint32_t c = atomicAdd(&g.fconsumed[f], nbytes);
   uint32_t v = ld_rlx(&g.fvalid[f]);
   bool push = c < v && c + nbytes >= v;
   frame_unpin(g, f);
-  // per-threadblock LRA queues (Section 5.1) replace the consumed FIFO entirely
-  if (push && g.repl != GFS_REPL_TB_LRA) fifo_push(g, (uint32_t)f, deadline);
+  if (push) fifo_push(g, (uint32_t)f, deadline);
 }
 
 // ---------------------------------------------------------------- copy-out
