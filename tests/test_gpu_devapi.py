@@ -208,3 +208,28 @@ def test_user_kernel_device_api(torch_cuda, gfs, datadir, user_lib, advice, xfer
         else:  # whether concurrent blocks leave readahead any page depends on timing: not checked
             assert (inf[:, 5] == 0).all()
         assert st["host_controls"] == blocks * (3 if advice >= 0 else 2)
+
+
+def test_user_kernel_gopen_of_missing_file_fails_cleanly(torch_cuda, gfs, datadir, user_lib):
+    """gopen of a path the host cannot open returns the host's -errno to every block;
+    no request of the kernel hangs and the context stays usable."""
+    torch = torch_cuda
+    P, S, blocks = 256 * KiB, 512 * KiB, 8
+    missing = os.path.join(datadir, "no_such_file.bin")
+    with gfs.Context(cache_bytes=16 * MiB, page_size=P, xfer=2, max_rpc_pages=16) as ctx:
+        h = ctx.device_handle(blocks, S)
+        bufs = torch.empty(blocks * S, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(16, dtype=torch.int64, device="cuda")
+        sm = torch.zeros(16, dtype=torch.int64, device="cuda")
+        info = torch.zeros(8 * blocks, dtype=torch.int64, device="cuda")
+        assert user_lib.user_scan(h, len(h), missing.encode(), -1, S, 16, blocks, bufs.data_ptr(), cnt.data_ptr(),
+                                  sm.data_ptr(), info.data_ptr(), None) == 0
+        torch.cuda.synchronize()
+        inf = info.cpu().numpy().reshape(blocks, 8)
+        assert (inf[:, 0] == -errno.ENOENT).all()
+        assert (cnt.cpu().numpy() == -errno.ENOENT).all()
+        assert ctx.stats()["timeouts"] == 0
+        path = _file(datadir, 28, 8 * MiB + 321)          # the context still serves
+        out = ctx.scan_path(path, MiB, blocks=8)
+        torch.cuda.synchronize()
+        _check_scan(gfs, path, MiB, *out)
