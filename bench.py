@@ -142,8 +142,8 @@ def data_dir():
 
 # DRAM bytes per scanned file byte of k_scan, from the ncu capture summarised in
 # profiles/k_scan_cfg2s_2GiB_sol.md (2 GiB case; traffic grows with the bytes scanned),
-# valid only for the library build it was taken on.
-NCU_DRAM = {"build_digest": "1006b98120dda8bf5526d9baf7a690d8783dbaf189d42274433498072afcd1c2",
+# valid only while the kernel's sources are those it was taken on.
+NCU_DRAM = {"kernel_digest": "43c2d071166d3befb2eeec10c78df7b55af689ce3fb57e4e42440967ac009067",
             "bytes_per_file_byte": (2.960236e9 + 4.321291e9) / (2 * GiB),
             "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 2 GiB case scaled by bytes scanned"}
 
@@ -827,7 +827,7 @@ def run_gfs(args):
     if binding:
         from paper_2109_05366_gb300 import build as _b
         traffic = None
-        if _b._digest() == NCU_DRAM["build_digest"] and args.xfer == "mapped" and not args.fused:
+        if _b.kernel_digest() == NCU_DRAM["kernel_digest"] and args.xfer == "mapped" and not args.fused:
             traffic = int(NCU_DRAM["bytes_per_file_byte"] * size)  # DRAM bytes per launch
         line["roofline"] = {"bound": "link", "achieved": round(value / world, 2), "peak": round(binding, 1),
                             "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": traffic,

@@ -41,6 +41,23 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# The sources the stride-scan kernel is compiled from (its device code); profiles
+# taken on one build stay valid while these are unchanged.
+KERNEL_SOURCES = ["gfs_kernels.cu", "gfs_device.cuh", "gfs_internal.h"]
+
+
+def kernel_digest() -> str:
+    """Digest of the stride-scan kernel's sources (device code, shared layouts, ABI header, arch)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(ROOT, "include", "gfs.h"), "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(ARCH).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libgfs.so unless it is up to date; returns its path."""
     digest = _digest()

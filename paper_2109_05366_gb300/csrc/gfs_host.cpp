@@ -1232,6 +1232,11 @@ int gfs_scan_graph(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint32_t reps,
         rc = cuda_err(cudaMemsetAsync(ctx->dev.fetch_count, 0, (size_t)ctx->dev.debug_pages * 4, cs));
       for (auto& f : ctx->files)
         if (!rc && f.open && f.d_fetched) rc = cuda_err(cudaMemsetAsync(f.d_fetched, 0, f.fetched_bytes, cs));
+      if (!rc && ctx->dev.paper_streams) {  // private buffers and per-block LRA queues start empty too
+        rc = cuda_err(cudaMemsetAsync(ctx->dev.pmeta, 0, (size_t)ctx->dev.paper_streams * sizeof(PrivBuf), cs));
+        if (!rc) rc = cuda_err(cudaMemsetAsync(ctx->dev.lra_head, 0, (size_t)ctx->dev.paper_streams * 4, cs));
+        if (!rc) rc = cuda_err(cudaMemsetAsync(ctx->dev.lra_len, 0, (size_t)ctx->dev.paper_streams * 4, cs));
+      }
       if (!rc) rc = launch_reset(ctx->dev, cs);
       if (!rc && a->serialize) rc = cuda_err(cudaMemsetAsync(&g.ctrl->ticket.v, 0, 8, cs));
       if (!rc) rc = launch_scan(g, fid, *a, ns, ctx->d_scan_buf, bs, d_count, d_sum, d_hash, cs);

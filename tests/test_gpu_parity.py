@@ -266,6 +266,28 @@ def test_scan_graph_steady_loop_exact(torch_cuda, gfs, datadir, xfer):
             assert st["pages_fetched"] == 256 and st["timeouts"] == 0  # last repetition, from an empty cache
 
 
+@pytest.mark.parametrize("xfer", [1, 2])
+@pytest.mark.parametrize("mode", [0, 2])  # readahead, the paper's prefetcher; both with per-block LRA
+def test_scan_graph_repetitions_start_from_empty_lra_queues(torch_cuda, gfs, datadir, xfer, mode):
+    """Every repetition of the captured loop starts from an empty cache, empty per-block
+    LRA queues and (paper mode) empty private buffers: the last repetition's serialized
+    logs equal a fresh oracle run."""
+    size, page, frames, blocks, stride, ra = 24 * MiB + 999, 256 * KiB, 24, 6, 512 * KiB, 2
+    path = _file(datadir, 12, size)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=mode, replacement=1, ra_cap_pages=ra,
+                     trace_capacity=1 << 16, max_rpc_pages=16, xfer=xfer, reserve_frames=1,
+                     timeout_ns=2 * 10**9) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan_graph(fid, stride, 3, blocks=blocks, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode=("paper" if mode == 2 else "readahead"),
+                               ra_cap=ra, reserve=1, max_rpc_pages=16, replacement="tb_lra")
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
 def test_scan_graph_refuses_dma(torch_cuda, gfs, datadir):
     path = _file(datadir, 1, 64 * MiB)
     with gfs.Context(cache_bytes=128 * MiB, page_size=256 * KiB, xfer=0) as ctx:
