@@ -44,8 +44,10 @@ Rules (R1-R7) as implemented below:
      count; when it first reaches the page's valid bytes the frame is appended
      to the consumed FIFO.
   R6 victims: (1) never-used frames, lowest index first; (2) the consumed FIFO,
-     oldest first; (3) demand pages only, when (1) and (2) are empty: the
-     oldest-allocated frame not allocated during the current gread.  Readahead
+     oldest first; (3) only for the page the gread waits for (the first page of
+     a demand run), when (1) and (2) are empty: the oldest-allocated frame not
+     allocated during the current gread; later pages of the run end the request
+     instead of evicting unconsumed pages.  Readahead
      pages take victims only from (1)/(2) and only while
      free + consumed > reserve.  Frames of the request being built and the
      frame of the page being delivered are never victims (a FIFO entry for the
@@ -218,7 +220,7 @@ class PageCacheSim:
             if fr.consumed < fr.valid or fr.state == ERROR:
                 self.stats.unconsumed_evictions += 1
 
-    def _take(self, for_readahead: bool, gread_seq0: int, new_key) -> int | None:
+    def _take(self, for_readahead: bool, gread_seq0: int, new_key, fallback: bool = True) -> int | None:
         if for_readahead and self._avail() <= self.reserve:
             return None
         if self.next_unused < self.F:                      # (1)
@@ -232,7 +234,7 @@ class PageCacheSim:
                 continue
             self._evict(f, new_key)
             return f
-        if for_readahead:
+        if for_readahead or not fallback:
             return None
         best = None                                         # (3)
         for f, fr in enumerate(self.frames):
@@ -290,8 +292,8 @@ class PageCacheSim:
             try:
                 if self.replacement == "tb_lra":                   # P2
                     f = self._take_lra(stream, q - p >= demand, (fid, q))
-                else:
-                    f = self._take(q - p >= demand, gread_seq0, (fid, q))
+                else:  # only the page the gread waits for may take an unconsumed victim (3)
+                    f = self._take(q - p >= demand, gread_seq0, (fid, q), fallback=q == p)
             except NoFrame:
                 if q == p:
                     raise

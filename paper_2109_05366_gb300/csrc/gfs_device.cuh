@@ -376,7 +376,7 @@ static __device__ bool ra_allowed(const DevHandle& g) {  // one thread
 // by the caller with its old mapping removed, -1 if none (readahead), or a
 // negative errno.
 static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long long seq0, unsigned long long new_key,
-                          unsigned long long deadline) {
+                          unsigned long long deadline, bool fallback = true) {
   const int lane = lane_id();
   int r = 0;
   if (for_ra) {
@@ -410,9 +410,11 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
       return c;
     }
   }
-  if (for_ra) return -1;
-  // (3) demand only: the least recently allocated unconsumed frame that this
-  //     gread did not allocate.  A cache of at most kLraWindow frames is scanned
+  if (for_ra || !fallback) return -1;
+  // (3) only for the page a gread waits for (later pages of a demand run end the
+  //     request instead of evicting unconsumed pages): the least recently
+  //     allocated unconsumed frame that this gread did not allocate.  A cache of
+  //     at most kLraWindow frames is scanned
   //     whole.  A larger one is scanned a window of kLraWindow frames at a time,
   //     from a place that depends on the gread, and the oldest frame of the first
   //     window that has one is taken: concurrent greads then pick different
@@ -749,39 +751,51 @@ static __device__ bool block_help(const DevHandle& g, int target, bool any) {
 }
 
 // ---------------------------------------------------------------- request ring
-// Take the next ticket of the ring and wait until its slot is free for this
-// lap (one warp).  Returns 0 with *t and *si set, or -ETIMEDOUT; a ticket once
-// taken is always published by the caller.
+// Claim the next ticket of the ring whose slot is free for its lap (one warp).
+// A ticket is claimed (compare-and-swap, Vyukov's bounded queue) only after its
+// slot was seen free, so a claimed ticket is always published by the caller and
+// a wait that runs out claims nothing: the host threads, which serve tickets in
+// order, never wait for a ticket nobody will publish.  GFS_QUEUE_SHARED: the
+// shared position ring_tail.  GFS_QUEUE_STATIC (Section 3.2): the threadblock's
+// own slot and its lap counter; ring_tail then only counts requests.  Returns 0
+// with *t and *si set, or -ETIMEDOUT.
 static __device__ int ring_acquire(const DevHandle& g, unsigned long long* t_out, uint32_t* si_out,
                                    unsigned long long deadline) {
   const int lane = lane_id();
-  unsigned long long t = 0;
-  if (lane == 0) {
-    const unsigned long long k = atomicAdd(&g.ctrl->ring_tail.v, 1ull);  // requests issued (drain counts them)
-    if (g.queue == GFS_QUEUE_STATIC) {  // Section 3.2: the threadblock's own slot
-      const uint32_t slot = blockIdx.x % g.rpc_slots;
-      t = atomicAdd(&g.slot_lap[slot], 1ull) * g.rpc_slots + slot;
-    } else {
-      t = k;
-    }
-  }
-  t = bcast64(t);
-  const uint32_t si = (uint32_t)(t % g.rpc_slots);
-  RingSlot* s = ring_slot(g, si);
-  *t_out = t;
-  *si_out = si;
-  for (unsigned ns = 64;;) {  // wait until the slot is free for this lap
-    int free_ = 0, late = 0;
+  const bool stat = g.queue == GFS_QUEUE_STATIC;
+  const uint32_t own = blockIdx.x % g.rpc_slots;
+  for (unsigned ns = 64;;) {
+    int state = 0;  // 0 slot busy, 1 claimed, 2 lost a race (retry at once), 3 late
+    unsigned long long t = 0;
     if (lane == 0) {
-      free_ = ld_acq_sys64(&s->seq) == t;
-      late = now_ns() > deadline;
+      if (stat) {
+        const unsigned long long lap = ld_rlx64(&g.slot_lap[own]);
+        t = lap * g.rpc_slots + own;
+        if (ld_acq_sys64(&ring_slot(g, own)->seq) == t)
+          state = atomicCAS(&g.slot_lap[own], lap, lap + 1) == lap ? 1 : 2;
+        if (state == 1) atomicAdd(&g.ctrl->ring_tail.v, 1ull);  // requests issued (drain counts them)
+      } else {
+        t = ld_rlx64(&g.ctrl->ring_tail.v);
+        if (ld_acq_sys64(&ring_slot(g, (uint32_t)(t % g.rpc_slots))->seq) == t)
+          state = atomicCAS(&g.ctrl->ring_tail.v, t, t + 1) == t ? 1 : 2;
+      }
+      if (state == 0 && now_ns() > deadline) state = 3;
     }
-    if (bcast(free_)) return 0;
-    if (bcast(late)) {
+    state = bcast(state);
+    if (state == 1) {
+      t = bcast64(t);
+      *t_out = t;
+      *si_out = (uint32_t)(t % g.rpc_slots);
+      return 0;
+    }
+    if (state == 2) continue;
+    if (state == 3) {
       if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
       return -kETIMEDOUT;
     }
-    // in pull mode slots are freed by GPU copies: help instead of idling
+    // the ring is full: in the GPU copy transfers slots are freed by GPU copies,
+    // so help instead of idling
+    const uint32_t si = stat ? own : (uint32_t)(bcast64(t) % g.rpc_slots);
     if (g.xfer != GFS_XFER_DMA && warp_help(g, si)) continue;
     if (lane == 0) __nanosleep(ns);
     __syncwarp();
@@ -861,12 +875,13 @@ static __device__ int take_frame_lra(const DevHandle& g, int stream, bool for_ra
                                      unsigned long long new_key, unsigned long long deadline);
 
 // A frame for a request of `stream`: with GFS_REPL_TB_LRA from the stream's own
-// queue (Section 5.1), else by victim classes 1-3.
-static __device__ int take_for(const DevHandle& g, int stream, bool for_ra, unsigned long long seq0,
+// queue (Section 5.1), else by victim classes 1-3 (class 3 only for the page the
+// gread waits for, `awaited`).
+static __device__ int take_for(const DevHandle& g, int stream, bool for_ra, bool awaited, unsigned long long seq0,
                                unsigned long long new_key, unsigned long long deadline) {
   if (g.repl == GFS_REPL_TB_LRA && stream >= 0 && (uint32_t)stream < g.paper_streams)
     return take_frame_lra(g, stream, for_ra, seq0, new_key, deadline);
-  return take_frame(g, for_ra, seq0, new_key, deadline);
+  return take_frame(g, for_ra, seq0, new_key, deadline, awaited);
 }
 
 static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi,
@@ -884,7 +899,7 @@ static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid
     const bool is_ra = i >= demand;
     // R8: readahead does not fetch a page again once fetched (sequential data is used once)
     if (is_ra && fi.fetched && (ld_rlx(&fi.fetched[q >> 5]) >> (q & 31)) & 1u) break;
-    int f = take_for(g, stream, is_ra, seq0, key, deadline);
+    int f = take_for(g, stream, is_ra, i == 0, seq0, key, deadline);
     while (f < 0 && !is_ra && i == 0) {  // the first demand page waits for a victim
       int late = 0;
       if (lane == 0) late = now_ns() > deadline;
@@ -897,7 +912,7 @@ static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid
         if (lane == 0) __nanosleep(256);
         __syncwarp();
       }
-      f = take_for(g, stream, false, seq0, key, deadline);
+      f = take_for(g, stream, false, true, seq0, key, deadline);
     }
     if (f < 0) break;
     const bool pin = pin_first && i == 0;

@@ -102,10 +102,11 @@ struct FileDev {
 static_assert(sizeof(FileDev) == 48, "FileDev");
 
 // One request-ring slot in mapped pinned memory (64-byte header + frame list).
-// Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; the GPU
-// producer with ticket t waits for seq == t, fills the slot and publishes
-// seq = t + 1; the host consumer with ticket h waits for seq == h + 1, copies the
-// request out and frees the slot with seq = h + R.  Tickets of slot i are
+// Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; a GPU
+// producer claims ticket t only once it sees seq == t (slot free for that lap),
+// fills the slot and publishes seq = t + 1; the host consumer with ticket h waits
+// for seq == h + 1, copies the request out and frees the slot with seq = h + R
+// (in the GPU copy transfers the GPU frees it once every page is copied).  Tickets of slot i are
 // i, i + R, i + 2R, ...: GFS_QUEUE_SHARED hands out tickets in order from one
 // counter (slot = ticket mod R); GFS_QUEUE_STATIC picks the slot from the
 // threadblock and numbers that slot's uses (ticket = lap * R + slot).

@@ -67,7 +67,10 @@ def tune(path: str, stride: int, space: dict = SPACE, start: dict = START, round
     def get(p):
         k = key(p)
         if k not in seen:
-            r = measure(path, stride, p, **kw)
+            try:
+                r = measure(path, stride, p, **kw)
+            except OSError as e:  # a point the library refuses or that fails is never the best
+                r = {**p, "stride": stride, "gbps": 0.0, "error": str(e), "timeouts": -1, "short_strides": -1}
             seen[k] = r
         return seen[k]
 
