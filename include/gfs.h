@@ -363,7 +363,11 @@ int gfs_serve_start(gfs_ctx* ctx, const gfs_serve_config* cfg, void* stream);
 int gfs_submit_scan(gfs_ctx* ctx, int fid, uint64_t off, uint64_t len, uint64_t tag);
 /* Copy up to `max` completions (in completion order); returns how many. */
 int gfs_poll(gfs_ctx* ctx, gfs_completion* out, int max);
-/* Ask the kernel to finish once every submitted request is done, wait, free. */
+/* Ask the kernel to finish once every submitted request is done, wait, free.
+ * Completions not polled by then are discarded.  A completion the device could
+ * not post because the host left the completion ring full for longer than the
+ * device deadline is dropped, not written over an unread one; gfs_serve_stop
+ * then returns -ENOBUFS. */
 int gfs_serve_stop(gfs_ctx* ctx);
 
 /* ---------------------------------------------------------------- application streams

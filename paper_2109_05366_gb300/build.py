@@ -46,14 +46,22 @@ def _digest() -> str:
 KERNEL_SOURCES = ["gfs_kernels.cu", "gfs_device.cuh", "gfs_internal.h"]
 
 
+def _code_only(text: bytes) -> bytes:
+    """C/C++ source without comments and with whitespace collapsed (a comment edit is not a code change)."""
+    import re
+    t = re.sub(rb"/\*.*?\*/", b" ", text, flags=re.S)
+    t = re.sub(rb"//[^\n]*", b" ", t)
+    return b" ".join(t.split())
+
+
 def kernel_digest() -> str:
-    """Digest of the stride-scan kernel's sources (device code, shared layouts, ABI header, arch)."""
+    """Digest of the stride-scan kernel's code (device code, shared layouts, ABI header, arch)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
         with open(os.path.join(CSRC, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+            h.update(name.encode() + b"\0" + _code_only(f.read()))
     with open(os.path.join(ROOT, "include", "gfs.h"), "rb") as f:
-        h.update(f.read())
+        h.update(_code_only(f.read()))
     h.update(" ".join(ARCH).encode())
     return h.hexdigest()
 

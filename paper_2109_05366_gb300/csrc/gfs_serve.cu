@@ -20,6 +20,7 @@
 // up; their units interleave with the running ones on the same CTAs.
 #include <cuda_runtime.h>
 #include <errno.h>
+#include <unistd.h>
 
 #include <chrono>
 #include <cstring>
@@ -62,6 +63,7 @@ struct Ctl {  // device memory
   Line active;
   Line adm_lock;
   Line last_work;
+  Line lost;  // completions dropped because the host left the completion ring full past the deadline
 };
 
 struct Handle {
@@ -81,13 +83,35 @@ __device__ __forceinline__ uint32_t ld_sys32(const uint32_t* p) {
   return v;
 }
 
-// Write a completion record and free the request slot (one thread).
+// Write a completion record and free the request slot (one thread).  A
+// completion slot is claimed (compare-and-swap) only once the host has freed it,
+// so a record is never written over one the host has not read; if the host
+// leaves the ring full past the deadline the completion is dropped and counted.
 __device__ void complete(const DevHandle& g, const Handle& h, uint32_t r) {
   Req& q = h.req[r];
-  const unsigned long long c = atomicAdd(&h.ctl->compl_tail.v, 1ull);
-  ComplSlot* cs = &h.compl_[c % h.compl_slots];
   const unsigned long long dl = dev::now_ns() + g.timeout_ns;
-  while (dev::ld_acq_sys64(&cs->seq) != c && dev::now_ns() < dl) __nanosleep(256);
+  unsigned long long c = 0;
+  bool claimed = false;
+  for (;;) {
+    c = dev::ld_rlx64(&h.ctl->compl_tail.v);
+    if (dev::ld_acq_sys64(&h.compl_[c % h.compl_slots].seq) == c) {
+      if (atomicCAS(&h.ctl->compl_tail.v, c, c + 1) == c) {
+        claimed = true;
+        break;
+      }
+      continue;
+    }
+    if (dev::now_ns() > dl) break;
+    __nanosleep(256);
+  }
+  if (!claimed) {
+    atomicAdd(&h.ctl->lost.v, 1ull);
+    atomicAdd(&h.ctl->frames_reserved.v, (unsigned long long)(0ull - q.frames));
+    atomicAdd(&h.ctl->active.v, ~0ull);
+    dev::st_rel(&q.state, 0u);
+    return;
+  }
+  ComplSlot* cs = &h.compl_[c % h.compl_slots];
   dev::st_sys64((unsigned long long*)&cs->status, (unsigned long long)dev::ld_rlx64((unsigned long long*)&q.status));
   dev::st_sys64(&cs->tag, q.tag);
   dev::st_sys64(&cs->sum, dev::ld_rlx64(&q.sum));
@@ -392,8 +416,23 @@ extern "C" int gfs_serve_stop(gfs_ctx* ctx) {
   gfs_server* s = ctx->server;
   if (!s) return 0;
   __atomic_store_n(s->h_stop, 1u, __ATOMIC_RELEASE);
-  const int rc = cerr(cudaStreamSynchronize(s->stream));
+  // completions not polled by now are discarded: keep the ring drained so no CTA
+  // waits for a slot while the kernel finishes its last requests
+  cudaError_t q;
+  while ((q = cudaStreamQuery(s->stream)) == cudaErrorNotReady) {
+    for (;;) {
+      const unsigned long long c = s->compl_head;
+      ComplSlot* cs = &s->h_compl[c % s->h.compl_slots];
+      if (__atomic_load_n(&cs->seq, __ATOMIC_ACQUIRE) != c + 1) break;
+      __atomic_store_n(&cs->seq, c + s->h.compl_slots, __ATOMIC_RELEASE);
+      s->compl_head = c + 1;
+    }
+    usleep(100);
+  }
+  int rc = cerr(q);
+  unsigned long long lost = 0;
+  if (!rc) rc = cerr(cudaMemcpy(&lost, &s->h.ctl->lost.v, 8, cudaMemcpyDeviceToHost));
   free_server(s);
   ctx->server = nullptr;
-  return rc;
+  return rc ? rc : (lost ? -ENOBUFS : 0);
 }
