@@ -623,6 +623,7 @@ __device__ __forceinline__ void pull_finish(const DevHandle& g, const PullJob& j
   if (c == np) {
     __threadfence_system();
     st_rel_sys64(&ring_slot(g, j.s)->seq, j.t + g.rpc_slots);
+    st_rel64(&g.slot_free[j.s], j.t + g.rpc_slots);
     atomicAdd(&g.ctrl->freed.v, 1ull);
   }
 }
@@ -751,6 +752,14 @@ static __device__ bool block_help(const DevHandle& g, int target, bool any) {
 }
 
 // ---------------------------------------------------------------- request ring
+// The ticket slot `si` is free for: in the GPU copy transfers the GPU frees
+// slots itself and keeps a device copy (an L2 read instead of one over the host
+// link, which matters when many warps race for tickets); the DMA transfer's host
+// threads free them in the ring.
+__device__ __forceinline__ unsigned long long slot_free_for(const DevHandle& g, uint32_t si) {
+  return g.xfer != GFS_XFER_DMA ? ld_acq64(&g.slot_free[si]) : ld_acq_sys64(&ring_slot(g, si)->seq);
+}
+
 // Claim the next ticket of the ring whose slot is free for its lap (one warp).
 // A ticket is claimed (compare-and-swap, Vyukov's bounded queue) only after its
 // slot was seen free, so a claimed ticket is always published by the caller and
@@ -771,12 +780,11 @@ static __device__ int ring_acquire(const DevHandle& g, unsigned long long* t_out
       if (stat) {
         const unsigned long long lap = ld_rlx64(&g.slot_lap[own]);
         t = lap * g.rpc_slots + own;
-        if (ld_acq_sys64(&ring_slot(g, own)->seq) == t)
-          state = atomicCAS(&g.slot_lap[own], lap, lap + 1) == lap ? 1 : 2;
+        if (slot_free_for(g, own) == t) state = atomicCAS(&g.slot_lap[own], lap, lap + 1) == lap ? 1 : 2;
         if (state == 1) atomicAdd(&g.ctrl->ring_tail.v, 1ull);  // requests issued (drain counts them)
       } else {
         t = ld_rlx64(&g.ctrl->ring_tail.v);
-        if (ld_acq_sys64(&ring_slot(g, (uint32_t)(t % g.rpc_slots))->seq) == t)
+        if (slot_free_for(g, (uint32_t)(t % g.rpc_slots)) == t)
           state = atomicCAS(&g.ctrl->ring_tail.v, t, t + 1) == t ? 1 : 2;
       }
       if (state == 0 && now_ns() > deadline) state = 3;
@@ -1279,6 +1287,7 @@ static __device__ int block_paper_job(const DevHandle& g, int stream, uint32_t f
     }
     __threadfence_system();
     st_rel_sys64(&ring_slot(g, j.slot)->seq, j.t + g.rpc_slots);
+    st_rel64(&g.slot_free[j.slot], j.t + g.rpc_slots);
     atomicAdd(&g.ctrl->freed.v, 1ull);
     st_rel(&g.fstate[j.f], first_ok ? (uint32_t)FR_READY : (uint32_t)FR_ERROR);
   }
@@ -1654,6 +1663,7 @@ static __device__ int rpc_control(const DevHandle& g, uint32_t op, uint32_t fid,
     ls = vm->last;
     __threadfence_system();
     st_rel_sys64(&s->seq, t + g.rpc_slots);  // the slot is free for the next lap
+    if (g.xfer != GFS_XFER_DMA) st_rel64(&g.slot_free[si], t + g.rpc_slots);
     atomicAdd(&g.ctrl->freed.v, 1ull);
   }
   *status = bcast(st);

@@ -615,7 +615,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
                o_dtick = take((size_t)c.rpc_slots * 8), o_dnp = take((size_t)c.rpc_slots * 4),
                o_dcop = take((size_t)c.rpc_slots * 4), o_dfr = take((size_t)c.rpc_slots * c.max_rpc_pages * 4),
                o_fsrc = take((size_t)F * 4), o_lat = take((size_t)std::max<uint32_t>(1, c.latency_capacity) * 8),
-               o_lap = take((size_t)c.rpc_slots * 8);
+               o_lap = take((size_t)c.rpc_slots * 8), o_sfree = take((size_t)c.rpc_slots * 8);
   ctx->arena_bytes = off;
   rc = cuda_err(cudaMalloc(&ctx->d_arena, off));
   if (!rc) rc = cuda_err(cudaMemset(ctx->d_arena, 0, off));
@@ -654,6 +654,16 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.lat_cap = c.latency_capacity;
   g.queue = c.queue;
   g.slot_lap = (unsigned long long*)(a + o_lap);  // zero: every slot at lap 0, for the life of the context
+  g.slot_free = (unsigned long long*)(a + o_sfree);
+  {
+    std::vector<unsigned long long> init(c.rpc_slots);
+    for (uint32_t i = 0; i < c.rpc_slots; ++i) init[i] = i;  // slot i free for ticket i, like its seq
+    rc = cuda_err(cudaMemcpy(g.slot_free, init.data(), init.size() * 8, cudaMemcpyHostToDevice));
+    if (rc) {
+      gfs_shutdown(ctx);
+      return rc;
+    }
+  }
   g.staging = nullptr;
   g.done = nullptr;
   g.pages = nullptr;

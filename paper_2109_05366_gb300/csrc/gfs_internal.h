@@ -178,6 +178,8 @@ struct DevHandle {
   char* paths;                   // rpc_slots * GFS_PATH_MAX bytes, mapped pinned
   uint32_t queue;                // GFS_QUEUE_*
   unsigned long long* slot_lap;  // GFS_QUEUE_STATIC: per slot, requests placed in it so far
+  unsigned long long* slot_free; // GPU copy transfers: per slot, the ticket it is free for (device
+                                 // mirror of `seq` after the GPU frees it; slot i starts at i)
   // traces
   gfs_rpc_rec* trace_rpc;
   gfs_evict_rec* trace_evict;
