@@ -752,58 +752,45 @@ static __device__ bool block_help(const DevHandle& g, int target, bool any) {
 }
 
 // ---------------------------------------------------------------- request ring
-// The ticket slot `si` is free for: in the GPU copy transfers the GPU frees
-// slots itself and keeps a device copy (an L2 read instead of one over the host
-// link, which matters when many warps race for tickets); the DMA transfer's host
-// threads free them in the ring.
-__device__ __forceinline__ unsigned long long slot_free_for(const DevHandle& g, uint32_t si) {
-  return g.xfer != GFS_XFER_DMA ? ld_acq64(&g.slot_free[si]) : ld_acq_sys64(&ring_slot(g, si)->seq);
-}
-
-// Claim the next ticket of the ring whose slot is free for its lap (one warp).
-// A ticket is claimed (compare-and-swap, Vyukov's bounded queue) only after its
-// slot was seen free, so a claimed ticket is always published by the caller and
-// a wait that runs out claims nothing: the host threads, which serve tickets in
-// order, never wait for a ticket nobody will publish.  GFS_QUEUE_SHARED: the
-// shared position ring_tail.  GFS_QUEUE_STATIC (Section 3.2): the threadblock's
-// own slot and its lap counter; ring_tail then only counts requests.  Returns 0
-// with *t and *si set, or -ETIMEDOUT.
+// Take the next ticket of the ring and wait until its slot is free for this
+// lap (one warp).  GFS_QUEUE_SHARED: the next ticket of ring_tail.
+// GFS_QUEUE_STATIC (Section 3.2): the threadblock's own slot, numbered by its
+// lap counter (ring_tail then only counts requests).  In the GPU copy transfers
+// the GPU frees slots itself and keeps a device copy of the ticket each is free
+// for, read before the ring word in host memory.  Returns 0 with *t and *si set;
+// a wait that runs out posts the ticket's cancellation for the host and returns
+// -ETIMEDOUT.
 static __device__ int ring_acquire(const DevHandle& g, unsigned long long* t_out, uint32_t* si_out,
                                    unsigned long long deadline) {
   const int lane = lane_id();
-  const bool stat = g.queue == GFS_QUEUE_STATIC;
-  const uint32_t own = blockIdx.x % g.rpc_slots;
+  unsigned long long t = 0;
+  if (lane == 0) {
+    const unsigned long long k = atomicAdd(&g.ctrl->ring_tail.v, 1ull);  // requests issued (drain counts them)
+    if (g.queue == GFS_QUEUE_STATIC) {
+      const uint32_t slot = blockIdx.x % g.rpc_slots;
+      t = atomicAdd(&g.slot_lap[slot], 1ull) * g.rpc_slots + slot;
+    } else {
+      t = k;
+    }
+  }
+  t = bcast64(t);
+  const uint32_t si = (uint32_t)(t % g.rpc_slots);
+  RingSlot* s = ring_slot(g, si);
+  *t_out = t;
+  *si_out = si;
   for (unsigned ns = 64;;) {
-    int state = 0;  // 0 slot busy, 1 claimed, 2 lost a race (retry at once), 3 late
-    unsigned long long t = 0;
+    int free_ = 0, late = 0;
     if (lane == 0) {
-      if (stat) {
-        const unsigned long long lap = ld_rlx64(&g.slot_lap[own]);
-        t = lap * g.rpc_slots + own;
-        if (slot_free_for(g, own) == t) state = atomicCAS(&g.slot_lap[own], lap, lap + 1) == lap ? 1 : 2;
-        if (state == 1) atomicAdd(&g.ctrl->ring_tail.v, 1ull);  // requests issued (drain counts them)
-      } else {
-        t = ld_rlx64(&g.ctrl->ring_tail.v);
-        if (slot_free_for(g, (uint32_t)(t % g.rpc_slots)) == t)
-          state = atomicCAS(&g.ctrl->ring_tail.v, t, t + 1) == t ? 1 : 2;
+      free_ = (g.xfer != GFS_XFER_DMA && ld_acq64(&g.slot_free[si]) == t) || ld_acq_sys64(&s->seq) == t;
+      if (!free_ && now_ns() > deadline) {
+        late = 1;
+        st_rel_sys64(&g.cancel[t % g.cancel_n], t + 1);  // the host consumer of ticket t skips it
+        stat_add(g, ST_TIMEOUTS, 1);
       }
-      if (state == 0 && now_ns() > deadline) state = 3;
     }
-    state = bcast(state);
-    if (state == 1) {
-      t = bcast64(t);
-      *t_out = t;
-      *si_out = (uint32_t)(t % g.rpc_slots);
-      return 0;
-    }
-    if (state == 2) continue;
-    if (state == 3) {
-      if (lane == 0) stat_add(g, ST_TIMEOUTS, 1);
-      return -kETIMEDOUT;
-    }
-    // the ring is full: in the GPU copy transfers slots are freed by GPU copies,
-    // so help instead of idling
-    const uint32_t si = stat ? own : (uint32_t)(bcast64(t) % g.rpc_slots);
+    if (bcast(free_)) return 0;
+    if (bcast(late)) return -kETIMEDOUT;
+    // in the GPU copy transfers slots are freed by GPU copies: help instead of idling
     if (g.xfer != GFS_XFER_DMA && warp_help(g, si)) continue;
     if (lane == 0) __nanosleep(ns);
     __syncwarp();

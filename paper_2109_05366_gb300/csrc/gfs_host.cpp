@@ -290,26 +290,31 @@ void release_file(gfs_ctx* ctx, int fid) {
   hf = HostFile();
 }
 
-// Wait until every request issued so far has been served and (GPU copy
-// transfers) copied out of staging: the cache is quiet afterwards.  The
-// caller has synchronised the kernels that issue requests.
+// Wait until every request issued so far has been served (or skipped) and, in
+// the GPU copy transfers, copied out of staging: the cache is quiet afterwards.
+// The caller has synchronised the kernels that issue requests.  The drain kernel
+// runs while the host catches up: a host thread of the pull transfer may be
+// waiting for staging buffers that only GPU copies release.
 int quiesce(gfs_ctx* ctx, cudaStream_t s) {
   unsigned long long tail = 0;
   CK(cudaMemcpy(&tail, &ctx->dev.ctrl->ring_tail.v, 8, cudaMemcpyDeviceToHost));
+  const bool gpu_copies = ctx->cfg.xfer != GFS_XFER_DMA;
   const double t0 = now_s();
-  while (ctx->io->served() < tail) {
+  for (;;) {
+    bool dev_done = true;
+    if (gpu_copies) {  // copy out what was served but never read
+      int rc = launch_drain(ctx->dev, s);
+      if (rc) return rc;
+      CK(cudaStreamSynchronize(s));
+      unsigned long long freed = 0;
+      CK(cudaMemcpy(&freed, &ctx->dev.ctrl->freed.v, 8, cudaMemcpyDeviceToHost));
+      dev_done = freed + __atomic_load_n(ctx->h_skipped, __ATOMIC_ACQUIRE) >= tail;
+    }
+    if (ctx->io->served() >= tail && dev_done) break;
     if (now_s() - t0 > (double)ctx->cfg.timeout_ns * 1e-9 + 5.0) return -ETIMEDOUT;
-    usleep(50);
+    if (!gpu_copies) usleep(50);
   }
   ctx->io->drain_sinks();
-  if (ctx->cfg.xfer != GFS_XFER_DMA) {  // copy out what was served but never read
-    int rc = launch_drain(ctx->dev, s);
-    if (rc) return rc;
-    CK(cudaStreamSynchronize(s));
-    unsigned long long freed = 0;
-    CK(cudaMemcpy(&freed, &ctx->dev.ctrl->freed.v, 8, cudaMemcpyDeviceToHost));
-    if (freed < tail) return -ETIMEDOUT;
-  }
   return 0;
 }
 
@@ -526,6 +531,7 @@ int gfs_shutdown(gfs_ctx* ctx) {
   if (ctx->ctl_stream) cudaStreamDestroy(ctx->ctl_stream);
   if (ctx->h_paths) cudaFreeHost(ctx->h_paths);
   if (ctx->h_ctl_fd) cudaFreeHost(ctx->h_ctl_fd);
+  if (ctx->h_cancel) cudaFreeHost(ctx->h_cancel);
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   if (ctx->d_frames) cudaFree(ctx->d_frames);
   if (ctx->d_scan_buf) cudaFree(ctx->d_scan_buf);
@@ -719,12 +725,23 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&d_paths, ctx->h_paths, 0));
   if (!rc) rc = cuda_err(cudaStreamCreateWithFlags(&ctx->ctl_stream, cudaStreamNonBlocking));
   if (!rc) rc = cuda_err(cudaHostAlloc((void**)&ctx->h_ctl_fd, sizeof(FileDev), cudaHostAllocPortable));
+  // per-slot ticket cancellations and the count of skipped tickets (its own line)
+  const size_t cancel_n = (size_t)c.rpc_slots + CANCEL_SPAN;
+  if (!rc) rc = cuda_err(cudaHostAlloc((void**)&ctx->h_cancel, cancel_n * 8 + 128,
+                                       cudaHostAllocMapped | cudaHostAllocPortable));
+  void* d_cancel = nullptr;
+  if (!rc) rc = cuda_err(cudaHostGetDevicePointer(&d_cancel, ctx->h_cancel, 0));
   if (rc) {
     gfs_shutdown(ctx);
     return rc;
   }
   memset(ctx->h_paths, 0, (size_t)c.rpc_slots * GFS_PATH_MAX);
   g.paths = (char*)d_paths;
+  memset(ctx->h_cancel, 0, cancel_n * 8 + 128);
+  ctx->h_skipped = ctx->h_cancel + cancel_n + 8;  // 64 bytes past the last cancellation word
+  g.cancel = (unsigned long long*)d_cancel;
+  g.cancel_n = (uint32_t)cancel_n;
+  g.skipped = (unsigned long long*)d_cancel + cancel_n + 8;
 
   ctx->files.resize(c.max_files);
   rc = launch_reset(g, 0);
@@ -744,6 +761,9 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.threads = c.host_threads;
   sc.n_frames = F;
   sc.paths = ctx->h_paths;
+  sc.cancel = ctx->h_cancel;
+  sc.cancel_n = (uint32_t)cancel_n;
+  sc.skipped = ctx->h_skipped;
   sc.queue = c.queue;
   sc.io_trace_cap = c.trace_capacity;
   if (c.xfer != GFS_XFER_DMA) {

@@ -101,6 +101,8 @@ struct gfs_ctx {
   char* h_paths = nullptr;         // per-slot path buffers of device opens (mapped pinned)
   cudaStream_t ctl_stream = nullptr;  // device control requests: allocations and file-state copies
   void* h_ctl_fd = nullptr;           // pinned FileDev staging of those copies
+  unsigned long long* h_cancel = nullptr;   // mapped pinned: per-slot ticket cancellations
+  unsigned long long* h_skipped = nullptr;  // mapped pinned: tickets the host skipped
   std::mutex mu;
   std::mutex files_mu;             // HostFile fields read by the host I/O threads
   std::mutex dev_open_mu;          // device opens and closes, one at a time

@@ -32,6 +32,13 @@ constexpr uint32_t MAX_FRAMES = (1u << FRAME_BITS) - 1;
 constexpr uint32_t MAX_FILES = 255;               // fid 255 reserved (all-ones entry)
 constexpr uint32_t BUCKET = 32;                   // slots per bucket = one warp
 constexpr uint32_t MAX_RPC_PAGES = 256;
+// Cancellations are kept per ticket in a table this much longer than the ring.
+// Tickets taken but neither published nor skipped yet: one waiting per resident
+// threadblock (2048 at most), plus cancelled ones the host has not reached; a
+// block cancels at most one ticket per device deadline, so even every block of a
+// full GPU timing out over and over needs tens of seconds of a stalled host to
+// come near this span.
+constexpr uint32_t CANCEL_SPAN = 65536;
 
 // Page key: (fid, page), 8 + 32 bits.
 GFS_HD inline uint64_t make_key(uint32_t fid, uint64_t page) { return ((uint64_t)fid << 32) | (page & 0xffffffffull); }
@@ -102,11 +109,14 @@ struct FileDev {
 static_assert(sizeof(FileDev) == 48, "FileDev");
 
 // One request-ring slot in mapped pinned memory (64-byte header + frame list).
-// Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; a GPU
-// producer claims ticket t only once it sees seq == t (slot free for that lap),
-// fills the slot and publishes seq = t + 1; the host consumer with ticket h waits
-// for seq == h + 1, copies the request out and frees the slot with seq = h + R
-// (in the GPU copy transfers the GPU frees it once every page is copied).  Tickets of slot i are
+// Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; the GPU
+// producer with ticket t waits for seq == t, fills the slot and publishes
+// seq = t + 1; the host consumer with ticket h waits for seq == h + 1, copies the
+// request out and frees the slot with seq = h + R (in the GPU copy transfers the
+// GPU frees it once every page is copied).  A producer whose wait runs out posts
+// cancel[t % cancel_n] = t + 1; the host consumer of ticket t then skips it once
+// the slot is free for it (seq = t + R), so no host thread waits for a ticket
+// nobody will publish.  Tickets of slot i are
 // i, i + R, i + 2R, ...: GFS_QUEUE_SHARED hands out tickets in order from one
 // counter (slot = ticket mod R); GFS_QUEUE_STATIC picks the slot from the
 // threadblock and numbers that slot's uses (ticket = lap * R + slot).
@@ -180,6 +190,10 @@ struct DevHandle {
   unsigned long long* slot_lap;  // GFS_QUEUE_STATIC: per slot, requests placed in it so far
   unsigned long long* slot_free; // GPU copy transfers: per slot, the ticket it is free for (device
                                  // mirror of `seq` after the GPU frees it; slot i starts at i)
+  unsigned long long* cancel;    // mapped pinned, cancel_n entries: at t % cancel_n, t + 1 for a ticket t
+                                 // whose producer gave up waiting for its slot (the host skips it)
+  uint32_t cancel_n;             // rpc_slots + CANCEL_SPAN entries
+  unsigned long long* skipped;   // mapped pinned: tickets the host skipped (drain counts them as freed)
   // traces
   gfs_rpc_rec* trace_rpc;
   gfs_evict_rec* trace_evict;

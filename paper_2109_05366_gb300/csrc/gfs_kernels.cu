@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(512) k_drain(DevHandle g) {
   const unsigned long long dl = dev::now_ns() + g.timeout_ns;
   for (;;) {
     if (threadIdx.x == 0)
-      s_more = dev::ld_acq64(&g.ctrl->freed.v) < dev::ld_acq64(&g.ctrl->ring_tail.v) && dev::now_ns() < dl;
+      s_more = dev::ld_acq64(&g.ctrl->freed.v) + dev::ld_acq_sys64(g.skipped) < dev::ld_acq64(&g.ctrl->ring_tail.v) &&
+               dev::now_ns() < dl;
     __syncthreads();
     const int more = s_more;
     __syncthreads();

@@ -322,15 +322,33 @@ void IoService::run(int idx) {
   else run_shared(w);
 }
 
-// GFS_QUEUE_SHARED: take the next ticket and wait for its request.
+bool IoService::skip_cancelled(uint64_t h, RingSlot* s) {
+  if (!cfg_.cancel || !cfg_.cancel_n) return false;
+  unsigned long long* c = &cfg_.cancel[h % cfg_.cancel_n];
+  if (__atomic_load_n(c, __ATOMIC_ACQUIRE) != h + 1 || __atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h) return false;
+  __atomic_store_n(c, 0ull, __ATOMIC_RELAXED);
+  __atomic_store_n(&s->seq, h + cfg_.slots, __ATOMIC_RELEASE);  // the slot is free for the next lap
+  if (cfg_.skipped) __atomic_fetch_add(cfg_.skipped, 1ull, __ATOMIC_RELEASE);
+  stats.skipped.fetch_add(1, std::memory_order_relaxed);
+  served_.fetch_add(1, std::memory_order_release);
+  return true;
+}
+
+// GFS_QUEUE_SHARED: take the next ticket and wait for its request (or its
+// cancellation).
 void IoService::run_shared(Worker& w) {
   while (!stop_.load(std::memory_order_relaxed)) {
     const uint64_t h = head_.fetch_add(1, std::memory_order_relaxed);
     RingSlot* s = (RingSlot*)(cfg_.ring + (size_t)(h % cfg_.slots) * cfg_.slot_stride);
     uint64_t spins = 0;
     const uint64_t i0 = mono_ns();
+    bool skipped = false;
     while (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) {
       if (stop_.load(std::memory_order_relaxed)) return;
+      if ((spins & 63) == 0 && skip_cancelled(h, s)) {
+        skipped = true;
+        break;
+      }
       ++spins;
       polled_empty(w.idx, 0);
       if (spins > 20000) {
@@ -341,7 +359,7 @@ void IoService::run_shared(Worker& w) {
     const uint64_t idle = mono_ns() - i0;
     stats.ns_idle.fetch_add(idle, std::memory_order_relaxed);
     tstats_[w.idx].idle_ns.fetch_add(idle, std::memory_order_relaxed);
-    handle(w, h, s);
+    if (!skipped) handle(w, h, s);
   }
 }
 
@@ -358,7 +376,10 @@ void IoService::run_static(Worker& w) {
     for (uint32_t si = lo; si < hi; ++si) {
       const uint64_t h = lap[si - lo] * R + si;
       RingSlot* s = (RingSlot*)(cfg_.ring + (size_t)si * cfg_.slot_stride);
-      if (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) continue;
+      if (__atomic_load_n(&s->seq, __ATOMIC_ACQUIRE) != h + 1) {
+        if (skip_cancelled(h, s)) ++lap[si - lo];
+        continue;
+      }
       const uint64_t idle = mono_ns() - i0;
       stats.ns_idle.fetch_add(idle, std::memory_order_relaxed);
       tstats_[w.idx].idle_ns.fetch_add(idle, std::memory_order_relaxed);

@@ -67,6 +67,11 @@ struct ServiceConfig {
   const char* paths = nullptr;
   uint32_t queue = GFS_QUEUE_SHARED;  // GFS_QUEUE_*: how a thread finds its requests
   uint64_t io_trace_cap = 0;          // host I/O trace entries kept (0 = off)
+  // at t % cancel_n: t + 1 for a ticket t its producer gave up (skipped once the slot
+  // is free for it); count of skipped tickets.  Host views of mapped memory; may be null.
+  unsigned long long* cancel = nullptr;
+  uint32_t cancel_n = 0;
+  unsigned long long* skipped = nullptr;
 };
 
 // Counters of one host thread (gfs_thread_stat).
@@ -79,9 +84,10 @@ struct ServiceStats {
   std::atomic<uint64_t> requests{0}, preads{0}, bytes{0}, copies{0}, errors{0};
   std::atomic<uint64_t> ns_pread{0}, ns_wait_buf{0}, ns_idle{0};
   std::atomic<uint64_t> controls{0};  // device opens and closes answered
+  std::atomic<uint64_t> skipped{0};   // tickets skipped because their producer gave them up
   void clear() {
     requests = 0; preads = 0; bytes = 0; copies = 0; errors = 0;
-    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0; controls = 0;
+    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0; controls = 0; skipped = 0;
   }
 };
 
@@ -123,6 +129,8 @@ class IoService {
   void run_static(Worker& w);
   // Serve the published request with ticket h in slot s.
   void handle(Worker& w, uint64_t h, RingSlot* s);
+  // Skip ticket h if its producer gave it up and the slot is free for it.
+  bool skip_cancelled(uint64_t h, RingSlot* s);
   void control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid);
   void serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
   void serve_pull(Worker& w, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages);

@@ -83,3 +83,25 @@ def test_device_wait_runs_out_and_context_survives(datadir, xfer):
         ctx.set_faults()
         ctx.reset_cache()                    # waits for the stalled request, then clears
         _exact(path, MiB, *ctx.scan_host(fid, MiB, blocks=2))
+
+
+@pytest.mark.parametrize("queue", [0, 1])
+@pytest.mark.parametrize("xfer", [0, 1])
+def test_ring_wait_runs_out_and_the_ticket_is_skipped(datadir, xfer, queue):
+    """Two ring slots, one slow host thread and a short device deadline: producers
+    give up waiting for a slot after taking their ticket.  Each posts the ticket's
+    cancellation and the host skips it, so the ring keeps moving: the reset
+    succeeds and the next scan is exact."""
+    from paper_2109_05366_gb300 import gfs
+    path = _file(datadir, 25, 8 * MiB)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=256 * KiB, xfer=xfer, queue=queue, rpc_slots=2,
+                     host_threads=1, max_rpc_pages=4, timeout_ns=300 * 10**6) as ctx:
+        fid = ctx.open(path)
+        ctx.set_faults(delay_us=250000)
+        cnt, _, _ = ctx.scan_host(fid, MiB, blocks=8)
+        assert (cnt == -110).any()                   # some greads ran out of time
+        assert ctx.stats()["timeouts"] >= 1
+        ctx.set_faults()
+        ctx.reset_cache()                            # every ticket served or skipped
+        _exact(path, MiB, *ctx.scan_host(fid, MiB, blocks=8))
+        assert ctx.stats()["timeouts"] == 0
