@@ -211,7 +211,13 @@ int gfs_fstat(gfs_ctx* ctx, int fid, gfs_stat* st);
 int gfs_set_faults(gfs_ctx* ctx, uint32_t eio_every, uint32_t short_every, uint32_t delay_us);
 
 /* Drop every cached page, clear the counters, traces and stream history.
- * Enqueued on `stream`; the ring keeps running.  Waits for requests in flight. */
+ * Synchronises `stream`, then waits until every request issued so far has been
+ * served (or skipped: a device wait that ran out before its request got a ring
+ * slot posts the request's cancellation, and the host skips it), copies out
+ * what was served but never read (GPU copy transfers), and clears the cache on
+ * `stream`.  No kernel of the context may be running on another stream.
+ * -ETIMEDOUT if the host does not finish within timeout_ns + 5 s (the context
+ * is then unusable and should be shut down). */
 int gfs_reset_cache(gfs_ctx* ctx, void* stream);
 
 /* Read the counters (synchronises `stream`). */
