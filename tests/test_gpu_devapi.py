@@ -119,6 +119,20 @@ def test_scan_path_exact_and_shared_id(torch_cuda, gfs, datadir, xfer):
         assert st["timeouts"] == 0 and st["eio"] == 0
 
 
+@pytest.mark.parametrize("xfer", [0, 2])
+def test_scan_path_with_static_queue_and_per_block_lra(torch_cuda, gfs, datadir, xfer):
+    path = _file(datadir, 29, 40 * MiB + 77)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=256 * KiB, xfer=xfer, queue=1, replacement=1, rpc_slots=16,
+                     host_threads=4, max_rpc_pages=16) as ctx:
+        for _ in range(2):
+            out = ctx.scan_path(path, MiB, blocks=32)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            assert st["host_controls"] == 64 and st["timeouts"] == 0 and st["evictions"] > 0
+            ctx.reset_cache()
+
+
 def test_scan_path_ids_retire_until_reset(torch_cuda, gfs, datadir):
     a = _file(datadir, 26, 2 * MiB + 5)
     b = _file(datadir, 27, 2 * MiB + 9)

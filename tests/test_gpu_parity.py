@@ -325,6 +325,28 @@ def test_pull_partial_requests_are_helped(torch_cuda, gfs, datadir):
 
 # ------------------------------------------------ readahead with the per-block LRA of Section 5.1
 @pytest.mark.parametrize("xfer", XFERS)
+@pytest.mark.parametrize("replacement", ["fifo", "tb_lra"])
+def test_serialized_logs_do_not_depend_on_the_queue(torch_cuda, gfs, datadir, xfer, replacement):
+    """GPUfs's static slot partition carries the same requests as the shared ring: with
+    one gread at a time the logs still equal the oracle's."""
+    size, page, frames, blocks, stride, ra = 24 * MiB + 999, 256 * KiB, 24, 6, 512 * KiB, 2
+    path = _file(datadir, 12, size)
+    reserve = policy.default_reserve(blocks, stride, page)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=0, ra_cap_pages=ra, queue=1, rpc_slots=4,
+                     host_threads=2, replacement=(1 if replacement == "tb_lra" else 0), reserve_frames=reserve,
+                     trace_capacity=1 << 16, max_rpc_pages=16, xfer=xfer, timeout_ns=2 * 10**9) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode="readahead", ra_cap=ra, reserve=reserve,
+                               max_rpc_pages=16, replacement=replacement)
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
+@pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("size,page,frames,blocks,stride,ra_cap,async_ra", [
     (24 * MiB + 999, 256 * KiB, 24, 6, 512 * KiB, 2, 1),     # file 4x the cache, quota 4
     (16 * MiB + 7, 64 * KiB, 40, 4, 192 * KiB, 8, 0),        # sync readahead only, quota 10

@@ -559,3 +559,36 @@ def test_paper_mode_prefetches_duplicates_and_delivers_plain_bytes(tmp_path):
     assert [r[0] for r in res] == c and [r[1] for r in res] == s and [r[2] for r in res] == h
     assert max(sim.stats.fetch_count.values()) > 1        # duplicates happen
     assert sim.stats.buffer_hits > 0
+
+
+@pytest.mark.parametrize("mode,replacement", [("readahead", "fifo"), ("readahead", "tb_lra"), ("ondemand", "fifo"),
+                                              ("ondemand", "tb_lra"), ("paper", "fifo"), ("paper", "tb_lra")])
+def test_random_configurations_deliver_the_file_and_keep_the_invariants(tmp_path, mode, replacement):
+    """Seeded random page sizes, cache sizes, streams, strides and read lengths: every
+    gread delivers exactly the file's bytes, every request stays inside the file and the
+    request cap, frames never exceed the cache, and a page is never mapped twice."""
+    import random
+    rng = random.Random(hash((mode, replacement)) & 0xffff)
+    for trial in range(6):
+        P = rng.choice([4096, 8192, 65536])
+        npages = rng.randint(5, 60)
+        size = npages * P - rng.randint(0, P - 1)
+        path = _file(tmp_path, "rc%d" % trial, 40 + trial, size)
+        ref = open(path, "rb").read()
+        blocks = rng.randint(1, 5)
+        frames = rng.randint(max(blocks * 2, 3), 3 * npages)
+        stride = P * rng.randint(1, 4) + rng.choice([0, 0, 17])
+        read_len = max(1, stride - rng.choice([0, 1, 100]))
+        cap = rng.choice([4, 16])
+        sim = policy.PageCacheSim(P, frames, mode, ra_cap=rng.choice([1, 3, 8]), reserve=blocks + 1,
+                                  async_ra=rng.random() < 0.5, max_rpc_pages=cap, replacement=replacement,
+                                  streams=blocks)
+        sim.open(0, path)
+        for stream, fid, off, ln in policy.canonical_scan_trace(size, stride, blocks, read_len):
+            n, data = sim.gread(stream, fid, off, ln)
+            assert n == len(data) == min(ln, max(0, size - off))
+            assert data == ref[off:off + n]
+            assert len(sim.table) <= frames and len(set(sim.table.values())) == len(sim.table)
+        for fid, lo, n, kind in sim.rpc_log:
+            assert 0 <= lo and lo + n <= npages and 1 <= n <= cap
+        sim.close_all()
