@@ -38,6 +38,8 @@ WORKLOADS = {
     "cfg1_64MiB_file_128MiB_cache": (64 * MiB, 1, 256 * KiB, 128 * MiB, 64, MiB),
     # same shape as the 8 GiB workload at a quarter of the size (profiling captures)
     "cfg2s_2GiB_file_256MiB_cache": (2 * GiB, 2, 512 * KiB, 256 * MiB, 296, MiB),
+    # the same with 4 KiB pages (profiling the per-page cost of small pages)
+    "cfg2s4k_2GiB_file_256MiB_cache_4KiB_pages": (2 * GiB, 2, 4 * KiB, 256 * MiB, 296, MiB),
 }
 DEFAULT_WORKLOAD = "cfg2_8GiB_file_1GiB_cache"
 METRIC = "sequential gread GB/s (readahead vs on-demand vs CPU-I/O) + % link roofline; p50/p99 latency"
