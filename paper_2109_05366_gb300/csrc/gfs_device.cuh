@@ -259,8 +259,9 @@ static __device__ void tab_remove(const DevHandle& g, unsigned long long key, ui
 
 // ---------------------------------------------------------------- consumed FIFO
 // Bounded MPMC queue (Vyukov) over fifo_cap cells; each frame is in it at most once.
-static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
-  unsigned long long t = atomicAdd(&g.ctrl->fifo_tail.v, 1ull);
+// Store frame f into cell t, a ticket the caller took from fifo_tail.
+static __device__ bool fifo_put(const DevHandle& g, unsigned long long t, uint32_t f,
+                                unsigned long long deadline) {  // one thread
   unsigned long long* c = &g.fifo[t % g.fifo_cap];
   while ((ld_acq64(c) >> FRAME_BITS) != t) {
     if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return false; }
@@ -268,6 +269,9 @@ static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long l
   }
   st_rel64(c, ((t + 1) << FRAME_BITS) | f);
   return true;
+}
+static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
+  return fifo_put(g, atomicAdd(&g.ctrl->fifo_tail.v, 1ull), f, deadline);
 }
 
 // Returns a frame, -1 when empty, -ETIMEDOUT.
@@ -1393,6 +1397,99 @@ static __device__ void release_page(const DevHandle& g, int f, uint32_t nbytes, 
   if (push) fifo_push(g, (uint32_t)f, deadline);
 }
 
+// ---------------------------------------------------------------- page runs
+// With small pages a page's control chain (lookup, pin, mark check, release)
+// costs more than its copy, so a gread takes up to 32 consecutive pages that are
+// already in the cache at once, one lane per page.  A run ends before the first
+// page that is missing, in error, being reclaimed, or READY with a readahead
+// mark still set (R4 stays with the one-page path, at the page's turn).  The
+// pages of a run are released in page order, so the consumed FIFO receives the
+// same pushes, in the same order, as from pages read one at a time.
+constexpr uint32_t kRunMaxShift = 14;  // runs for pages of at most 16 KiB
+constexpr uint32_t kRunPages = 32;
+
+// Warp 0: look up and pin pages p .. p + k - 1 (k <= 32).  Returns the length of
+// the leading run of pages that are READY without a mark, FILLING or COPYING;
+// their frames and states are left in s_f / s_st, pinned.  Pages after the run
+// are left unpinned.
+static __device__ uint32_t run_begin(const DevHandle& g, uint32_t fid, unsigned long long p, uint32_t k, bool marks,
+                                     uint32_t* s_f, int* s_st) {
+  const int lane = lane_id();
+  int f = -1;  // frame of page p + lane
+  // home buckets only, eight keys in flight: a key in an overflow bucket ends the run
+  for (uint32_t q0 = 0; q0 < k; q0 += 8) {
+    unsigned long long e[8];
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      const uint32_t b = bucket_of(make_key(fid, p + q0 + j), g.nbuckets);
+      e[j] = q0 + j < k ? ld_rlx64(&g.tab[(size_t)b * BUCKET + lane]) : ENTRY_EMPTY;
+    }
+    bool gap = false;
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      const unsigned long long key = make_key(fid, p + q0 + j);
+      const unsigned m = __ballot_sync(kFull, e[j] != ENTRY_EMPTY && (e[j] >> FRAME_BITS) == key);
+      const int fj = m ? (int)(__shfl_sync(kFull, e[j], __ffs(m) - 1) & MAX_FRAMES) : -1;
+      if (lane == (int)(q0 + j)) f = fj;
+      gap |= q0 + j < k && fj < 0;
+    }
+    if (gap) break;
+  }
+  // pin as frame_pin does, one lane per page
+  const bool mine = (uint32_t)lane < k && f >= 0;
+  if (mine) atomicAdd(&g.fpins[f], 1u);
+  __threadfence();
+  int st = -1;
+  bool ok = false;
+  if (mine) {
+    st = (int)ld_acq(&g.fstate[f]);
+    ok = (st == FR_READY || st == FR_FILLING || st == FR_COPYING) && ld_rlx64(&g.fkey[f]) == make_key(fid, p + lane);
+    // a READY page's mark was set before the page was published
+    if (ok && st == FR_READY && marks && ld_rlx(&g.fmark[f]) != 0u) ok = false;
+  }
+  const unsigned okm = __ballot_sync(kFull, ok);
+  const uint32_t c = okm == kFull ? 32u : (uint32_t)(__ffs(~okm) - 1);
+  if (mine && (uint32_t)lane >= c) atomicSub(&g.fpins[f], 1u);
+  if ((uint32_t)lane < c) {
+    s_f[lane] = (uint32_t)f;
+    s_st[lane] = st;
+  }
+  __syncwarp();
+  return c;
+}
+
+// Warp 0, after the block copied the run: R5 for its n pages (page p + i in frame
+// s_f[i]; the gread covers [off, end)).  FIFO cells are reserved with one ticket
+// add and filled in page order.
+static __device__ void run_release(const DevHandle& g, const uint32_t* s_f, uint32_t n, unsigned long long p,
+                                   unsigned long long off, unsigned long long end, unsigned long long deadline) {
+  const int lane = lane_id();
+  const bool mine = (uint32_t)lane < n;
+  bool push = false;
+  uint32_t f = 0;
+  if (mine) {
+    f = s_f[lane];
+    const unsigned long long base = (p + lane) << g.page_shift;
+    const unsigned long long lo = off > base ? off : base;
+    const unsigned long long hi = end < base + g.page_size ? end : base + g.page_size;
+    const uint32_t nb = (uint32_t)(hi - lo);
+    const uint32_t c = atomicAdd(&g.fconsumed[f], nb);
+    if (g.repl != GFS_REPL_TB_LRA) {  // per-threadblock LRA queues keep no consumed FIFO
+      const uint32_t v = ld_rlx(&g.fvalid[f]);
+      push = c < v && c + nb >= v;
+    }
+  }
+  __threadfence();
+  if (mine) atomicSub(&g.fpins[f], 1u);
+  const unsigned m = __ballot_sync(kFull, push);
+  if (!m) return;
+  unsigned long long t0 = 0;
+  if (lane == 0) t0 = atomicAdd(&g.ctrl->fifo_tail.v, (unsigned long long)__popc(m));
+  t0 = bcast64(t0);
+  if (push) fifo_put(g, t0 + (unsigned long long)__popc(m & ((1u << lane) - 1u)), f, deadline);
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------- copy-out
 // Checksum accumulators of the stride-scan consumer (per thread).
 struct Sums {
@@ -1418,14 +1515,14 @@ __device__ __forceinline__ void sums_add1(Sums& s, uint8_t b, unsigned long long
   s.hash += (o + 1) * (unsigned long long)b;
 }
 
-// Copy n bytes of a cache frame (src) to the user buffer (dst).  Frame data is
-// read through L2 (ld.global.cg): frames are rewritten by the copy engine, so
-// L1 may hold an older page.  With FUSED the checksums of the copied bytes are
-// accumulated on the way (src_off = file offset of src[0]).
+// Copy n bytes of a cache frame (src) to the user buffer (dst), thread `tid` of
+// the `nt` that share the copy.  Frame data is read through L2 (ld.global.cg):
+// frames are rewritten by the copy engine, so L1 may hold an older page.  With
+// FUSED the checksums of the copied bytes are accumulated on the way (src_off =
+// file offset of src[0]).
 template <bool FUSED>
-__device__ __forceinline__ void copy_out(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n,
-                                         unsigned long long src_off, Sums& acc) {
-  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+__device__ __forceinline__ void copy_range(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n,
+                                           unsigned long long src_off, Sums& acc, uint32_t tid, uint32_t nt) {
   const uint32_t phase_s = (uint32_t)((uintptr_t)src & 15), phase_d = (uint32_t)((uintptr_t)dst & 15);
   if (phase_s == phase_d) {
     uint32_t head = (16 - phase_s) & 15;
@@ -1472,6 +1569,13 @@ __device__ __forceinline__ void copy_out(const uint8_t* __restrict__ src, uint8_
   }
 }
 
+// The whole block copies.
+template <bool FUSED>
+__device__ __forceinline__ void copy_out(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, uint32_t n,
+                                         unsigned long long src_off, Sums& acc) {
+  copy_range<FUSED>(src, dst, n, src_off, acc, threadIdx.x, blockDim.x);
+}
+
 // Block-wide sum of two u64 values (mod 2^64); the result is valid in thread 0.
 __device__ __forceinline__ void block_sum2(unsigned long long& a, unsigned long long& b) {
   __shared__ unsigned long long ra[32], rb[32];
@@ -1497,6 +1601,72 @@ __device__ __forceinline__ void block_sum2(unsigned long long& a, unsigned long 
 }
 
 // ---------------------------------------------------------------- gread
+// Whole block: read the run of cached pages that starts at page p (p1 = last
+// page of the gread, which covers [off, end) into buf): pin it, wait for pages
+// still being filled in page order, copy it a warp per page, release it.  Returns
+// the number of pages read (0: page p takes the one-page path) or -errno.
+// Kept out of line so that it leaves the one-page path's registers alone.
+template <bool FUSED>
+__device__ __noinline__ long long read_run(const DevHandle& g, uint32_t fid, unsigned long long p,
+                                           unsigned long long p1, unsigned long long off, unsigned long long end,
+                                           uint8_t* buf, bool marks, unsigned long long deadline, Sums* part) {
+  __shared__ uint32_t s_rf[kRunPages], s_rn;
+  __shared__ int s_rst[kRunPages], s_mark;
+  const uint32_t tid = threadIdx.x;
+  if (tid < 32) {
+    const unsigned long long left = p1 - p + 1;
+    const uint32_t c = run_begin(g, fid, p, left < kRunPages ? (uint32_t)left : kRunPages, marks, s_rf, s_rst);
+    if (tid == 0) s_rn = c;
+  }
+  __syncthreads();
+  uint32_t n = s_rn;
+  // a mark found on a waited page once it is READY ends the run before it
+  for (uint32_t i = 0; i < n; ++i) {
+    if (s_rst[i] == FR_READY) continue;
+    const int st = block_wait_ready(g, (int)s_rf[i], deadline);
+    if (st != FR_READY) {
+      if (tid == 0) {
+        for (uint32_t j = 0; j < n; ++j) frame_unpin(g, (int)s_rf[j]);
+        stat_add(g, ST_HITS, i + 1);
+        if (st == FR_ERROR) stat_add(g, ST_EIO, 1);
+      }
+      __syncthreads();
+      return st < 0 ? st : -kEIO;
+    }
+    if (marks) {
+      if (tid == 0) s_mark = ld_rlx(&g.fmark[s_rf[i]]) != 0u;
+      __syncthreads();
+      const int mk = s_mark;
+      __syncthreads();
+      if (mk) {
+        if (tid == 0)
+          for (uint32_t j = i; j < n; ++j) frame_unpin(g, (int)s_rf[j]);
+        n = i;
+      }
+    }
+  }
+  if (n == 0) return 0;
+  if (tid == 0) {
+    uint32_t waited = 0;
+    for (uint32_t i = 0; i < n; ++i) waited += s_rst[i] != FR_READY;
+    stat_add(g, ST_HITS, n);
+    stat_add(g, ST_COALESCED, waited);
+  }
+  Sums acc{0ull, 0ull};
+  const uint32_t lane = tid & 31, nw = blockDim.x >> 5;
+  for (uint32_t i = tid >> 5; i < n; i += nw) {  // a warp per page
+    const unsigned long long base = (p + i) << g.page_shift;
+    const unsigned long long lo = (off > base ? off : base) - base;
+    const unsigned long long hi = (end < base + g.page_size ? end : base + g.page_size) - base;
+    copy_range<FUSED>(g.frames + ((size_t)s_rf[i] << g.page_shift) + lo, buf + (base + lo - off),
+                      (uint32_t)(hi - lo), base + lo, acc, lane, 32);
+  }
+  if (FUSED) *part = acc;
+  __syncthreads();
+  if (tid < 32) run_release(g, s_rf, n, p, off, end, deadline);
+  return n;
+}
+
 // Threadblock-collective read of [off, off + len) of file `fid` into buf.
 // Every thread of the block must call it with the same arguments.  `stream`
 // identifies the reader for sequential detection (the threadblock).  Returns
@@ -1521,7 +1691,25 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
   const unsigned long long seq0 = s_seq0;
   const unsigned long long deadline = now_ns() + g.timeout_ns;
   long long err = 0;
-  for (unsigned long long p = p0; p <= p1; ++p) {
+  const bool runs = g.mode != GFS_MODE_PAPER && g.page_shift <= kRunMaxShift && p1 > p0;
+  const bool marks = g.mode == GFS_MODE_READAHEAD && g.async_ra && fi.ra;
+  for (unsigned long long p = p0; p <= p1;) {
+    if (runs) {
+      Sums part{0ull, 0ull};
+      const long long n = read_run<FUSED>(g, (uint32_t)fid, p, p1, off, end, buf, marks, deadline, &part);
+      if (n < 0) {
+        err = n;
+        break;
+      }
+      if (n) {
+        if (FUSED) {
+          acc.sum += part.sum;
+          acc.hash += part.hash;
+        }
+        p += (unsigned long long)n;
+        continue;
+      }
+    }
     if (tid == 0) s_job.kind = PJ_NONE;
     __syncthreads();
     if (tid < 32) {
@@ -1560,6 +1748,7 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
                     base + lo, acc);
     __syncthreads();
     if (tid == 0) release_page(g, f, (uint32_t)(hi - lo), deadline);
+    ++p;
   }
   if (tid == 0 && stream >= 0 && (uint32_t)stream < g.max_streams)
     st_rlx64(&g.last_end[(size_t)stream * g.max_files + fid], p1 + 2);  // end page + 1

@@ -92,6 +92,11 @@ def test_config1_second_pass_hits(torch_cuda, gfs, datadir):
     (24 * MiB, 256 * KiB, 24, 6, 512 * KiB, 2, 0, 1),
     (16 * MiB + 7, 64 * KiB, 40, 4, 192 * KiB, 8, 0, 0),   # sync readahead only
     (8 * MiB, 128 * KiB, 10, 4, 256 * KiB, 8, 1, 1),       # on-demand
+    # small pages: greads take runs of cached pages, released in page order
+    (4 * MiB + 5, 4 * KiB, 256, 4, 64 * KiB, 8, 0, 1),
+    (2 * MiB + 3, 16 * KiB, 48, 4, 128 * KiB, 4, 0, 1),
+    (3 * MiB + 7, 4 * KiB, 200, 6, 40 * KiB + 4, 15, 0, 0),  # runs start and end inside pages
+    (2 * MiB, 4 * KiB, 128, 4, 64 * KiB, 8, 1, 1),           # on-demand
 ])
 def test_serialized_logs_match_oracle(torch_cuda, gfs, datadir, size, page, frames, blocks, stride, ra_cap, mode,
                                       async_ra, xfer):
@@ -112,6 +117,36 @@ def test_serialized_logs_match_oracle(torch_cuda, gfs, datadir, size, page, fram
 
 
 # ------------------------------------------------ concurrent: larger than the cache
+@pytest.mark.parametrize("xfer", XFERS)
+@pytest.mark.parametrize("page", [4 * KiB, 16 * KiB])
+def test_small_pages_streaming_and_cached_exact(torch_cuda, gfs, datadir, page, xfer):
+    """Small pages through a cache 4x smaller than the file, many blocks (runs of pages
+    still being filled, readahead marks inside runs), then a file that fits, read twice
+    (the second scan is all runs of cached pages)."""
+    big = _file(datadir, 13, 64 * MiB + 4097)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=page, xfer=xfer, max_rpc_pages=64,
+                     ra_cap_pages=min(63, MiB // page)) as ctx:
+        fid = ctx.open(big)
+        for fused in (False, True):
+            out = ctx.scan(fid, 256 * KiB, blocks=48, threads=256, fused=fused)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, big, 256 * KiB, *out)
+        st = ctx.stats()
+        assert st["timeouts"] == 0 and st["eio"] == 0 and st["enomem"] == 0
+    small = _file(datadir, 14, 6 * MiB + 333)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=page, xfer=xfer, max_rpc_pages=64,
+                     ra_cap_pages=min(63, MiB // page)) as ctx:
+        fid = ctx.open(small)
+        for _ in range(2):
+            out = ctx.scan(fid, 96 * KiB + 8, blocks=32, threads=256, fused=True)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, small, 96 * KiB + 8, *out)
+        st = ctx.stats()
+        assert st["pages_fetched"] == (6 * MiB + 333 + page - 1) // page  # fits: every page once
+        assert st["timeouts"] == 0 and st["eio"] == 0
+
+
+
 @pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("threads", [256, 512])
 def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads, xfer):
@@ -136,6 +171,8 @@ def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads, xfer):
     (700 * KiB + 3, 300 * KiB + 5, 64 * KiB),  # odd offsets: unaligned copy path
     (64 * KiB, 64 * KiB, 2 * MiB),       # 32 blocks share one page
     (3 * MiB, 2 * MiB + 1, 1 * MiB),
+    (100 * KiB + 3, 50 * KiB + 7, 4 * KiB),  # runs of small pages from unaligned offsets
+    (256 * KiB, 256 * KiB, 16 * KiB),
 ])
 def test_ragged_strides_exact(torch_cuda, gfs, datadir, stride, read_len, page, xfer):
     size = 40 * MiB + 999
@@ -351,6 +388,7 @@ def test_serialized_logs_do_not_depend_on_the_queue(torch_cuda, gfs, datadir, xf
     (24 * MiB + 999, 256 * KiB, 24, 6, 512 * KiB, 2, 1),     # file 4x the cache, quota 4
     (16 * MiB + 7, 64 * KiB, 40, 4, 192 * KiB, 8, 0),        # sync readahead only, quota 10
     (8 * MiB, 128 * KiB, 64, 2, 128 * KiB, 8, 1),            # file as large as the cache, quota 32 each
+    (4 * MiB + 5, 4 * KiB, 256, 4, 64 * KiB, 8, 1),          # small pages: runs of cached pages
 ])
 def test_readahead_per_block_lra_serialized_logs_match_oracle(torch_cuda, gfs, datadir, xfer, size, page, frames,
                                                                blocks, stride, ra_cap, async_ra):
