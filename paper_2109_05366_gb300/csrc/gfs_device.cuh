@@ -258,17 +258,34 @@ static __device__ void tab_remove(const DevHandle& g, unsigned long long key, ui
 }
 
 // ---------------------------------------------------------------- consumed FIFO
-// Bounded MPMC queue (Vyukov) over fifo_cap cells; each frame is in it at most once.
-// Store frame f into cell t, a ticket the caller took from fifo_tail.
+// Bounded MPMC queue over fifo_cap cells; each frame is in it at most once.  Cell
+// t % cap holds (seq << FRAME_BITS) | frame: seq = t while free for the push of
+// ticket t, t + 1 once that push landed, t + cap once popped (free for the next
+// lap).  Both ends take tickets by fetch-and-add (one atomic per operation, no
+// retry loop every block contends on).  A pop whose ticket ran past the tail
+// gives the ticket up by moving its cell straight to t + cap; the push that later
+// draws that ticket sees a cell already past it and draws another.  Give-ups only
+// happen when the queue is empty, so the order of the frames in it is kept.
+
+// Store frame f into cell t, a ticket the caller took from fifo_tail (another if
+// a pop gave that one up).
 static __device__ bool fifo_put(const DevHandle& g, unsigned long long t, uint32_t f,
                                 unsigned long long deadline) {  // one thread
-  unsigned long long* c = &g.fifo[t % g.fifo_cap];
-  while ((ld_acq64(c) >> FRAME_BITS) != t) {
+  __threadfence();  // the frame's state before its entry
+  for (;;) {
+    unsigned long long* c = &g.fifo[t % g.fifo_cap];
+    const unsigned long long v = ld_acq64(c), s = v >> FRAME_BITS;
+    if (s == t) {  // a CAS: a pop may give this ticket up at the same time
+      if (atomicCAS(c, v, ((t + 1) << FRAME_BITS) | f) == v) return true;
+      continue;
+    }
+    if (s > t) {  // given up by a pop
+      t = atomicAdd(&g.ctrl->fifo_tail.v, 1ull);
+      continue;
+    }
     if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return false; }
     __nanosleep(32);
   }
-  st_rel64(c, ((t + 1) << FRAME_BITS) | f);
-  return true;
 }
 static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
   return fifo_put(g, atomicAdd(&g.ctrl->fifo_tail.v, 1ull), f, deadline);
@@ -276,19 +293,29 @@ static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long l
 
 // Returns a frame, -1 when empty, -ETIMEDOUT.
 static __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
+  if (ld_rlx64(&g.ctrl->fifo_head.v) >= ld_rlx64(&g.ctrl->fifo_tail.v)) return -1;
+  const unsigned long long h = atomicAdd(&g.ctrl->fifo_head.v, 1ull);
+  unsigned long long* c = &g.fifo[h % g.fifo_cap];
+  const unsigned long long gone = ((h + g.fifo_cap) << FRAME_BITS) | MAX_FRAMES;
   for (;;) {
-    unsigned long long h = ld_acq64(&g.ctrl->fifo_head.v);
-    unsigned long long t = ld_acq64(&g.ctrl->fifo_tail.v);
-    if (h >= t) return -1;
-    if (atomicCAS(&g.ctrl->fifo_head.v, h, h + 1) != h) continue;
-    unsigned long long* c = &g.fifo[h % g.fifo_cap];
-    unsigned long long v;
-    while (((v = ld_acq64(c)) >> FRAME_BITS) != h + 1) {
-      if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return -kETIMEDOUT; }
-      __nanosleep(32);
+    const unsigned long long v = ld_acq64(c), s = v >> FRAME_BITS;
+    if (s == h + 1) {
+      st_rel64(c, gone);
+      return (int)(v & MAX_FRAMES);
     }
-    st_rel64(c, ((h + g.fifo_cap) << FRAME_BITS) | MAX_FRAMES);
-    return (int)(v & MAX_FRAMES);
+    const bool late = now_ns() > deadline;
+    // not pushed: give the ticket up if no push holds it (the queue was empty),
+    // or when out of time
+    if (s == h && (late || ld_acq64(&g.ctrl->fifo_tail.v) <= h)) {
+      if (atomicCAS(c, v, gone) == v) {
+        if (!late) return -1;
+        stat_add(g, ST_TIMEOUTS, 1);
+        return -kETIMEDOUT;
+      }
+      continue;  // the push landed first
+    }
+    if (late) { stat_add(g, ST_TIMEOUTS, 1); return -kETIMEDOUT; }
+    __nanosleep(32);
   }
 }
 
