@@ -149,8 +149,8 @@ def data_dir():
 # DRAM bytes per scanned file byte of k_scan, from the ncu capture summarised in
 # profiles/k_scan_cfg2s_2GiB_sol.md (2 GiB case; traffic grows with the bytes scanned),
 # valid only while the kernel's sources are those it was taken on.
-NCU_DRAM = {"kernel_digest": "50e22fa11a66098e94075605a8f846aa7eb0fe6d394f93cf77c5c87f7951eb85",
-            "bytes_per_file_byte": (2.962231e9 + 4.321885e9) / (2 * GiB),
+NCU_DRAM = {"kernel_digest": "d3c191e3b452ee2a164f9feb0138460c06b329b1bba23eb632c5cb630fa1e3cd",
+            "bytes_per_file_byte": (2.982510e9 + 4.350567e9) / (2 * GiB),
             "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 2 GiB case scaled by bytes scanned"}
 
 
