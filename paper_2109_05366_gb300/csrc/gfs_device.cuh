@@ -154,18 +154,45 @@ static __device__ int tab_lookup(const DevHandle& g, unsigned long long key) {
   uint32_t b = bucket_of(key, g.nbuckets);
   for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {
     unsigned long long e = ld_rlx64(&g.tab[(size_t)b * BUCKET + lane]);
+    int ovf = 0;
+    if (lane == 0) ovf = (int)ld_rlx(&g.tovf[b]);  // in flight with the bucket
     bool hit = e != ENTRY_EMPTY && (e >> FRAME_BITS) == key;
     unsigned m = __ballot_sync(kFull, hit);
     if (m) {
       unsigned long long w = __shfl_sync(kFull, e, __ffs(m) - 1);
       return (int)(w & MAX_FRAMES);
     }
-    int ovf = 0;
-    if (lane == 0) ovf = (int)ld_rlx(&g.tovf[b]);
     if (!bcast(ovf)) return -1;
     b = (b + 1) & (g.nbuckets - 1);
   }
   return -1;
+}
+
+// Warp: how many of the pages p, p + 1, ..., p + k - 1 (k <= 32), counted from p,
+// are not in the table before the first that is.  Eight keys are looked up at a
+// time (eight bucket loads in flight, with their overflow flags); a key missing
+// from a bucket that overflowed is followed along the chain by tab_lookup.
+static __device__ uint32_t absent_prefix(const DevHandle& g, uint32_t fid, unsigned long long p, uint32_t k) {
+  const int lane = lane_id();
+  for (uint32_t q0 = 0; q0 < k; q0 += 8) {
+    unsigned long long e[8];
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      const uint32_t b = bucket_of(make_key(fid, p + q0 + j), g.nbuckets);
+      e[j] = q0 + j < k ? ld_rlx64(&g.tab[(size_t)b * BUCKET + lane]) : ENTRY_EMPTY;
+    }
+    const uint32_t jb = bucket_of(make_key(fid, p + q0 + (lane & 7)), g.nbuckets);
+    const uint32_t ovf = lane < 8 && q0 + lane < k ? ld_rlx(&g.tovf[jb]) : 0u;
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+      if (q0 + j >= k) return k;
+      const unsigned long long key = make_key(fid, p + q0 + j);
+      bool present = __ballot_sync(kFull, e[j] != ENTRY_EMPTY && (e[j] >> FRAME_BITS) == key) != 0u;
+      if (!present && __shfl_sync(kFull, ovf, (int)j) != 0u) present = tab_lookup(g, key) >= 0;
+      if (present) return q0 + j;
+    }
+  }
+  return k;
 }
 
 static __device__ bool bucket_lock(const DevHandle& g, uint32_t b, unsigned long long deadline) {
@@ -291,10 +318,9 @@ static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long l
   return fifo_put(g, atomicAdd(&g.ctrl->fifo_tail.v, 1ull), f, deadline);
 }
 
-// Returns a frame, -1 when empty, -ETIMEDOUT.
-static __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
-  if (ld_rlx64(&g.ctrl->fifo_head.v) >= ld_rlx64(&g.ctrl->fifo_tail.v)) return -1;
-  const unsigned long long h = atomicAdd(&g.ctrl->fifo_head.v, 1ull);
+// The frame of ticket h, drawn by the caller from fifo_head: -1 when the ticket
+// was given up (no push held it), -ETIMEDOUT.
+static __device__ int fifo_take(const DevHandle& g, unsigned long long h, unsigned long long deadline) {  // one thread
   unsigned long long* c = &g.fifo[h % g.fifo_cap];
   const unsigned long long gone = ((h + g.fifo_cap) << FRAME_BITS) | MAX_FRAMES;
   for (;;) {
@@ -317,6 +343,12 @@ static __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) 
     if (late) { stat_add(g, ST_TIMEOUTS, 1); return -kETIMEDOUT; }
     __nanosleep(32);
   }
+}
+
+// Returns a frame, -1 when empty, -ETIMEDOUT.
+static __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
+  if (ld_rlx64(&g.ctrl->fifo_head.v) >= ld_rlx64(&g.ctrl->fifo_tail.v)) return -1;
+  return fifo_take(g, atomicAdd(&g.ctrl->fifo_head.v, 1ull), deadline);
 }
 
 // ---------------------------------------------------------------- frames
@@ -892,6 +924,144 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
   return 0;
 }
 
+// Warp: frames for pages 1 .. L of a request (page i of the request is a
+// readahead page when i >= demand), victim classes 1 and 2 only, taken in page
+// order into s_frames[1 ..] exactly as one take_frame per page would take them:
+// never-used frames first (one fetch-and-add for the run), then the consumed FIFO
+// (one ticket add per round).  A readahead page needs never + consumed > reserve
+// at its turn, and every page before it in the run has taken one frame since page
+// 0 did.  Returns how many pages, from page 1 on, got a frame; claimed victims
+// still hold their old keys.
+static __device__ uint32_t take_run(const DevHandle& g, uint32_t L, uint32_t demand, unsigned long long deadline,
+                                    uint32_t* s_frames) {
+  const int lane = lane_id();
+  const uint32_t first_ra = demand > 1 ? demand : 1u;
+  if (L >= first_ra) {  // ra_allowed at page i: N0 - (i - 1) > reserve, i.e. i <= N0 - reserve
+    long long lim = 0;
+    if (lane == 0) {
+      const unsigned long long used = ld_rlx64(&g.ctrl->next_unused.v);
+      const unsigned long long never = used >= g.n_frames ? 0 : g.n_frames - used;
+      const unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
+      lim = (long long)(never + (t > h ? t - h : 0)) - (long long)g.reserve;
+    }
+    lim = (long long)bcast64((unsigned long long)lim);
+    const long long last = lim > (long long)first_ra - 1 ? lim : (long long)first_ra - 1;
+    if ((long long)L > last) L = (uint32_t)last;
+  }
+  if (L == 0) return 0;
+  // class 1: never-used frames, lowest index first
+  unsigned long long u0 = 0;
+  uint32_t got = 0;
+  if (lane == 0 && ld_rlx64(&g.ctrl->next_unused.v) < g.n_frames) {
+    u0 = atomicAdd(&g.ctrl->next_unused.v, (unsigned long long)L);
+    if (u0 < g.n_frames) got = g.n_frames - u0 < L ? (uint32_t)(g.n_frames - u0) : L;
+  }
+  got = (uint32_t)bcast((int)got);
+  u0 = bcast64(u0);
+  for (uint32_t j = lane; j < got; j += 32) s_frames[1 + j] = (uint32_t)(u0 + j);
+  // class 2: the consumed FIFO, oldest first; a pinned entry goes back to the tail
+  for (uint32_t round = 0; got < L && round < 8; ++round) {
+    unsigned long long h0 = 0;
+    uint32_t take = 0;
+    if (lane == 0) {
+      const unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
+      const unsigned long long avail = t > h ? t - h : 0;
+      take = avail < L - got ? (uint32_t)avail : L - got;
+      if (take) h0 = atomicAdd(&g.ctrl->fifo_head.v, (unsigned long long)take);
+    }
+    take = (uint32_t)bcast((int)take);
+    h0 = bcast64(h0);
+    if (take == 0) break;
+    for (uint32_t j0 = 0; j0 < take; j0 += 32) {
+      int c = -1, claimed = -1;
+      if (j0 + lane < take) {
+        c = fifo_take(g, h0 + j0 + lane, deadline);
+        if (c >= 0) {
+          claimed = frame_claim(g, c, true);
+          if (claimed == 0) fifo_push(g, (uint32_t)c, deadline);
+        }
+      }
+      const unsigned m = __ballot_sync(kFull, claimed == 1);
+      if (claimed == 1) s_frames[1 + got + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
+      got += (uint32_t)__popc(m);
+    }
+  }
+  __syncwarp();
+  return got;
+}
+
+// Warp: pages 1 .. of a request whose page 0 is installed (page i is p + i, a
+// readahead page when i >= demand).  The run is cut, as one page at a time would
+// cut it, at EOF, at the first page already in the table and at the first
+// readahead page fetched since the last reset (R8), then by take_run.  Victims
+// lose their old pages in page order, metadata is written a lane per page (one
+// sequence-number add), and the table entries go in in page order.  Returns how
+// many pages from page 1 on were installed; their frames are in s_frames[1 ..].
+static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p,
+                                       uint32_t want, uint32_t demand, unsigned long long seq0,
+                                       unsigned long long deadline, uint32_t* s_frames) {
+  const int lane = lane_id();
+  unsigned long long lim = want - 1ull;
+  if (p + 1 + lim > fi.npages) lim = fi.npages > p + 1 ? fi.npages - p - 1 : 0;
+  uint32_t L = 0;
+  while (L < lim) {
+    const uint32_t k = lim - L < 32ull ? (uint32_t)(lim - L) : 32u;
+    const uint32_t a = absent_prefix(g, fid, p + 1 + L, k);
+    L += a;
+    if (a < k) break;
+  }
+  if (fi.fetched) {  // R8
+    for (uint32_t i0 = demand > 1 ? demand : 1u; i0 <= L; i0 += 32) {
+      const uint32_t i = i0 + (uint32_t)lane;
+      const unsigned long long q = p + i;
+      const bool done = i <= L && ((ld_rlx(&fi.fetched[q >> 5]) >> (q & 31)) & 1u);
+      const unsigned m = __ballot_sync(kFull, done);
+      if (m) {
+        L = i0 + (uint32_t)__ffs(m) - 2;
+        break;
+      }
+    }
+  }
+  L = take_run(g, L, demand, deadline, s_frames);
+  if (L == 0) return 0;
+  for (uint32_t j = 1; j <= L; ++j) evict_key(g, (int)s_frames[j], make_key(fid, p + j), deadline);
+  unsigned long long a0 = 0;
+  if (lane == 0) a0 = atomicAdd(&g.ctrl->alloc_counter.v, (unsigned long long)L);
+  a0 = bcast64(a0);
+  for (uint32_t j = 1 + (uint32_t)lane; j <= L; j += 32) {  // metadata first, then FILLING, then the table
+    const uint32_t f = s_frames[j];
+    const unsigned long long q = p + j;
+    st_rlx64(&g.fkey[f], make_key(fid, q));
+    st_rlx(&g.fconsumed[f], 0u);
+    st_rlx(&g.fwindow[f], 0u);
+    st_rlx(&g.fmark[f], 0u);
+    st_rlx(&g.fvalid[f], expected_valid(g, fi, q));
+    st_rlx64(&g.faseq[f], ((a0 + j - 1) << kOwnerBits) | (seq0 & kOwnerMask));
+    if (g.fsrc) st_rlx(&g.fsrc[f], SRC_NONE);
+  }
+  __threadfence();
+  for (uint32_t j = 1 + (uint32_t)lane; j <= L; j += 32) st_rel(&g.fstate[s_frames[j]], FR_FILLING);
+  __syncwarp();
+  for (uint32_t j = 1; j <= L; ++j) {
+    const uint32_t f = s_frames[j];
+    const int r = tab_insert(g, make_key(fid, p + j), f, deadline);
+    if (r != (int)f) {  // inserted by someone else meanwhile: this frame and the rest go back
+      if (lane == 0)
+        for (uint32_t jj = j; jj <= L; ++jj) frame_return(g, (int)s_frames[jj], false, deadline);
+      __syncwarp();
+      L = j - 1;
+      break;
+    }
+  }
+  for (uint32_t j = 1 + (uint32_t)lane; j <= L; j += 32) {
+    const unsigned long long q = p + j;
+    if (fi.fetched) atomicOr(&fi.fetched[q >> 5], 1u << (q & 31));
+    if (g.fetch_count && fid == 0 && q < g.debug_pages) atomicAdd(&g.fetch_count[q], 1u);
+  }
+  __syncwarp();
+  return L;
+}
+
 // Allocate and install frames for [p, p + want): the first `demand` pages are
 // demand pages, the rest readahead.  Cut at EOF, at the first present page and
 // when no readahead victim is allowed.  Frames go to s_frames; the first is
@@ -918,6 +1088,9 @@ static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid
   if (want > g.max_rpc_pages) want = g.max_rpc_pages;
   uint32_t n = 0;
   for (uint32_t i = 0; i < want; ++i) {
+    // with the consumed FIFO, the pages after the first are taken as one run
+    if (i == 1 && g.repl != GFS_REPL_TB_LRA)
+      return 1 + (int)install_run(g, fid, fi, p, want, demand, seq0, deadline, s_frames);
     const unsigned long long q = p + i;
     if (q >= fi.npages) break;
     const unsigned long long key = make_key(fid, q);
@@ -1019,7 +1192,14 @@ static __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, 
   uint32_t d = 1, T = 1;
   bool seq = false;
   if (ra) {
-    while (p + d <= p1 && d < g.max_rpc_pages && tab_lookup(g, make_key(fid, p + d)) < 0) ++d;  // R2
+    // R2: the demand run is p and the absent pages after it, within the gread and a request
+    const unsigned long long cap = p1 - p < g.max_rpc_pages - 1ull ? p1 - p : g.max_rpc_pages - 1ull;
+    while (d - 1 < cap) {
+      const uint32_t k = cap - (d - 1) < 32ull ? (uint32_t)(cap - (d - 1)) : 32u;
+      const uint32_t a = absent_prefix(g, fid, p + d, k);
+      d += a;
+      if (a < k) break;
+    }
     int prev = -1;
     seq = p == 0;                                                                              // R3
     if (!seq) {
