@@ -146,9 +146,9 @@ def data_dir():
     return tempfile.gettempdir()
 
 
-# DRAM bytes per scanned file byte of k_scan, from the ncu capture summarised in
-# profiles/k_scan_cfg2s_2GiB_sol.md (2 GiB case; traffic grows with the bytes scanned),
-# valid only while the kernel's sources are those it was taken on.
+# DRAM bytes per scanned file byte of k_scan, from an ncu capture of the 2 GiB
+# quarter-scale case (traffic grows with the bytes scanned), valid only while the
+# kernel's sources are those it was taken on.
 NCU_DRAM = {"kernel_digest": "5550a86d83b8ba230fa9250701d29308befd21e929ea73648f5916d39ea11802",
             "bytes_per_file_byte": (2.968324e9 + 4.351640e9) / (2 * GiB),
             "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 2 GiB case scaled by bytes scanned"}

@@ -58,13 +58,28 @@ extern "C" {
 #define GFS_ADV_SEQUENTIAL 1
 #define GFS_ADV_RANDOM 2
 
-/* How a served request reaches the cache frames. */
+/* How a served request reaches the cache frames.
+ * In GFS_XFER_PULL and GFS_XFER_MAPPED the host I/O threads make no CUDA call:
+ * the GPU copies every page itself, so a kernel waiting for a page depends only
+ * on host threads and its own blocks.  In GFS_XFER_DMA the waiting kernel
+ * depends on copies the host threads issue on side streams while it runs;
+ * anything that serialises GPU work (a profiler's kernel replay or launch
+ * capture, a debugger, some MPS set-ups) then holds those copies back until the
+ * kernel's device deadline expires (-ETIMEDOUT).  Use DMA only where kernels
+ * and copies run concurrently. */
 #define GFS_XFER_DMA 0  /* host: pread -> pinned staging -> cudaMemcpyAsync -> stream write of the frame state */
 #define GFS_XFER_PULL 1 /* host: pread -> pinned staging; GPU copies staging -> frames over the host link */
-#define GFS_XFER_MAPPED 2 /* the file's page cache is mapped for the GPU (shared mapping registered with
-                           * CUDA); the host serves a request by publishing where its pages are and the
-                           * GPU copies them into frames over the host link.  Files that cannot be mapped
-                           * read-write (permissions, file system) fall back to GFS_XFER_PULL. */
+#define GFS_XFER_MAPPED 2 /* default.  The file's page cache is mapped for the GPU (shared mapping
+                           * registered with CUDA); the host serves a request by publishing where its
+                           * pages are and the GPU copies them into frames over the host link.  Only a
+                           * file whose pages are all resident in the host page cache at gfs_open is
+                           * mapped (registration pins every page; a page not yet read would be read
+                           * from storage inside gfs_open).  The mapping is opened read-write, because
+                           * read-only registration is not available on every platform; the library
+                           * never writes through it.  A file that is not fully resident, cannot be
+                           * opened read-write (permissions) or cannot be registered (file systems
+                           * whose pages cannot be pinned) is served as in GFS_XFER_PULL;
+                           * gfs_stat.mapped tells which. */
 
 /* How requests are placed in the ring and how host threads find them (gfs_config.queue). */
 #define GFS_QUEUE_SHARED 0 /* one shared ring: the GPU takes the next ticket, any host thread serves any
@@ -176,7 +191,8 @@ typedef struct gfs_scan_args {
 
 /* Fill *cfg with defaults: 1 GiB cache, 512 KiB pages, readahead, Wmax 8,
  * async readahead on, 128 slots, 64 pages per request, 16 host threads,
- * 4 MiB staging, 4096 streams, 16 files, no trace, DMA transfer, device 0. */
+ * 4 MiB staging, 4096 streams, 16 files, no trace, mapped transfer
+ * (GFS_XFER_MAPPED, falling back to pread staging per file), device 0. */
 int gfs_config_default(gfs_config* cfg);
 
 /* Create a context: allocates the cache frames and metadata in device memory,
@@ -189,7 +205,10 @@ int gfs_init(const gfs_config* cfg, gfs_ctx** out);
 int gfs_shutdown(gfs_ctx* ctx);
 
 /* Open `path` read-only; *fid (0 .. max_files-1) names it on host and device.
- * Readahead applies only with GFS_RDONLY (Section 4.4). */
+ * Readahead applies only with GFS_RDONLY (Section 4.4).  With GFS_XFER_MAPPED
+ * the open also maps and registers the file when it is fully resident in the
+ * host page cache (see GFS_XFER_MAPPED): that pins the whole file, which takes
+ * time in proportion to its size, and gfs_close unpins it. */
 int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid);
 
 /* Close a file id and drop its cached pages, so that a file opened later under
@@ -278,15 +297,22 @@ int gfs_scan_host(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* h_c
  * allocates (no cudaMalloc, cudaFree or allocating library routine): the
  * buffers live in a file-scope device array of GFS_STATIC_SCRATCH_BYTES that
  * every device loading the library holds until the process exits.
- *   - blocks * round_up(read_len, 256) must fit in GFS_STATIC_SCRATCH_BYTES,
- *     else the call returns -ENOSPC and launches nothing.
- *   - The first call on a device looks the array's device address up (once per
- *     device, with that device made current); make that first call before any
- *     stream capture.
+ *   - blocks * round_up(min(read_len, file size), 256) must fit in
+ *     GFS_STATIC_SCRATCH_BYTES, else the call returns -ENOSPC and launches
+ *     nothing.
+ *   - The first call on a device looks the array's device address up (with that
+ *     device made current) and caches it per device and CUDA context; make that
+ *     first call before any stream capture.  A caller that resets the device
+ *     (cudaDeviceReset) loses every context of this library anyway; the address
+ *     is then looked up again in the new context.
  *   - Every call shares the one array and leaves its contents behind; nothing
  *     in it needs to start at zero.  Calls whose kernels overlap on the GPU
  *     race on the array: serialise them (one stream, or events).
- * Arguments, outputs and the other errors are those of gfs_scan. */
+ *   - With GFS_MODE_PAPER or GFS_REPL_TB_LRA the context keeps per-threadblock
+ *     state that an allocating call sizes: -ENOTSUP until a gfs_scan (or
+ *     gfs_scan_path, gfs_read_many) with at least `blocks` threadblocks has run
+ *     on the context.
+ * Arguments and outputs are those of gfs_scan; its other errors apply too. */
 #define GFS_STATIC_SCRATCH_BYTES (64ull << 20)
 int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* args, int64_t* d_count, uint64_t* d_sum,
                     uint64_t* d_hash, void* stream);

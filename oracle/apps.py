@@ -33,9 +33,19 @@ def rowdot(path: str, rows: int, cols: int, vec: np.ndarray, row_lo: int = 0, ro
     return np.concatenate(dots), np.concatenate(abss)
 
 
-def histogram(path: str, nbins: int) -> tuple[np.ndarray, int]:
-    """(counts of each value < nbins, number of values outside [0, nbins))."""
-    x = np.fromfile(path, dtype=np.int32)
-    inside = (x >= 0) & (x < nbins)
-    counts = np.bincount(x[inside], minlength=nbins).astype(np.uint64)
-    return counts, int((~inside).sum())
+def histogram(path: str, nbins: int, piece_values: int = 1 << 26) -> tuple[np.ndarray, int]:
+    """(counts of each value < nbins, number of values outside [0, nbins)).
+
+    The file is counted `piece_values` values at a time (exact integer counts add up,
+    so the pieces only bound the memory a multi-GiB file needs)."""
+    counts = np.zeros(nbins, dtype=np.uint64)
+    outside = 0
+    with open(path, "rb") as f:
+        while True:
+            x = np.fromfile(f, dtype=np.int32, count=piece_values)
+            if x.size == 0:
+                break
+            inside = (x >= 0) & (x < nbins)
+            counts += np.bincount(x[inside], minlength=nbins).astype(np.uint64)
+            outside += int((~inside).sum())
+    return counts, outside

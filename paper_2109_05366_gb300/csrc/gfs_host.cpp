@@ -188,6 +188,19 @@ class HostSink : public Sink {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Whether every page of the mapping [m, m + len) is in the host page cache
+// (mincore; touches no page).
+bool fully_resident(void* m, size_t len) {
+  const long pg = sysconf(_SC_PAGESIZE);
+  if (pg <= 0) return false;
+  const size_t n = (len + (size_t)pg - 1) / (size_t)pg;
+  std::vector<unsigned char> v(n);
+  if (mincore(m, len, v.data()) != 0) return false;
+  for (unsigned char c : v)
+    if (!(c & 1)) return false;
+  return true;
+}
+
 bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
   if (fid >= ctx->files.size()) return false;
   std::lock_guard<std::mutex> lk(ctx->files_mu);
@@ -202,7 +215,11 @@ bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
 // GFS_XFER_MAPPED: map the file shared and register the mapping with CUDA so the
 // GPU can read its page-cache pages.  Registration of read-only mappings is not
 // available on every platform, so the mapping is read-write; nothing ever writes
-// through it.  Returns false (and leaves the file unmapped) when any step fails.
+// through it.  Only a file whose pages are all in the host page cache is mapped:
+// registration pins every page, so a page not yet read would be read from storage
+// inside the open, where no read is timed.  Returns false (and leaves the file
+// unmapped: its requests are then served by pread into staging) when the file is
+// not fully resident or any step fails.
 bool map_file(HostFile& hf) {
   if (hf.size == 0) return false;
   int rw = open(hf.path.c_str(), O_RDWR | O_CLOEXEC);
@@ -211,6 +228,10 @@ bool map_file(HostFile& hf) {
   void* m = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_SHARED, rw, 0);
   close(rw);
   if (m == MAP_FAILED) return false;
+  if (!fully_resident(m, len)) {
+    munmap(m, len);
+    return false;
+  }
   if (cudaHostRegister(m, len, cudaHostRegisterMapped) != cudaSuccess) {
     cudaGetLastError();
     munmap(m, len);
@@ -511,7 +532,7 @@ int gfs_config_default(gfs_config* c) {
   c->max_streams = 4096;
   c->max_files = 16;
   c->trace_capacity = 0;
-  c->xfer = GFS_XFER_DMA;
+  c->xfer = GFS_XFER_MAPPED;
   c->debug_counts = 0;
   c->device = 0;
   return 0;
@@ -1115,7 +1136,12 @@ static int scan_prepare(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint64_t*
   if (a->threads != 128 && a->threads != 256 && a->threads != 512) return -EINVAL;
   const uint64_t size = ctx->files[fid].size;
   *nstrides = size ? (size + a->stride - 1) / a->stride : 0;
-  *buf_stride = align_up(a->read_len, 256);
+  // a gread never delivers more than the file holds; the checks divide so that
+  // no size wraps around
+  const uint64_t per_block = std::min<uint64_t>(a->read_len, size);
+  if (per_block > SIZE_MAX / 2) return -ENOMEM;
+  *buf_stride = align_up(per_block, 256);
+  if (*buf_stride && a->blocks > SIZE_MAX / *buf_stride) return -ENOMEM;
   CK(cudaSetDevice(ctx->cfg.device));
   const size_t need = (size_t)a->blocks * *buf_stride;
   if (need > ctx->scan_buf_bytes) {
@@ -1130,9 +1156,10 @@ static int scan_prepare(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint64_t*
     if (prc) return prc;
   }
   *g = ctx->dev;
-  const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  const uint64_t pages_per_read = (a->read_len >> ctx->dev.page_shift) + ((a->read_len & (ctx->cfg.page_size - 1)) != 0);
   g->reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
-                                       : (uint32_t)std::min<uint64_t>(0xffffffffull, a->blocks * pages_per_read + 1);
+                                       : (uint32_t)(pages_per_read >= 0xffffffffull / a->blocks ? 0xffffffffull
+                                                                      : a->blocks * pages_per_read + 1);
   if (a->serialize) {
     int maxb = 0;
     int rc = scan_max_resident_blocks(a->threads, a->fused != 0, ctx->cfg.device, &maxb);
@@ -1171,14 +1198,18 @@ int gfs_scan_path(gfs_ctx* ctx, const char* path, const gfs_scan_args* a, int64_
   if (ns == 0) return 0;
   if (!d_count || !d_sum || !d_hash) return -EINVAL;
   CK(cudaSetDevice(ctx->cfg.device));
-  const uint64_t bs = align_up(a->read_len, 256);
+  const uint64_t per_block = std::min<uint64_t>(a->read_len, size);
+  if (per_block > SIZE_MAX / 2) return -ENOMEM;
+  const uint64_t bs = align_up(per_block, 256);
+  if (bs && a->blocks > SIZE_MAX / bs) return -ENOMEM;
   int rc = ensure_scan_buf(ctx, (size_t)a->blocks * bs);
   if (!rc) rc = ensure_paper_state(ctx, a->blocks);
   if (rc) return rc;
   DevHandle g = ctx->dev;
-  const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  const uint64_t pages_per_read = (a->read_len >> ctx->dev.page_shift) + ((a->read_len & (ctx->cfg.page_size - 1)) != 0);
   g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
-                                      : (uint32_t)std::min<uint64_t>(0xffffffffull, a->blocks * pages_per_read + 1);
+                                      : (uint32_t)(pages_per_read >= 0xffffffffull / a->blocks ? 0xffffffffull
+                                                                      : a->blocks * pages_per_read + 1);
   PathArg pa;
   memset(pa.s, 0, sizeof(pa.s));
   memcpy(pa.s, path, len);
@@ -1189,9 +1220,10 @@ int gfs_device_handle(gfs_ctx* ctx, uint32_t blocks, uint64_t read_len, void* ou
   if (!ctx || !out || blocks == 0 || read_len == 0) return -EINVAL;
   if (cap < sizeof(DevHandle)) return -ENOSPC;
   DevHandle g = ctx->dev;
-  const uint64_t pages_per_read = (read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
+  const uint64_t pages_per_read = (read_len >> ctx->dev.page_shift) + ((read_len & (ctx->cfg.page_size - 1)) != 0);
   g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
-                                      : (uint32_t)std::min<uint64_t>(0xffffffffull, blocks * pages_per_read + 1);
+                                      : (uint32_t)(pages_per_read >= 0xffffffffull / blocks ? 0xffffffffull
+                                                                      : blocks * pages_per_read + 1);
   memcpy(out, &g, sizeof(g));
   return (int)sizeof(DevHandle);
 }

@@ -1,6 +1,7 @@
 // Kernels of the GPU file-read path: the stride scan (Section 6.1 microbenchmark
 // shape: block b greads strides b, b+B, ... and checksums each), independent
 // greads, cache reset, and the checksum kernel of the CPU-I/O baseline.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <errno.h>
 
@@ -323,21 +324,42 @@ namespace {
 constexpr size_t kStaticScratchBytes = 64ull << 20;  // GFS_STATIC_SCRATCH_BYTES in include/gfs.h
 static __device__ __align__(256) uint8_t g_scan_scratch[kStaticScratchBytes];
 
+// The context an address was looked up in: a caller that resets the device and
+// so creates a new primary context gets the array's address looked up again.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+CUcontext current_context() {
+  if (!g_ctx_current) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_current = (CtxGetCurrentFn)fn;
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_current && g_ctx_current(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 // Device address of the scratch array on `device` (current).  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once per
-// device and cached.
+// device and context and cached.
 int static_scratch(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return -EINVAL;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[device]) {
+  const CUcontext cur = current_context();
+  if (!g_scratch_addr[device] || g_scratch_ctx[device] != cur) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scan_scratch);
     if (e != cudaSuccess || !p) return e == cudaErrorNoDevice ? -ENODEV : -EINVAL;
     g_scratch_addr[device] = p;
+    g_scratch_ctx[device] = cur;
   }
   *out = g_scratch_addr[device];
   return 0;
@@ -353,23 +375,27 @@ extern "C" int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* a, in
   if (a->threads != 128 && a->threads != 256 && a->threads != 512) return -EINVAL;
   const uint64_t size = ctx->files[fid].size;
   const uint64_t nstrides = size ? (size + a->stride - 1) / a->stride : 0;
-  const uint64_t buf_stride = (a->read_len + 255) / 256 * 256;
-  if ((uint64_t)a->blocks * buf_stride > kStaticScratchBytes) return -ENOSPC;  // beyond the static array
+  // a gread never delivers more than the file holds; bound before rounding up
+  // and divide instead of multiplying, so that no size wraps around
+  const uint64_t per_block = a->read_len < size ? a->read_len : size;
+  if (per_block > kStaticScratchBytes) return -ENOSPC;
+  const uint64_t buf_stride = (per_block + 255) / 256 * 256;
+  if (buf_stride && a->blocks > kStaticScratchBytes / buf_stride) return -ENOSPC;  // beyond the static array
   if (nstrides == 0) return 0;
   if (!d_count || !d_sum || !d_hash) return -EINVAL;
   if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return -ENODEV;
   if ((ctx->cfg.mode == GFS_MODE_PAPER || ctx->cfg.replacement == GFS_REPL_TB_LRA) &&
       ctx->dev.paper_streams < a->blocks)
-    return -ENOTSUP;  // would allocate
+    return -ENOTSUP;  // the per-block state would have to be allocated
   void* scratch = nullptr;
   int rc = static_scratch(ctx->cfg.device, &scratch);
   if (rc) return rc;
   gfs::DevHandle g = ctx->dev;
-  const uint64_t pages_per_read = (a->read_len + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
-  g.reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
-                                      : (uint32_t)((uint64_t)a->blocks * pages_per_read + 1 > 0xffffffffull
-                                                       ? 0xffffffffull
-                                                       : (uint64_t)a->blocks * pages_per_read + 1);
+  const uint64_t pages_per_read = (a->read_len >> ctx->dev.page_shift) + ((a->read_len & (ctx->cfg.page_size - 1)) != 0);
+  g.reserve = ctx->cfg.reserve_frames
+                  ? ctx->cfg.reserve_frames
+                  : (uint32_t)(pages_per_read >= 0xffffffffull / a->blocks ? 0xffffffffull
+                                                                             : (uint64_t)a->blocks * pages_per_read + 1);
   cudaStream_t s = (cudaStream_t)stream;
   if (a->serialize) {
     int maxb = 0;

@@ -290,6 +290,81 @@ def test_mapped_file_is_mapped_and_exact(torch_cuda, gfs, datadir):
         ctx.close(fid)
 
 
+def test_mapped_transfer_skips_files_not_in_the_host_page_cache(torch_cuda, gfs, datadir):
+    """A file whose pages are not all resident is not mapped (its pages would be read from
+    storage inside gfs_open); its requests are served by pread into staging instead.  A
+    sparse tmpfs file has pages that were never written, so it is not fully resident."""
+    if not datadir.startswith("/dev/shm"):
+        pytest.skip("no tmpfs")
+    path = os.path.join(datadir, "sparse.bin")
+    size = 8 * MiB + 5
+    with open(path, "wb") as f:
+        f.write(b"\x5a" * 4096)
+        f.truncate(size)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=256 * KiB, xfer=2, max_rpc_pages=16) as ctx:
+        fid = ctx.open(path)
+        assert ctx.fstat(fid).mapped == 0
+        out = ctx.scan(fid, MiB, blocks=8)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, MiB, *out)
+        assert ctx.stats()["host_preads"] > 0
+    full = _file(datadir, 8, 4 * MiB)
+    with gfs.Context(cache_bytes=16 * MiB, page_size=256 * KiB, max_rpc_pages=16) as ctx:  # the default transfer
+        assert ctx.cfg.xfer == gfs.XFER_MAPPED
+        assert ctx.fstat(ctx.open(full)).mapped == 1
+
+
+def _golden(name):
+    params, rows = {}, []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        parts = line.split()
+        if not parts or parts[0].startswith("#"):
+            continue
+        if parts[0] == "params":
+            params.update(kv.split("=") for kv in parts[1:])
+        else:
+            rows.append(parts)
+    return params, rows
+
+
+@pytest.mark.parametrize("xfer", XFERS)
+def test_golden_demand_run_awaited_page_only_on_gpu(torch_cuda, gfs, datadir, xfer):
+    """The hand-derived trace of tests/golden/policy_demand_run_awaited_only.txt replayed by
+    one threadblock (greads one at a time): a later page of a demand run ends the request
+    instead of evicting an unconsumed page; the logs equal the derivation."""
+    torch = torch_cuda
+    params, rows = _golden("policy_demand_run_awaited_only.txt")
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(datadir, int(params["seed"]), npg * page)
+    greads = [(int(r[2]), int(r[3])) for r in rows if r[0] == "gread"]
+    kinds = {"DEMAND": 0, "SYNC_RA": 1, "ASYNC_RA": 2}
+    with gfs.Context(cache_bytes=int(params["frames"]) * page, page_size=page, mode=0,
+                     ra_cap_pages=int(params["ra_cap"]), async_ra=int(params["async_ra"]),
+                     reserve_frames=int(params["reserve"]), trace_capacity=256, max_rpc_pages=16, xfer=xfer) as ctx:
+        fid = ctx.open(path)
+        d_off = torch.tensor([o for o, _ in greads], dtype=torch.int64, device="cuda")
+        d_len = torch.tensor([n for _, n in greads], dtype=torch.int64, device="cuda")
+        dst, pos = [], 0
+        for _, n in greads:
+            dst.append(pos)
+            pos += (n + 255) // 256 * 256
+        d_dst = torch.tensor(dst, dtype=torch.int64, device="cuda")
+        buf = torch.zeros(pos, dtype=torch.uint8, device="cuda")
+        ret = torch.zeros(len(greads), dtype=torch.int64, device="cuda")
+        ctx.read_many(fid, d_off, d_len, d_dst, buf, ret, blocks=1, threads=256)
+        torch.cuda.synchronize()
+        rpc, ev, nr, ne = ctx.trace()
+        st = ctx.stats()
+    ref = np.fromfile(path, dtype=np.uint8)
+    got = buf.cpu().numpy()
+    for (o, n), d in zip(greads, dst):
+        assert np.array_equal(got[d:d + n], ref[o:o + n])
+    assert ret.cpu().tolist() == [n for _, n in greads]
+    assert rpc == [(0, int(r[1]), int(r[2]), kinds[r[3]]) for r in rows if r[0] == "rpc"]
+    assert ev == [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert st["unconsumed_evictions"] == int([r for r in rows if r[0] == "unconsumed_evictions"][0][1])
+
+
 @pytest.mark.parametrize("xfer", [1, 2])
 def test_scan_graph_steady_loop_exact(torch_cuda, gfs, datadir, xfer):
     path = _file(datadir, 1, 64 * MiB)

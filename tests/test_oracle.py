@@ -276,6 +276,29 @@ def test_max_rpc_pages_caps_requests(tmp_path):
     sim.close_all()
 
 
+# ---------------------------------------------------------------- plain definition on many cores
+def test_pool_scan_equals_the_single_process_scan(tmp_path):
+    from oracle import pool
+    size = 5 * P * 7 + 333
+    path = _file(tmp_path, "pl", 31, size)
+    want = plain.scan_plain(path, 3 * P + 5, 2 * P)
+    got = pool.scan_plain_parallel(path, 3 * P + 5, 2 * P, procs=3, chunk_bytes=4 * P)
+    assert got == want
+    assert pool.scan_plain_parallel(path, 3 * P + 5, 2 * P, procs=1, chunk_bytes=4 * P) == want
+
+
+def test_pool_range_checksums_brute_force(tmp_path):
+    from oracle import pool
+    size = 9 * P + 7
+    path = _file(tmp_path, "pr", 32, size)
+    ref = inputs.xorshift64_bytes(32, size)
+    for off, ln in ((0, size), (5, 3 * P), (P - 1, 10 * P), (size - 3, 100), (size, 10)):
+        data = ref[off:off + ln]
+        s = sum(data) % (1 << 64)
+        h = sum(b * (off + i + 1) for i, b in enumerate(data)) % (1 << 64)
+        assert pool.range_checksums(path, off, ln, procs=2, piece=P + 3) == (len(data), s, h)
+
+
 # ---------------------------------------------------------------- policy: hand-derived traces
 def _kind(name):
     return {"DEMAND": policy.DEMAND, "SYNC_RA": policy.SYNC_RA, "ASYNC_RA": policy.ASYNC_RA}[name]
@@ -311,6 +334,30 @@ def test_golden_ondemand_fallback(tmp_path):
             s, off, ln = int(r[1]), int(r[2]), int(r[3])
             n, data = sim.gread(s, 0, off, ln)
             assert data == ref[off:off + ln]
+    want_rpc = [(0, int(r[1]), int(r[2]), _kind(r[3])) for r in rows if r[0] == "rpc"]
+    want_ev = [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert sim.rpc_log == want_rpc
+    assert sim.evict_log == want_ev
+    unc = int([r for r in rows if r[0] == "unconsumed_evictions"][0][1])
+    assert sim.stats.unconsumed_evictions == unc
+    sim.close_all()
+
+
+def test_golden_demand_run_awaited_page_only(tmp_path):
+    """Only the page a gread waits for may evict an unconsumed frame; a later page of
+    its demand run ends the request (tests/golden/policy_demand_run_awaited_only.txt)."""
+    params, rows = _parse("policy_demand_run_awaited_only.txt")
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(tmp_path, "g3", int(params["seed"]), npg * page)
+    sim = policy.PageCacheSim(page, int(params["frames"]), "readahead", ra_cap=int(params["ra_cap"]),
+                              reserve=int(params["reserve"]), async_ra=params["async_ra"] == "1")
+    sim.open(0, path)
+    ref = inputs.xorshift64_bytes(int(params["seed"]), npg * page)
+    for r in rows:
+        if r[0] == "gread":
+            s, off, ln = int(r[1]), int(r[2]), int(r[3])
+            n, data = sim.gread(s, 0, off, ln)
+            assert n == ln and data == ref[off:off + ln]
     want_rpc = [(0, int(r[1]), int(r[2]), _kind(r[3])) for r in rows if r[0] == "rpc"]
     want_ev = [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
     assert sim.rpc_log == want_rpc
@@ -472,6 +519,9 @@ def test_histogram_brute_force(tmp_path):
     assert all(int(counts[k]) == c.get(k, 0) for k in range(1 << 10))
     counts, out = apps.histogram(path, 4)       # values >= 4 are counted as outside
     assert out == sum(v for k, v in c.items() if k >= 4)
+    counts, out = apps.histogram(path, 4, piece_values=333)  # read in pieces: same counts
+    assert out == sum(v for k, v in c.items() if k >= 4)
+    assert all(int(counts[k]) == c.get(k, 0) for k in range(4))
 
 
 # ---------------------------------------------------------------- paper mode (Sections 4.1, 5.1)
