@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define GFS_ABI_VERSION 2
+#define GFS_ABI_VERSION 3
 
 /* Cache policy modes. */
 #define GFS_MODE_READAHEAD 0 /* Section 4.1 prefetcher + Section 2.3 window growth */
@@ -118,7 +118,12 @@ typedef struct gfs_config {
   uint32_t latency_capacity; /* greads whose latency (globaltimer ns, entry to exit) is kept; 0 = off */
   uint32_t replacement;    /* GFS_REPL_* */
   uint32_t queue;          /* GFS_QUEUE_* */
-  uint32_t reserved[4];
+  uint32_t host_merge_pages; /* GFS_QUEUE_SHARED: a host thread that takes a read also takes the next
+                              * requests already waiting in the ring that continue the same file range,
+                              * up to this many pages in all, and serves them with one read into staging
+                              * (Section 4.1's several pages from one pread, across threadblocks).
+                              * 0 = one staging buffer's worth; 1 = one request at a time */
+  uint32_t reserved[3];
 } gfs_config;
 
 typedef struct gfs_stat {
@@ -142,7 +147,8 @@ typedef struct gfs_stats {
   uint64_t host_ns_idle;      /* time waiting for a request */
   uint64_t buffer_hits;       /* GFS_MODE_PAPER: misses served from the private buffer */
   uint64_t host_controls;     /* opens and closes requested by the device (gopen, gclose) */
-  uint64_t reserved[3];
+  uint64_t host_merged;       /* requests a host thread served together with the request before them */
+  uint64_t reserved[2];
 } gfs_stats;
 
 /* Per host I/O thread counters since the last gfs_reset_cache (Section 3.2: the
@@ -340,15 +346,15 @@ int gfs_scan_graph(gfs_ctx* ctx, int fid, const gfs_scan_args* args, uint32_t re
 int gfs_scan_path(gfs_ctx* ctx, const char* path, const gfs_scan_args* args, int64_t* d_count,
                   uint64_t* d_sum, uint64_t* d_hash, void* stream);
 
-/* Copy the context's device handle (the plain-data struct every kernel that
- * calls the device API receives by value: gfs::DevHandle of
- * csrc/gfs_internal.h; device functions gread, gopen, gclose, gfstat, gfadvise
- * in csrc/gfs_device.cuh) into `out`, which holds `cap` bytes.  `blocks` and
- * `read_len` size the readahead reserve (blocks * ceil(read_len / page) + 1
- * frames kept free for demand misses) unless gfs_config.reserve_frames is set.
- * Returns the handle's size in bytes; -ENOSPC (nothing copied) when cap is
- * smaller.  The handle stays valid until gfs_shutdown; a later gfs_open does
- * not change it. */
+/* Copy the context's device handle (the plain-data gfs_dev of
+ * include/gfs_device.h that every kernel calling the device API -- gopen,
+ * gread, gclose, gfstat, gfadvise -- receives by value) into `out`, which holds
+ * `cap` bytes (GFS_DEV_HANDLE_BYTES, i.e. sizeof(gfs_dev), always suffices).
+ * `blocks` and `read_len` size the readahead reserve (blocks * ceil(read_len /
+ * page) + 1 frames kept free for demand misses) unless
+ * gfs_config.reserve_frames is set.  Returns the number of bytes written;
+ * -ENOSPC (nothing copied) when cap is smaller.  The handle stays valid until
+ * gfs_shutdown; a later gfs_open does not change it. */
 int gfs_device_handle(gfs_ctx* ctx, uint32_t blocks, uint64_t read_len, void* out, uint64_t cap);
 
 /* n independent greads: request i reads [d_off[i], d_off[i]+d_len[i]) into
@@ -444,13 +450,16 @@ int gfs_probe_pull(uint64_t bytes, int reps, double* gbps);
  * thread plays the device client (same slot protocol), the service preads the
  * file into host frames; returns 0 when every page matches pread.  queue:
  * GFS_QUEUE_*; with GFS_QUEUE_STATIC request i comes from client block
- * i mod client_blocks and uses that block's slot.  *h_served = requests the
- * service handed to its sinks; h_thread_requests (threads entries, or NULL)
- * gets each host thread's request count. */
+ * i mod client_blocks and uses that block's slot.  Every other request of a
+ * batch continues the file range of the one before it; merge_pages is the
+ * service's host_merge_pages (<= 1: no merging).  *h_served = requests the
+ * service handed to its sinks; *h_merged (or NULL) = requests it served merged
+ * with the one before; h_thread_requests (threads entries, or NULL) gets each
+ * host thread's request count. */
 int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests,
                       uint32_t max_pages, uint32_t threads, uint32_t slots, uint32_t queue,
-                      uint32_t client_blocks, uint64_t seed, uint64_t* h_served,
-                      uint64_t* h_thread_requests);
+                      uint32_t client_blocks, uint64_t seed, uint32_t merge_pages, uint64_t* h_served,
+                      uint64_t* h_thread_requests, uint64_t* h_merged);
 
 /* Library ABI version (GFS_ABI_VERSION). */
 int gfs_abi_version(void);

@@ -1,9 +1,12 @@
 """Build the native library (libgfs.so) in-tree for sm_103a.
 
-nvcc compiles the CUDA translation unit for `-gencode arch=compute_103a,code=sm_103a`
+nvcc compiles the CUDA translation units for `-gencode arch=compute_103a,code=sm_103a`
 and the host translation units as C++17; the objects are linked into
-paper_2109_05366_gb300/libgfs.so (static cudart).  Translation units compile in
-parallel; nothing is rebuilt when no source changed.
+paper_2109_05366_gb300/libgfs.so (static cudart).  The device-side file API of
+include/gfs_device.h is compiled as relocatable device code into
+paper_2109_05366_gb300/libgfs_device.a, which user kernels link with
+`nvcc -rdc=true`.  Translation units compile in parallel; nothing is rebuilt when
+no source changed.
 """
 from __future__ import annotations
 
@@ -17,9 +20,11 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgfs.so")
+DEVLIB = os.path.join(PKG, "libgfs_device.a")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gfs_kernels.cu", "gfs_serve.cu", "gfs_apps.cu", "gfs_host.cpp", "gfs_service.cpp"]
+DEVAPI_SOURCE = "gfs_devapi.cu"  # relocatable device code: libgfs_device.a
 HEADERS = ["gfs_internal.h", "gfs_device.cuh", "gfs_host.h", "gfs_service.h", "gfs_serve.h"]
 
 
@@ -32,11 +37,12 @@ def _nvcc() -> str:
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for name in SOURCES + HEADERS:
+    for name in SOURCES + [DEVAPI_SOURCE] + HEADERS:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
-    with open(os.path.join(ROOT, "include", "gfs.h"), "rb") as f:
-        h.update(f.read())
+    for name in ("gfs.h", "gfs_device.h"):
+        with open(os.path.join(ROOT, "include", name), "rb") as f:
+            h.update(f.read())
     h.update(" ".join(ARCH).encode())
     return h.hexdigest()
 
@@ -70,7 +76,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libgfs.so unless it is up to date; returns its path."""
     digest = _digest()
     stamp = LIB + ".stamp"
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(LIB) and os.path.exists(DEVLIB) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == digest:
                 return LIB
@@ -87,6 +93,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    devobj = os.path.join(BUILD_DIR, "gfs_devapi.o")
+    cmd = [nvcc] + ARCH + ["-lineinfo", "-O3", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC", "-c",
+                           os.path.join(CSRC, DEVAPI_SOURCE), "-o", devobj]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    procs.append((DEVAPI_SOURCE, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     errors = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -99,6 +111,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".%d.tmp" % os.getpid()
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
     os.replace(tmp, LIB)
+    tmp = DEVLIB + ".%d.tmp.a" % os.getpid()
+    subprocess.check_call([nvcc] + ARCH + ["-lib", "-o", tmp, devobj])
+    os.replace(tmp, DEVLIB)
     with open(stamp, "w") as f:
         f.write(digest + "\n")
     return LIB

@@ -787,6 +787,10 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   sc.skipped = ctx->h_skipped;
   sc.queue = c.queue;
   sc.io_trace_cap = c.trace_capacity;
+  // merged host reads: by default one staging buffer's worth of pages
+  sc.merge_pages = c.host_merge_pages ? c.host_merge_pages
+                                      : (c.xfer != GFS_XFER_DMA ? (uint32_t)(chunk_bytes / c.page_size)
+                                                                : sc.staging_pages);
   if (c.xfer != GFS_XFER_DMA) {
     sc.pull_arena = ctx->h_staging;
     sc.pull_done = ctx->h_done;
@@ -1018,6 +1022,7 @@ int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
   o->host_ns_idle = ctx->io->stats.ns_idle.load();
   o->buffer_hits = st[ST_BUFHITS];
   o->host_controls = ctx->io->stats.controls.load();
+  o->host_merged = ctx->io->stats.merged.load();
   return 0;
 }
 
@@ -1564,7 +1569,7 @@ int gfs_replay_io(const char* path, const gfs_io_rec* recs, uint64_t n, uint32_t
 // ---------------------------------------------------------------- CPU self-test
 int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uint32_t requests, uint32_t max_pages,
                       uint32_t threads, uint32_t slots, uint32_t queue, uint32_t client_blocks, uint64_t seed,
-                      uint64_t* h_served, uint64_t* h_thread_requests) {
+                      uint32_t merge_pages, uint64_t* h_served, uint64_t* h_thread_requests, uint64_t* h_merged) {
   if (!path || !is_pow2(page_size) || page_size < 16 || frames == 0 || max_pages == 0 ||
       max_pages > MAX_RPC_PAGES || threads == 0 || threads > 64 || slots < 2 || seed == 0 ||
       queue > GFS_QUEUE_STATIC || (queue == GFS_QUEUE_STATIC && client_blocks == 0))
@@ -1592,6 +1597,7 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
   sc.threads = threads;
   sc.n_frames = frames;
   sc.queue = queue;
+  sc.merge_pages = merge_pages;
   const size_t stg = (size_t)sc.staging_pages * page_size;
   IoService io(
       sc, [&](int) -> Sink* { return new HostSink(fr.data(), state.data(), shift, stg); },
@@ -1628,6 +1634,8 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
     while (batch.size() < batch_max && done + batch.size() < requests) {
       Pending p;
       p.page_lo = rnd() % (npages + 1);  // one past the end exercises EOF
+      // every other request continues the one before it (host threads may merge them)
+      if (!batch.empty() && (rnd() & 1)) p.page_lo = batch.back().page_lo + batch.back().n;
       p.n = 1 + (uint32_t)(rnd() % max_pages);
       p.frame0 = next_frame;
       if (next_frame + p.n > frames) break;
@@ -1689,6 +1697,7 @@ int gfs_selftest_ring(const char* path, uint32_t page_size, uint32_t frames, uin
   io.stop();
   close(fd);
   if (h_served) *h_served = io.stats.requests.load();
+  if (h_merged) *h_merged = io.stats.merged.load();
   if (h_thread_requests)
     for (uint32_t i = 0; i < threads; ++i) h_thread_requests[i] = io.thread_counters(i).requests.load();
   return bad ? -(int)(1000 + bad) : 0;

@@ -154,7 +154,8 @@ void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages
   const uint64_t off0 = page_lo << cfg_.page_shift;
   if (have && off0 < fv.size)
     record_io(w.idx, fid, off0, std::min<uint64_t>((uint64_t)npages * P, fv.size - off0), mono_ns());
-  bool full[MAX_RPC_PAGES];
+  if (w.full.size() < cfg_.staging_pages) w.full.resize(cfg_.staging_pages);
+  uint8_t* full = w.full.data();
   for (uint32_t c0 = 0; c0 < npages; c0 += cfg_.staging_pages) {
     const uint32_t cn = std::min(cfg_.staging_pages, npages - c0);
     const uint64_t coff = off0 + (uint64_t)c0 * P;
@@ -179,7 +180,7 @@ void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages
     for (uint32_t i = 0; i < cn; ++i) {
       const uint64_t base = coff + (uint64_t)i * P;
       const uint64_t expect = (have && base < fv.size) ? std::min<uint64_t>(P, fv.size - base) : 0;
-      full[i] = expect > 0 && (uint64_t)got >= (uint64_t)i * P + expect;
+      full[i] = expect > 0 && (uint64_t)got >= (uint64_t)i * P + expect ? 1 : 0;
     }
     for (uint32_t i = 0; i < cn;) {
       if (!full[i]) {
@@ -192,7 +193,7 @@ void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages
       const uint64_t bytes = (uint64_t)(j - 1 - i) * P + std::min<uint64_t>(P, fv.size - last_base);
       if (sink->copy(frames[c0 + i], buf + (size_t)i * P, (size_t)bytes) != 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);
-        for (uint32_t q = i; q < j; ++q) full[q] = false;
+        for (uint32_t q = i; q < j; ++q) full[q] = 0;
       } else {
         stats.copies.fetch_add(1, std::memory_order_relaxed);
       }
@@ -204,47 +205,61 @@ void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages
   }
 }
 
-void IoService::serve_pull(Worker& w, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo,
-                           uint32_t npages) {
+void IoService::serve_pull(Worker& w, uint32_t fid, const Req* group, int ng) {
   const int idx = w.idx;
   uint32_t& cur = w.pull_cur;
   FileView fv{-1, 0, 0};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
-  const uint64_t off0 = page_lo << cfg_.page_shift;
-  if (have && off0 < fv.size)
-    record_io(idx, fid, off0, std::min<uint64_t>((uint64_t)npages * P, fv.size - off0), mono_ns());
-  const uint32_t cpages = (uint32_t)(cfg_.chunk_bytes >> cfg_.page_shift);
-  long long total = have ? 0 : -EBADF;
+  const uint64_t off0 = group[0].page_lo << cfg_.page_shift;
+  uint64_t npages = 0;
+  for (int k = 0; k < ng; ++k) npages += group[k].npages;
+  if (have && off0 < fv.size) record_io(idx, fid, off0, std::min<uint64_t>(npages * P, fv.size - off0), mono_ns());
+  auto publish_done = [&](const Req& r, long long result) {
+    PullDone* d = cfg_.pull_done + r.slot;
+    __atomic_store_n(&d->result, result, __ATOMIC_RELAXED);
+    __atomic_store_n(&d->done, r.ticket + 1, __ATOMIC_RELEASE);
+  };
   if (have && fv.dev_map) {  // mapped file: the pages are already in host memory the GPU can read
-    // injected host read errors apply here too (the request fails as a whole)
-    const uint64_t k = pread_count_.fetch_add(1, std::memory_order_relaxed);
-    const uint32_t eio = eio_every_.load(std::memory_order_relaxed);
-    const bool fail = eio && k % eio == eio - 1;
-    if (fail) {
-      stats.errors.fetch_add(1, std::memory_order_relaxed);
-      total = -EIO;
+    for (int k = 0; k < ng; ++k) {
+      const Req& r = group[k];
+      // injected host read errors apply here too (the request fails as a whole)
+      const uint64_t c = pread_count_.fetch_add(1, std::memory_order_relaxed);
+      const uint32_t eio = eio_every_.load(std::memory_order_relaxed);
+      const bool fail = eio && c % eio == eio - 1;
+      long long total = 0;
+      if (fail) {
+        stats.errors.fetch_add(1, std::memory_order_relaxed);
+        total = -EIO;
+      }
+      const uint64_t roff = r.page_lo << cfg_.page_shift;
+      for (uint32_t i = 0; i < r.npages; ++i) {
+        const uint64_t base = roff + (uint64_t)i * P;
+        PullPage* pp = cfg_.pull_pages + (size_t)r.slot * cfg_.max_pages + i;
+        pp->src = fv.dev_map + base;
+        pp->buf = BUF_MAPPED;
+        pp->ok = (!fail && base < fv.size) ? 1u : 0u;
+        if (!fail && base < fv.size) total += (long long)std::min<uint64_t>(P, fv.size - base);
+        __atomic_store_n(&pp->tag, r.ticket + 1, __ATOMIC_RELEASE);
+      }
+      if (total > 0) {
+        stats.bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
+        tstats_[idx].bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
+      }
+      publish_done(r, total);
     }
-    for (uint32_t i = 0; i < npages; ++i) {
-      const uint64_t base = off0 + (uint64_t)i * P;
-      PullPage* pp = cfg_.pull_pages + (size_t)slot * cfg_.max_pages + i;
-      pp->src = fv.dev_map + base;
-      pp->buf = BUF_MAPPED;
-      pp->ok = (!fail && base < fv.size) ? 1u : 0u;
-      if (!fail && base < fv.size) total += (long long)std::min<uint64_t>(P, fv.size - base);
-      __atomic_store_n(&pp->tag, ticket + 1, __ATOMIC_RELEASE);
-    }
-    if (total > 0) {
-      stats.bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
-      tstats_[idx].bytes.fetch_add((uint64_t)total, std::memory_order_relaxed);
-    }
-    PullDone* d = cfg_.pull_done + slot;
-    __atomic_store_n(&d->result, total, __ATOMIC_RELAXED);
-    __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);
     return;
   }
-  for (uint32_t c0 = 0; c0 < npages; c0 += cpages) {
-    const uint32_t cn = std::min(cpages, npages - c0);
+  // The group's pages in file order, one pread per staging buffer: request k's
+  // page i goes to its own slot's descriptor, and request k's completion record is
+  // published after its last page.
+  const uint32_t cpages = (uint32_t)(cfg_.chunk_bytes >> cfg_.page_shift);
+  long long result[kMaxGroup];
+  for (int k = 0; k < ng; ++k) result[k] = have ? 0 : -EBADF;
+  int k = 0;
+  uint32_t i = 0;
+  for (uint64_t g0 = 0; g0 < npages; g0 += cpages) {
+    const uint32_t cn = (uint32_t)std::min<uint64_t>(cpages, npages - g0);
     const uint32_t id = (uint32_t)idx * cfg_.bufs_per_thread + cur;
     cur = (cur + 1) % cfg_.bufs_per_thread;
     uint8_t* buf = cfg_.pull_arena + (size_t)id * cfg_.chunk_bytes;
@@ -260,37 +275,43 @@ void IoService::serve_pull(Worker& w, uint32_t slot, uint64_t ticket, uint32_t f
       }
       stats.ns_wait_buf.fetch_add(mono_ns() - w0, std::memory_order_relaxed);
     }
-    const uint64_t coff = off0 + (uint64_t)c0 * P;
+    const uint64_t coff = off0 + g0 * P;
     size_t want = 0;
     if (have && coff < fv.size) want = (size_t)std::min<uint64_t>((uint64_t)cn * P, fv.size - coff);
     ssize_t got = 0;
+    long long err = 0;
     if (want) {
       got = do_pread(idx, fv.fd, buf, want, coff);
       stats.preads.fetch_add(1, std::memory_order_relaxed);
       if (got < 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);
-        if (total >= 0) total = got;
+        err = got;
         got = 0;
       } else {
         stats.bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
         tstats_[idx].bytes.fetch_add((uint64_t)got, std::memory_order_relaxed);
-        if (total >= 0) total += got;
       }
     }
     __atomic_store_n(&cfg_.pull_bcount[id], cn, __ATOMIC_RELAXED);  // published by the page tags below
-    for (uint32_t i = 0; i < cn; ++i) {
-      const uint64_t base = coff + (uint64_t)i * P;
+    for (uint32_t j = 0; j < cn; ++j) {
+      const Req& r = group[k];
+      const uint64_t base = coff + (uint64_t)j * P;
       const uint64_t expect = (have && base < fv.size) ? std::min<uint64_t>(P, fv.size - base) : 0;
-      PullPage* pp = cfg_.pull_pages + (size_t)slot * cfg_.max_pages + c0 + i;
-      pp->src = (uint64_t)id * cfg_.chunk_bytes + (uint64_t)i * P;
+      const bool ok = expect > 0 && (uint64_t)got >= (uint64_t)j * P + expect;
+      PullPage* pp = cfg_.pull_pages + (size_t)r.slot * cfg_.max_pages + i;
+      pp->src = (uint64_t)id * cfg_.chunk_bytes + (uint64_t)j * P;
       pp->buf = id;
-      pp->ok = (expect > 0 && (uint64_t)got >= (uint64_t)i * P + expect) ? 1u : 0u;
-      __atomic_store_n(&pp->tag, ticket + 1, __ATOMIC_RELEASE);  // the GPU may copy this page now
+      pp->ok = ok ? 1u : 0u;
+      if (result[k] >= 0) result[k] = err ? err : result[k] + (long long)(ok ? expect : 0);
+      __atomic_store_n(&pp->tag, r.ticket + 1, __ATOMIC_RELEASE);  // the GPU may copy this page now
+      if (++i == r.npages) {
+        publish_done(r, result[k]);
+        ++k;
+        i = 0;
+      }
     }
   }
-  PullDone* d = cfg_.pull_done + slot;
-  __atomic_store_n(&d->result, total, __ATOMIC_RELAXED);
-  __atomic_store_n(&d->done, ticket + 1, __ATOMIC_RELEASE);
+  for (; k < ng; ++k) publish_done(group[k], result[k]);  // requests with no page (none in practice)
 }
 
 // Answer a control request from the device in the slot's payload.  The slot
@@ -315,7 +336,7 @@ void IoService::control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid) {
 }
 
 void IoService::run(int idx) {
-  Worker w{idx, sinks_[idx], 0, 0u};
+  Worker w{idx, sinks_[idx], 0, 0u, {}, {}};
   w.sink->thread_init();
   prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);  // short sleeps while polling the ring
   if (cfg_.queue == GFS_QUEUE_STATIC) run_static(w);
@@ -400,15 +421,42 @@ void IoService::run_static(Worker& w) {
   }
 }
 
+int IoService::gather(Worker& w, uint32_t fid, Req* group, uint32_t max_pages_each) {
+  if (cfg_.queue != GFS_QUEUE_SHARED || cfg_.merge_pages <= 1) return 1;
+  int ng = 1;
+  uint64_t total = group[0].npages;
+  uint64_t next = group[0].page_lo + group[0].npages;
+  while (ng < kMaxGroup && total < cfg_.merge_pages) {
+    const uint64_t h2 = group[ng - 1].ticket + 1;
+    RingSlot* s2 = (RingSlot*)(cfg_.ring + (size_t)(h2 % cfg_.slots) * cfg_.slot_stride);
+    if (__atomic_load_n(&s2->seq, __ATOMIC_ACQUIRE) != h2 + 1) break;  // not published (yet)
+    // Read before claiming: while no thread has taken ticket h2 the slot keeps its
+    // request; if one has, the claim below fails and what was read is dropped.
+    const volatile RingSlot* v2 = s2;
+    const uint32_t op = v2->op, f2 = v2->fid, n2 = v2->npages;
+    const uint64_t lo2 = v2->page_lo;
+    if (op != OP_READ || f2 != fid || lo2 != next || n2 == 0 || n2 > max_pages_each ||
+        total + n2 > cfg_.merge_pages)
+      break;
+    uint64_t expect = h2;
+    if (!head_.compare_exchange_strong(expect, h2 + 1, std::memory_order_acq_rel)) break;  // taken meanwhile
+    took_request(w.idx);
+    stats.requests.fetch_add(1, std::memory_order_relaxed);
+    stats.merged.fetch_add(1, std::memory_order_relaxed);
+    group[ng++] = Req{h2, (uint32_t)(h2 % cfg_.slots), n2, lo2};
+    total += n2;
+    next += n2;
+  }
+  return ng;
+}
+
 void IoService::handle(Worker& w, uint64_t h, RingSlot* s) {
-  uint32_t frames[MAX_RPC_PAGES];
   took_request(w.idx);
   const volatile RingSlot* vs = s;
   const uint32_t fid = vs->fid;
   const uint32_t npages = vs->npages;
   const uint64_t page_lo = vs->page_lo;
   const uint32_t op = vs->op;
-  const uint32_t n = std::min<uint32_t>(npages, MAX_RPC_PAGES);
   if (op == OP_OPEN || op == OP_CLOSE || op == OP_ADVISE) {
     control(s, (uint32_t)(h % cfg_.slots), op, fid);
     stats.controls.fetch_add(1, std::memory_order_relaxed);
@@ -416,21 +464,36 @@ void IoService::handle(Worker& w, uint64_t h, RingSlot* s) {
     return;
   }
   stats.requests.fetch_add(1, std::memory_order_relaxed);
-  if (cfg_.pull_arena) {  // the GPU frees the slot once it has copied the pages
-    serve_pull(w, (uint32_t)(h % cfg_.slots), h, fid, page_lo, std::min<uint32_t>(npages, cfg_.max_pages));
-    served_.fetch_add(1, std::memory_order_release);
+  const uint32_t max_each = cfg_.pull_arena ? cfg_.max_pages : MAX_RPC_PAGES;
+  Req group[kMaxGroup];
+  group[0] = Req{h, (uint32_t)(h % cfg_.slots), std::min(npages, max_each), page_lo};
+  const int ng = (npages >= 1 && npages <= max_each) ? gather(w, fid, group, max_each) : 1;
+  if (cfg_.pull_arena) {  // the GPU frees the slots once it has copied the pages
+    serve_pull(w, fid, group, ng);
+    served_.fetch_add((uint64_t)ng, std::memory_order_release);
     return;
   }
-  for (uint32_t i = 0; i < n; ++i) frames[i] = vs->frames[i];
-  __atomic_store_n(&s->seq, h + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
+  // copy-engine transfer: take the frame lists out and free the slots for their next lap
+  uint64_t total = 0;
+  for (int k = 0; k < ng; ++k) total += group[k].npages;
+  if (w.frames.size() < total) w.frames.resize(total);
+  uint32_t* frames = w.frames.data();
   bool bad = npages == 0 || npages > MAX_RPC_PAGES;
-  for (uint32_t i = 0; i < n && !bad; ++i) bad = frames[i] >= cfg_.n_frames;
+  uint64_t at = 0;
+  for (int k = 0; k < ng; ++k) {
+    RingSlot* sk = (RingSlot*)(cfg_.ring + (size_t)group[k].slot * cfg_.slot_stride);
+    const volatile RingSlot* vk = sk;
+    for (uint32_t i = 0; i < group[k].npages; ++i) frames[at + i] = vk->frames[i];
+    __atomic_store_n(&sk->seq, group[k].ticket + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
+    for (uint32_t i = 0; i < group[k].npages && !bad; ++i) bad = frames[at + i] >= cfg_.n_frames;
+    at += group[k].npages;
+  }
   if (bad) {
     stats.errors.fetch_add(1, std::memory_order_relaxed);
   } else {
-    serve(w, fid, page_lo, n, frames);
+    serve(w, fid, page_lo, (uint32_t)total, frames);
   }
-  served_.fetch_add(1, std::memory_order_release);
+  served_.fetch_add((uint64_t)ng, std::memory_order_release);
 }
 
 }  // namespace gfs

@@ -66,6 +66,10 @@ struct ServiceConfig {
   // device opens: per-slot path buffers (host view), GFS_PATH_MAX bytes each
   const char* paths = nullptr;
   uint32_t queue = GFS_QUEUE_SHARED;  // GFS_QUEUE_*: how a thread finds its requests
+  // GFS_QUEUE_SHARED: a thread that takes a read also takes the next published,
+  // not yet taken tickets that continue the same file range, up to this many
+  // pages in all, and serves them with one read (<= 1: one request at a time)
+  uint32_t merge_pages = 1;
   uint64_t io_trace_cap = 0;          // host I/O trace entries kept (0 = off)
   // at t % cancel_n: t + 1 for a ticket t its producer gave up (skipped once the slot
   // is free for it); count of skipped tickets.  Host views of mapped memory; may be null.
@@ -85,9 +89,10 @@ struct ServiceStats {
   std::atomic<uint64_t> ns_pread{0}, ns_wait_buf{0}, ns_idle{0};
   std::atomic<uint64_t> controls{0};  // device opens and closes answered
   std::atomic<uint64_t> skipped{0};   // tickets skipped because their producer gave them up
+  std::atomic<uint64_t> merged{0};    // requests served together with the request before them
   void clear() {
     requests = 0; preads = 0; bytes = 0; copies = 0; errors = 0;
-    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0; controls = 0; skipped = 0;
+    ns_pread = 0; ns_wait_buf = 0; ns_idle = 0; controls = 0; skipped = 0; merged = 0;
   }
 };
 
@@ -123,7 +128,18 @@ class IoService {
     Sink* sink;
     int cur;
     uint32_t pull_cur;
+    std::vector<uint32_t> frames;  // frame lists of a merged group (copy-engine transfer)
+    std::vector<uint8_t> full;     // per page of a staging chunk: delivered whole
   };
+  // One read request of a merged group: ticket, slot, its first page and page count.
+  // The pages of a group are contiguous in one file, in ticket order.
+  struct Req {
+    uint64_t ticket;
+    uint32_t slot;
+    uint32_t npages;
+    uint64_t page_lo;
+  };
+  static constexpr int kMaxGroup = 64;  // requests one host read serves at most
   void run(int idx);
   void run_shared(Worker& w);
   void run_static(Worker& w);
@@ -132,8 +148,11 @@ class IoService {
   // Skip ticket h if its producer gave it up and the slot is free for it.
   bool skip_cancelled(uint64_t h, RingSlot* s);
   void control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid);
+  // Take the published tickets after group[0] that continue its file range (see
+  // merge_pages); returns the group's request count.
+  int gather(Worker& w, uint32_t fid, Req* group, uint32_t max_pages_each);
   void serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
-  void serve_pull(Worker& w, uint32_t slot, uint64_t ticket, uint32_t fid, uint64_t page_lo, uint32_t npages);
+  void serve_pull(Worker& w, uint32_t fid, const Req* group, int ng);
   ssize_t do_pread(int idx, int fd, uint8_t* buf, size_t n, uint64_t off);
   void record_io(int idx, uint32_t fid, uint64_t off, uint64_t bytes, uint64_t t_ns);
   void polled_empty(int idx, uint64_t idle_ns);

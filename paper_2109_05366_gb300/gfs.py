@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
                 ("max_rpc_pages", u32), ("host_threads", u32), ("staging_bytes", u32), ("max_streams", u32),
                 ("max_files", u32), ("trace_capacity", u32), ("xfer", u32), ("debug_counts", u32),
                 ("device", i32), ("latency_capacity", u32), ("replacement", u32), ("queue", u32),
-                ("reserved", u32 * 4)]
+                ("host_merge_pages", u32), ("reserved", u32 * 3)]
 
 
 class Stat(ctypes.Structure):
@@ -45,11 +45,11 @@ STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fe
                 "ra_pages_sync", "ra_pages_async", "evictions", "unconsumed_evictions", "retries", "timeouts",
                 "eio", "enomem", "host_requests", "host_preads", "host_bytes", "host_copies", "host_errors",
                 "trace_rpc_count", "trace_evict_count", "host_ns_pread", "host_ns_wait_buf", "host_ns_idle",
-                "buffer_hits", "host_controls"]
+                "buffer_hits", "host_controls", "host_merged"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 3)]
+    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 2)]
 
 
 class ThreadStat(ctypes.Structure):
@@ -117,8 +117,8 @@ SIGNATURES = {
     "gfs_probe_h2d": (ctypes.c_int, [u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pread": (ctypes.c_int, [ctypes.c_char_p, u32, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pull": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
-    "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u32, u32, u64,
-                                         ctypes.POINTER(u64), vp]),
+    "gfs_selftest_ring": (ctypes.c_int, [ctypes.c_char_p, u32, u32, u32, u32, u32, u32, u32, u32, u64, u32,
+                                         ctypes.POINTER(u64), vp, ctypes.POINTER(u64)]),
     "gfs_rowdot": (ctypes.c_int, [vp, ctypes.c_int, u32, u32, vp, vp, u32, u64, u32, vp, vp, vp, vp]),
     "gfs_histogram": (ctypes.c_int, [vp, ctypes.c_int, u32, vp, u64, u32, vp, vp, vp]),
     "gfs_serve_start": (ctypes.c_int, [vp, ctypes.POINTER(ServeConfig), vp]),
@@ -451,14 +451,21 @@ def probe_pread(path: str, threads: int, chunk: int, reps: int = 2) -> float:
 
 def selftest_ring(path: str, page_size: int = 4096, frames: int = 256, requests: int = 500, max_pages: int = 8,
                   threads: int = 4, slots: int = 16, seed: int = 1, queue: int = QUEUE_SHARED,
-                  client_blocks: int = 0, per_thread: bool = False):
-    """Requests served (and, with per_thread, each host thread's request count)."""
-    served = u64()
+                  client_blocks: int = 0, per_thread: bool = False, merge_pages: int = 1, merged: bool = False):
+    """Requests served (and, with per_thread, each host thread's request count; with merged,
+    the number of requests served merged with the one before)."""
+    served, nmerged = u64(), u64()
     counts = np.zeros(threads, dtype=np.uint64)
     _check(load().gfs_selftest_ring(path.encode(), page_size, frames, requests, max_pages, threads, slots, queue,
-                                    client_blocks, seed, ctypes.byref(served), counts.ctypes.data),
+                                    client_blocks, seed, merge_pages, ctypes.byref(served), counts.ctypes.data,
+                                    ctypes.byref(nmerged)),
            "gfs_selftest_ring")
-    return (served.value, counts.tolist()) if per_thread else served.value
+    out = [served.value]
+    if per_thread:
+        out.append(counts.tolist())
+    if merged:
+        out.append(nmerged.value)
+    return out[0] if len(out) == 1 else tuple(out)
 
 
 def replay_io(path: str, recs, threads: int):

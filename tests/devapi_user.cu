@@ -1,5 +1,6 @@
 // A kernel written the way a user of the library writes one: it includes the
-// device runtime and calls the device API itself.  Every threadblock opens the
+// public device API (include/gfs_device.h) and nothing else of the library, and
+// links libgfs_device.a (relocatable device code).  Every threadblock opens the
 // file (gopen), optionally sets an access hint (gfadvise), checks gfstat, reads
 // its strides with gread into its own buffer, sums the bytes, and closes the
 // file (gclose).  Built by tests/test_gpu_devapi.py with nvcc.
@@ -7,7 +8,7 @@
 #include <stdint.h>
 #include <string.h>
 
-#include "gfs_device.cuh"
+#include "gfs_device.h"
 
 namespace {
 
@@ -15,18 +16,17 @@ struct UserPath {
   char s[GFS_PATH_MAX];
 };
 
-__global__ void __launch_bounds__(256) k_user(gfs::DevHandle g, const __grid_constant__ UserPath path, int advice,
-                                              unsigned long long stride, unsigned long long nstrides, uint8_t* bufs,
-                                              long long* cnt, unsigned long long* sum, long long* info) {
-  using namespace gfs;
+__global__ void __launch_bounds__(256) k_user(const __grid_constant__ gfs_dev g, const __grid_constant__ UserPath path,
+                                              int advice, unsigned long long stride, unsigned long long nstrides,
+                                              uint8_t* bufs, long long* cnt, unsigned long long* sum, long long* info) {
   uint8_t* buf = bufs + (size_t)blockIdx.x * stride;
-  const int fid = dev::gopen(g, path.s, GFS_RDONLY);
+  const int fid = gopen(&g, path.s, GFS_RDONLY);
   int arc = 0;
-  if (fid >= 0 && advice >= 0) arc = dev::gfadvise(g, fid, advice);
+  if (fid >= 0 && advice >= 0) arc = gfadvise(&g, fid, advice);
   gfs_stat st{};
-  const int src = fid >= 0 ? dev::gfstat(g, fid, &st) : fid;
+  const int src = fid >= 0 ? gfstat(&g, fid, &st) : fid;
   for (unsigned long long s = blockIdx.x; s < nstrides; s += gridDim.x) {
-    const long long r = fid >= 0 ? dev::gread(g, (int)blockIdx.x, fid, s * stride, stride, buf) : fid;
+    const long long r = fid >= 0 ? gread(&g, fid, s * stride, stride, buf) : fid;
     unsigned long long acc = 0;
     for (long long i = threadIdx.x; i < r; i += blockDim.x) acc += buf[i];
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_user(gfs::DevHandle g, const __grid_con
     }
     __syncthreads();
   }
-  const int crc = fid >= 0 ? dev::gclose(g, fid) : 0;
+  const int crc = fid >= 0 ? gclose(&g, fid) : 0;
   if (threadIdx.x == 0) {
     long long* mine = info + 8 * blockIdx.x;
     mine[0] = fid;
@@ -62,10 +62,11 @@ __global__ void __launch_bounds__(256) k_user(gfs::DevHandle g, const __grid_con
 extern "C" int user_scan(const void* handle, uint64_t handle_bytes, const char* path, int advice, uint64_t stride,
                          uint64_t nstrides, uint32_t blocks, void* bufs, void* cnt, void* sum, void* info,
                          void* stream) {
-  if (handle_bytes != sizeof(gfs::DevHandle)) return (int)cudaErrorInvalidValue;
+  if (handle_bytes == 0 || handle_bytes > sizeof(gfs_dev)) return (int)cudaErrorInvalidValue;
   if (strlen(path) >= GFS_PATH_MAX) return (int)cudaErrorInvalidValue;
-  gfs::DevHandle g;
-  memcpy(&g, handle, sizeof(g));
+  gfs_dev g;
+  memset(&g, 0, sizeof(g));
+  memcpy(&g, handle, handle_bytes);
   UserPath p;
   memset(p.s, 0, sizeof(p.s));
   strcpy(p.s, path);

@@ -1,4 +1,5 @@
-"""C-ABI library: builds, loads, exports what include/gfs.h declares; host logic without a GPU."""
+"""C-ABI library: builds, loads, exports what include/gfs.h and include/gfs_device.h
+declare; host logic without a GPU."""
 import os
 import re
 
@@ -7,7 +8,9 @@ import pytest
 import inputs
 from paper_2109_05366_gb300 import gfs
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gfs.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gfs.h")
+DEVICE_HEADER = os.path.join(ROOT, "include", "gfs_device.h")
 
 
 def _declared():
@@ -25,9 +28,58 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(gfs.SIGNATURES), "binding and header disagree"
 
 
+def _device_declared():
+    text = open(DEVICE_HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"__device__\s+[a-z ]+?\s+(g[a-z_]+)\s*\(", text)))
+
+
+def test_device_library_resolves_every_declared_device_call(tmp_path):
+    """A kernel that calls every function include/gfs_device.h declares device-links
+    against libgfs_device.a (nvlink fails on an unresolved device symbol); nothing runs."""
+    import shutil
+    import subprocess
+    from paper_2109_05366_gb300 import build
+    build.build()
+    names = _device_declared()
+    assert names == ["gclose", "gfadvise", "gfstat", "gopen", "gread", "gread_as"]
+    src = tmp_path / "probe.cu"
+    src.write_text("\n".join([
+        '#include "gfs_device.h"',
+        "__global__ void probe(const __grid_constant__ gfs_dev h, const char* p, char* buf, long long* out) {",
+        "  gfs_stat st;",
+        "  int fid = gopen(&h, p, GFS_RDONLY);",
+        "  long long a = gread(&h, fid, 0, 4096, buf);",
+        "  long long b = gread_as(&h, 3, fid, 4096, 4096, buf);",
+        "  int c = gfstat(&h, fid, &st) + gfadvise(&h, fid, GFS_ADV_RANDOM) + gclose(&h, fid);",
+        "  if (threadIdx.x == 0) out[blockIdx.x] = a + b + c + (long long)st.size;",
+        "}",
+        'extern "C" int probe_launch(const gfs_dev* h, const char* p, char* buf, long long* out) {',
+        "  probe<<<1, 128>>>(*h, p, buf, out);",
+        "  return (int)cudaGetLastError();",
+        "}"]))
+    nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    out = str(tmp_path / "probe.so")
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-rdc=true", "-shared",
+                           "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), str(src), build.DEVLIB,
+                           "-o", out])
+    assert os.path.getsize(out) > 0
+
+
+def test_device_handle_fits_the_public_handle_type(tmp_path):
+    import subprocess
+    c = tmp_path / "h.c"
+    c.write_text('#include <stdio.h>\n#include "%s"\nint main(void){printf("%%zu %%zu\\n", sizeof(gfs_dev), '
+                 '_Alignof(gfs_dev));return 0;}' % DEVICE_HEADER)
+    exe = str(tmp_path / "h")
+    subprocess.check_call(["gcc", "-std=c11", "-o", exe, str(c)])
+    size, align = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert size == 1024 and align == 8
+
+
 def test_abi_version_and_errors():
     lib = gfs.load()
-    assert lib.gfs_abi_version() == 2
+    assert lib.gfs_abi_version() == 3
     assert lib.gfs_strerror(-22) == b"invalid argument"
     assert lib.gfs_strerror(-110) == b"device wait timed out"
 
@@ -44,11 +96,11 @@ def test_struct_layouts_match_header(tmp_path):
     import ctypes
     import subprocess
     checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "replacement",
-                                          "queue", "reserved"]),
+                                          "queue", "host_merge_pages", "reserved"]),
               ("gfs_thread_stat", gfs.ThreadStat, ["requests", "first_request_ns", "bytes"]),
               ("gfs_io_rec", gfs.IoRec, ["offset", "bytes", "fid", "thread", "t_ns"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
-              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "host_controls", "reserved"]),
+              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "host_controls", "host_merged", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
               ("gfs_evict_rec", gfs.EvictRec, ["new_fid", "new_page"]),
               ("gfs_scan_args", gfs.ScanArgs, ["read_len", "fused", "reserved"])]
@@ -93,6 +145,23 @@ def test_ring_and_service_selftest(tmp_path, page, frames, requests, max_pages, 
     inputs.write_file(path, 3, size)
     served = gfs.selftest_ring(path, page, frames, requests, max_pages, threads, slots, seed=7)
     assert served == requests
+
+
+@pytest.mark.parametrize("threads,max_pages,merge", [(1, 4, 16), (2, 1, 8), (4, 8, 64), (1, 16, 4)])
+def test_merged_host_reads_deliver_every_page(tmp_path, threads, max_pages, merge):
+    """Section 4.1 has the CPU deliver several pages from one pread; here a host thread
+    also takes the requests already waiting behind its own that continue the same file
+    range and reads them all at once.  Every page still matches pread, every request is
+    served once, and with a backlog some requests are merged."""
+    path = str(tmp_path / "f.bin")
+    inputs.write_file(path, 9, (2 << 20) + 333)
+    served, merged = gfs.selftest_ring(path, 4096, 512, 3000, max_pages, threads, 64, seed=11, merge_pages=merge,
+                                       merged=True)
+    assert served == 3000
+    assert merged > 0
+    served, merged = gfs.selftest_ring(path, 4096, 512, 3000, max_pages, threads, 64, seed=11, merge_pages=1,
+                                       merged=True)
+    assert served == 3000 and merged == 0
 
 
 @pytest.mark.parametrize("threads,slots,blocks", [(4, 64, 16), (4, 64, 48), (8, 16, 40), (3, 10, 7)])
@@ -141,8 +210,9 @@ def test_ring_needs_two_slots(tmp_path):
 
 
 def test_user_kernel_builds_against_device_api(tmp_path):
-    """A user's kernel that includes the device runtime and calls gopen / gfadvise /
-    gfstat / gread / gclose compiles for sm_103a and exports its launcher."""
+    """A user's kernel that includes only include/gfs_device.h and calls gopen / gfadvise /
+    gfstat / gread / gclose compiles for sm_103a, links libgfs_device.a and exports its
+    launcher."""
     import subprocess
 
     from tests.devapi_build import build_user_kernel

@@ -9,6 +9,11 @@ finds its ticket cancelled and its slot free for it clears the cancellation and 
 the slot for the next lap.  A served request's slot is freed later by whoever copies
 its pages (the GPU in the pull and mapped transfers), modelled as a separate actor.
 
+A host thread that has served a request may also take the next ticket when its request
+is already published and no host thread has drawn it yet (`IoService::gather`: it reads
+the slot's sequence word, then claims the ticket by compare-and-swap on the shared head),
+and serve both with one host read; the model explores that step too.
+
 Every step below is one access to shared state, as in the code; a producer may run out
 of time at any wait.  For every interleaving of small scenarios the test checks that
 some schedule always finishes every thread (a host thread is never stuck behind an
@@ -20,15 +25,18 @@ import pytest
 
 
 class Ring:
-    def __init__(self, slots, cancel_n, tickets):
-        self.R, self.n, self.P = slots, cancel_n, tickets
+    def __init__(self, slots, cancel_n, tickets, merge=None):
+        # merge: None (one request at a time), "cas" (the claim is one compare-and-swap, as
+        # in the code) or "racy" (a planted mistake: the claim is a load and a later store)
+        self.R, self.n, self.P, self.merge = slots, cancel_n, tickets, merge
 
     def initial(self):
-        # seq, cancel, head (host tickets), tail (producer tickets), pending copies, served, skipped
-        return (tuple(range(self.R)), (0,) * self.n, 0, 0, frozenset(), frozenset(), frozenset())
+        # seq, cancel, head (host tickets), tail (producer tickets), pending copies, served, skipped,
+        # and whether some ticket was served twice
+        return (tuple(range(self.R)), (0,) * self.n, 0, 0, frozenset(), frozenset(), frozenset(), False)
 
     def step(self, sh, th):
-        seq, cancel, head, tail, pending, served, skipped = sh
+        seq, cancel, head, tail, pending, served, skipped, dup = sh
         R, n = self.R, self.n
         kind, pc, t = th
 
@@ -44,7 +52,7 @@ class Ring:
 
         if kind == "prod":
             if pc == "draw":
-                return [((seq, cancel, head, tail + 1, pending, served, skipped), ("prod", "check", tail))]
+                return [((seq, cancel, head, tail + 1, pending, served, skipped, dup), ("prod", "check", tail))]
             if pc == "check":
                 if seq[t % R] == t:
                     return [(sh, ("prod", "write", t))]
@@ -52,42 +60,53 @@ class Ring:
             if pc == "late":
                 return [(sh, ("prod", "check", t)), (sh, ("prod", "cancel", t))]
             if pc == "write":  # publish the request
-                return [((with_seq(t % R, t + 1), cancel, head, tail, pending, served, skipped), ("prod", "wrote", t))]
+                return [((with_seq(t % R, t + 1), cancel, head, tail, pending, served, skipped, dup), ("prod", "wrote", t))]
             if pc == "cancel":
-                return [((seq, with_cancel(t % n, t + 1), head, tail, pending, served, skipped),
+                return [((seq, with_cancel(t % n, t + 1), head, tail, pending, served, skipped, dup),
                          ("prod", "cancelled", t))]
             return []
         if kind == "host":
             if pc == "draw":
                 if head >= self.P:  # every ticket of the scenario is taken: the thread stops
                     return [(sh, ("host", "stopped", None))]
-                return [((seq, cancel, head + 1, tail, pending, served, skipped), ("host", "wait", head))]
+                return [((seq, cancel, head + 1, tail, pending, served, skipped, dup), ("host", "wait", head))]
             if pc == "wait":
                 if seq[t % R] == t + 1:
                     return [(sh, ("host", "serve", t))]
                 return [(sh, ("host", "skip_c", t))]
             if pc == "serve":  # publish the pages; their copier frees the slot later
-                return [((seq, cancel, head, tail, pending | {t}, served | {t}, skipped), ("host", "draw", None))]
+                nxt = ("host", "mcheck", t) if self.merge else ("host", "draw", None)
+                return [((seq, cancel, head, tail, pending | {t}, served | {t}, skipped, dup or t in served), nxt)]
+            if pc == "mcheck":  # is the next ticket's request already published?
+                return [(sh, ("host", "mclaim" if seq[(t + 1) % R] == t + 2 else "draw", t + 1))]
+            if pc == "mclaim":
+                if self.merge == "cas":  # head: t -> t + 1 only if no host thread drew t meanwhile
+                    if head != t:
+                        return [(sh, ("host", "draw", None))]
+                    return [((seq, cancel, t + 1, tail, pending, served, skipped, dup), ("host", "serve", t))]
+                return [(sh, ("host", "mstore" if head == t else "draw", t))]
+            if pc == "mstore":  # the planted mistake: store after a separate load
+                return [((seq, cancel, t + 1, tail, pending, served, skipped, dup), ("host", "serve", t))]
             if pc == "skip_c":
                 return [(sh, ("host", "skip_s" if cancel[t % n] == t + 1 else "wait", t))]
             if pc == "skip_s":
                 return [(sh, ("host", "clear" if seq[t % R] == t else "wait", t))]
             if pc == "clear":
-                return [((seq, with_cancel(t % n, 0), head, tail, pending, served, skipped), ("host", "free", t))]
+                return [((seq, with_cancel(t % n, 0), head, tail, pending, served, skipped, dup), ("host", "free", t))]
             if pc == "free":
-                return [((with_seq(t % R, t + R), cancel, head, tail, pending, served, skipped | {t}),
+                return [((with_seq(t % R, t + R), cancel, head, tail, pending, served, skipped | {t}, dup),
                          ("host", "draw", None))]
             return []
         raise AssertionError(kind)
 
     def copier(self, sh):
         """The GPU copies a served request's pages and frees its slot."""
-        seq, cancel, head, tail, pending, served, skipped = sh
+        seq, cancel, head, tail, pending, served, skipped, dup = sh
         out = []
         for t in pending:
             s = list(seq)
             s[t % self.R] = t + self.R
-            out.append((tuple(s), cancel, head, tail, pending - {t}, served, skipped))
+            out.append((tuple(s), cancel, head, tail, pending - {t}, served, skipped, dup))
         return out
 
 
@@ -134,17 +153,19 @@ def _can_finish(seen, edges, finals):
     return good
 
 
+@pytest.mark.parametrize("merge", [None, "cas"])
 @pytest.mark.parametrize("slots,producers,hosts", [(2, 3, 1), (2, 3, 2), (2, 2, 1), (3, 4, 1), (2, 4, 2)])
-def test_cancelled_tickets_are_skipped_and_nothing_sticks(slots, producers, hosts):
-    ring = Ring(slots, cancel_n=slots + producers, tickets=producers)
+def test_cancelled_tickets_are_skipped_and_nothing_sticks(slots, producers, hosts, merge):
+    ring = Ring(slots, cancel_n=slots + producers, tickets=producers, merge=merge)
     threads = [("prod", "draw", None)] * producers + [("host", "draw", None)] * hosts
     seen, edges, finals = _explore(ring, threads)
     assert finals
     good = _can_finish(seen, edges, finals)
     assert len(good) == len(seen), "states from which no schedule finishes: %d" % (len(seen) - len(good))
     outcomes = set()
+    assert not any(sh[7] for sh, _ in seen), "a ticket was served twice"
     for sh, ths in finals:
-        seq, cancel, head, tail, pending, served, skipped = sh
+        seq, cancel, head, tail, pending, served, skipped, dup = sh
         wrote = {t for k, pc, t in ths if pc == "wrote"}
         gave_up = {t for k, pc, t in ths if pc == "cancelled"}
         assert served == wrote and skipped == gave_up
@@ -170,3 +191,27 @@ def test_one_slot_is_not_enough():
     threads = [("prod", "draw", None)] * 2 + [("host", "draw", None)]
     seen, edges, finals = _explore(ring, threads)
     assert len(_can_finish(seen, edges, finals)) < len(seen)
+
+
+def test_merge_claim_must_be_one_compare_and_swap():
+    """Planted mistake: a host thread that claims the next ticket with a load of the head
+    and a later store lets another host thread draw the same ticket in between, and the
+    request is served twice."""
+    ring = Ring(2, cancel_n=5, tickets=3, merge="racy")
+    threads = [("prod", "draw", None)] * 3 + [("host", "draw", None)] * 2
+    seen, edges, finals = _explore(ring, threads)
+    assert any(sh[7] for sh, _ in seen)
+    ring = Ring(2, cancel_n=5, tickets=3, merge="cas")
+    seen, edges, finals = _explore(ring, threads)
+    assert not any(sh[7] for sh, _ in seen)
+
+
+def test_merging_happens_in_some_schedule():
+    """With one host thread behind two published requests, the thread serves the second
+    one merged with the first (the head moves past it by the claim, not by a draw)."""
+    ring = Ring(3, cancel_n=5, tickets=2, merge="cas")
+    threads = [("prod", "draw", None)] * 2 + [("host", "draw", None)]
+    seen, edges, finals = _explore(ring, threads)
+    merged = any(th[1] == "mclaim" and sh[0][th[2] % 3] == th[2] + 1 and sh[2] == th[2]
+                 for sh, ths in seen for th in ths if th[0] == "host")
+    assert merged
