@@ -185,21 +185,42 @@ def oracle_sample(path, page, frames, blocks, stride, budget_s, mode="readahead"
     return nbytes, dt, done
 
 
-def serving_bench(args, xfer, mode):
-    """Config 5: 64 scans over log-uniform 16 MiB - 4 GiB files, Poisson 20 req/s, 6 GiB cache."""
-    import numpy as np
-    import torch
-
+def serving_files():
+    """The serving workload's files: 64 sizes 2^(24+8u) bytes (log-uniform 16 MiB - 4 GiB), seeds 1000+i."""
     import inputs
-    from paper_2109_05366_gb300 import gfs, serving
+    from paper_2109_05366_gb300 import serving
     sizes = serving.log_uniform_sizes(64, 24, 32, seed=5)
     paths = []
     for i, sz in enumerate(sizes):
         p = os.path.join(data_dir(), "gfs_serve_%d_%d.bin" % (i, sz))
         inputs.ensure_file(p, 1000 + i, sz)
         paths.append(p)
-    arrivals = serving.poisson_arrivals(64, 20.0, seed=5)
-    out = {}
+    return paths, sizes
+
+
+def peak_admitted(results) -> int:
+    """Largest number of requests admitted and not yet complete at one time (device timestamps)."""
+    ev = []
+    for r in results:
+        ev.append((r["t_admit_ns"], 1))
+        ev.append((r["t_done_ns"], -1))
+    ev.sort(key=lambda e: (e[0], e[1]))  # a completion at the same instant goes first
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def serving_bench(args, xfer, mode, rate_per_s):
+    """Config 5: 64 scans over the serving files, Poisson arrivals at rate_per_s (None: all at
+    once, saturating), 6 GiB cache.  Returns (summary, per-request results)."""
+    import numpy as np
+    import torch
+
+    from paper_2109_05366_gb300 import gfs, serving
+    paths, sizes = serving_files()
+    arrivals = serving.poisson_arrivals(64, rate_per_s, seed=5) if rate_per_s else [0.0] * 64
     with gfs.Context(cache_bytes=6 * GiB, page_size=512 * KiB, mode=mode, xfer=xfer, max_rpc_pages=16,
                      rpc_slots=512, latency_capacity=1 << 20, max_files=80, max_streams=1024) as ctx:
         fids = [ctx.open(p) for p in paths]
@@ -211,12 +232,15 @@ def serving_bench(args, xfer, mode):
         finally:
             ctx.serve_stop()
         out = serving.summarize(res, t0)
+        out["peak_admitted"] = peak_admitted(res)
         lat = ctx.latencies()
         if len(lat):
             out["gread_p50_us"] = round(float(np.percentile(lat, 50)) / 1e3, 1)
             out["gread_p99_us"] = round(float(np.percentile(lat, 99)) / 1e3, 1)
         out["total_file_bytes"] = int(sum(sizes))
-    return out
+        st = ctx.stats()
+        out["timeouts"] = st["timeouts"]
+    return out, res
 
 
 def run_cfg3(args):
@@ -700,7 +724,204 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- the GPU path
+def xfer_code(name):
+    from paper_2109_05366_gb300 import gfs
+    return {"pull": gfs.XFER_PULL, "dma": gfs.XFER_DMA, "mapped": gfs.XFER_MAPPED}[name]
+
+
+def scan_leg(path, stride, blocks, steps, warmup, stream, threads=256, fused=False, open_flags=0, before=None,
+             **cfg):
+    """Time `steps` scans of `path` (after `warmup` untimed ones), each from an empty GPU page
+    cache, in a context of its own; every scan's counts are checked.  `before(i)` runs before
+    scan i outside the timed region (e.g. dropping the host page cache).  Returns a dict."""
+    import torch
+
+    from paper_2109_05366_gb300 import gfs
+    size = os.path.getsize(path)
+    ns = (size + stride - 1) // stride
+    out = tuple(torch.empty(ns, dtype=torch.int64, device="cuda") for _ in range(3))
+    ts, ok = [], True
+    with gfs.Context(**cfg) as ctx:
+        fid = ctx.open(path, open_flags)
+        mapped = bool(ctx.fstat(fid).mapped)
+        for i in range(warmup + steps):
+            ctx.reset_cache(stream)
+            if before:
+                before(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.scan(fid, stride, blocks=blocks, threads=threads, fused=fused, out=out, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            cnt = out[0].cpu().numpy()
+            ok = ok and bool((cnt[:-1] == stride).all()) and int(cnt[-1]) == size - (ns - 1) * stride
+        st = ctx.stats(stream)
+    t = sum(ts) / len(ts)
+    return {"gbps": round(size / t / 1e9, 2), "ms": round(1e3 * t, 3), "steps": steps, "counts_ok": ok,
+            "rpcs": st["rpcs"], "host_preads": st["host_preads"], "host_merged": st["host_merged"],
+            "timeouts": st["timeouts"], "mapped": mapped}
+
+
+def ra_vs_od_legs(args, stream):
+    """Readahead against on-demand, the same steps each, where a request costs something:
+    4 KiB pages (the paper's page size, Section 6.1) with the mapped transfer, and 64 KiB
+    pages with host pread staging (pull), as GPUfs's host threads read."""
+    from paper_2109_05366_gb300 import gfs
+    res = {}
+    steps, warmup = max(1, min(args.steps, 5)), 1
+    small = os.path.join(data_dir(), "gfs_bench_s2_%d.bin" % (2 * GiB))
+    ensure_input(small, 2, 2 * GiB)
+    big = os.path.join(data_dir(), "gfs_bench_s2_%d.bin" % (8 * GiB))
+    ensure_input(big, 2, 8 * GiB)
+    for name, path, page, cache, xf, ra, mx in (
+            ("page4KiB_mapped_2GiB_file_256MiB_cache", small, 4 * KiB, 256 * MiB, gfs.XFER_MAPPED, 63, 64),
+            ("page64KiB_pull_8GiB_file_1GiB_cache", big, 64 * KiB, GiB, gfs.XFER_PULL, 15, 32)):
+        entry = {}
+        for label, mode in (("readahead", gfs.MODE_READAHEAD), ("ondemand", gfs.MODE_ONDEMAND)):
+            entry[label] = scan_leg(path, MiB, 296, steps, warmup, stream, cache_bytes=cache, page_size=page, mode=mode,
+                                    xfer=xf, ra_cap_pages=ra, max_rpc_pages=mx, rpc_slots=512)
+        entry["readahead_over_ondemand"] = round(entry["readahead"]["gbps"] / entry["ondemand"]["gbps"], 2)
+        res[name] = entry
+    return res
+
+
+def merge_legs(args, path, stream):
+    """Host reads merged across requests against one request per read, for the transfers whose
+    host threads pread (pull, dma), on the 8 GiB file: the bench's pages with readahead, and
+    64 KiB pages on demand (one page per request)."""
+    from paper_2109_05366_gb300 import gfs
+    size = os.path.getsize(path)
+    res = {}
+    for xname in ("pull", "dma"):
+        for page, mode, mname, mx in ((512 * KiB, gfs.MODE_READAHEAD, "readahead", 16),
+                                     (64 * KiB, gfs.MODE_ONDEMAND, "ondemand", 16)):
+            key = "%s_page%dKiB_%s" % (xname, page // KiB, mname)
+            entry = {}
+            for label, merge in (("one_request_per_read", 1), ("merged", 0)):
+                r = scan_leg(path, MiB, 296, 2, 1, stream, cache_bytes=GiB, page_size=page, mode=mode,
+                             xfer=xfer_code(xname), ra_cap_pages=8, max_rpc_pages=mx, rpc_slots=512,
+                             host_merge_pages=merge)
+                r["host_preads_per_GiB"] = round(r["host_preads"] / (size / GiB), 1)
+                entry[label] = r
+            res[key] = entry
+    return res
+
+
+def mapped_open_close(path):
+    """Cost of mapping a file for the GPU (registration pins every page) and of unmapping it."""
+    from paper_2109_05366_gb300 import gfs
+    with gfs.Context(cache_bytes=GiB, page_size=512 * KiB) as ctx:
+        t0 = time.perf_counter()
+        fid = ctx.open(path)
+        t1 = time.perf_counter()
+        mapped = bool(ctx.fstat(fid).mapped)
+        ctx.close(fid)
+        t2 = time.perf_counter()
+    return {"open_s": round(t1 - t0, 4), "close_s": round(t2 - t1, 4), "mapped": mapped}
+
+
+def _drop_host_cache(path):
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        os.posix_fadvise(fd, 0, 0, os.POSIX_FADV_DONTNEED)
+    finally:
+        os.close(fd)
+
+
+def cold_legs(args, stream):
+    """Cold reads of a 2 GiB file on the box's disk: the host page cache dropped before every
+    scan (posix_fadvise DONTNEED, checked with mincore), and O_DIRECT reads (GFS_DIRECT)."""
+    import torch
+
+    import inputs
+    from paper_2109_05366_gb300 import gfs
+    d = os.environ.get("GFS_COLD_DIR", tempfile.gettempdir())
+    size = 2 * GiB
+    path = os.path.join(d, "gfs_cold_s6_%d.bin" % size)
+    probe = os.path.join(d, "gfs_cold_probe")
+    try:
+        with open(probe, "wb") as f:
+            f.write(b"\0" * 4096)
+        fd = os.open(probe, os.O_RDONLY | os.O_DIRECT)
+        os.close(fd)
+    except OSError as e:
+        return {"unavailable": "no O_DIRECT under %s (%s): no disk-backed file system to read cold from" % (d, e)}
+    finally:
+        if os.path.exists(probe):
+            os.unlink(probe)
+    t0 = time.time()
+    inputs.ensure_file(path, 6, size)
+    fd = os.open(path, os.O_RDONLY)
+    os.fsync(fd)  # written pages must be clean before the cache can drop them
+    os.close(fd)
+    res = {"file": "2 GiB seeded file under %s (not tmpfs)" % d, "input_s": round(time.time() - t0, 1)}
+    resident = []
+
+    def drop(i):
+        _drop_host_cache(path)
+        resident.append(round(_resident_fraction(path), 4))
+
+    for label, xf, mode, flags in (("pull_readahead", gfs.XFER_PULL, 0, 0), ("pull_ondemand", gfs.XFER_PULL, 1, 0),
+                                   ("pull_readahead_direct", gfs.XFER_PULL, 0, gfs.DIRECT),
+                                   ("dma_readahead_direct", gfs.XFER_DMA, 0, gfs.DIRECT),
+                                   ("mapped_default_readahead", gfs.XFER_MAPPED, 0, 0)):
+        resident.clear()
+        _drop_host_cache(path)  # before the open too: a resident file would be mapped (and pinned)
+        try:
+            r = scan_leg(path, MiB, 296, 2, 0, stream, open_flags=flags, before=None if flags else drop,
+                         cache_bytes=256 * MiB, page_size=512 * KiB, mode=mode, xfer=xf, max_rpc_pages=16,
+                         rpc_slots=512)
+            if not flags:
+                r["resident_before_each_scan"] = list(resident)
+            res[label] = r
+        except Exception as e:  # report and go on
+            res[label] = {"error": str(e)}
+    _drop_host_cache(path)
+    res["pread_16thr_cold_gbps"] = round(gfs.probe_pread(path, 16, 4 * MiB, 1), 2)
+    _drop_host_cache(path)
+    d_file = torch.empty(size, dtype=torch.uint8, device="cuda")
+    out = tuple(torch.empty(size // MiB, dtype=torch.int64, device="cuda") for _ in range(3))
+    res["cpuio_16thr_cold_gbps"] = round(size / gfs.cpuio_scan(path, MiB, MiB, 16, 8 * MiB, d_file, out) / 1e9, 2)
+    return res
+
+
+def oracle_checks(path, stride, last, serving_results, cpu_seconds, workload):
+    """The CPU-baseline leg, after every GPU measurement: (1) the oracle as it stands timed on one
+    host core on a bounded sample of the workload; (2) parity: every stride of the last timed
+    step, and every serving completion, against the oracle's plain definition computed on all
+    host cores (worker processes started by spawn)."""
+    from oracle import pool
+    size_, seed_, page_, cache_, blocks_, stride_ = WORKLOADS[workload]
+    b, t, n = oracle_sample(path, page_, cache_ // page_, blocks_, stride_, cpu_seconds)
+    cpu = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": "first %d strides (%d MiB) of the canonical trace, %.1f s" % (n, b // MiB, t)}
+    t0 = time.perf_counter()
+    c, s, h = pool.scan_plain_parallel(path, stride)
+    import numpy as np
+    cnt, sm, hs = last
+    bad = int(np.count_nonzero(cnt[:len(c)] != np.array(c, dtype=np.int64)) +
+              np.count_nonzero(sm[:len(s)].view(np.uint64) != np.array(s, dtype=np.uint64)) +
+              np.count_nonzero(hs[:len(h)].view(np.uint64) != np.array(h, dtype=np.uint64)))
+    parity = {"timed_step": {"strides": len(c), "fields_checked": 3 * len(c), "mismatches": bad,
+                             "exact": bad == 0 and len(cnt) >= len(c),
+                             "against": "oracle/plain.py per stride (count, byte sum, position hash)",
+                             "oracle_s": round(time.perf_counter() - t0, 1), "oracle_procs": pool.workers()}}
+    if serving_results:
+        paths, sizes = serving_files()
+        t0 = time.perf_counter()
+        want = pool.many_range_checksums([(p, 0, sz) for p, sz in zip(paths, sizes)])
+        for label, res in serving_results.items():
+            wrong = sum(1 for i, r in enumerate(res)
+                        if r["status"] != 0 or (r["bytes"], r["sum"], r["hash"]) != want[i])
+            parity["serving_" + label] = {"completions": len(res), "mismatches": wrong, "exact": wrong == 0}
+        parity["serving_oracle_s"] = round(time.perf_counter() - t0, 1)
+    return cpu, parity
+
+
 def run_gfs(args):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -721,7 +942,6 @@ def run_gfs(args):
     nstr = (size + stride - 1) // stride
     out = tuple(torch.empty(nstr, dtype=torch.int64, device=dev) for _ in range(3))
     peaks = measured_peaks()
-    res = {}
 
     def timed_scans(ctx, fid, steps, warmup, fused=False):
         ev = []
@@ -742,18 +962,20 @@ def run_gfs(args):
     cfg = dict(cache_bytes=cache, page_size=page, host_threads=args.host_threads, ra_cap_pages=args.ra_cap,
                latency_capacity=1 << 16,
                rpc_slots=args.rpc_slots, staging_bytes=args.staging_mib * MiB, max_rpc_pages=args.max_rpc_pages,
-               xfer={"pull": gfs.XFER_PULL, "dma": gfs.XFER_DMA, "mapped": gfs.XFER_MAPPED}[args.xfer])
+               xfer=xfer_code(args.xfer))
     with gfs.Context(mode=gfs.MODE_READAHEAD, **cfg) as ctx:
         fid = ctx.open(path)
-        # correctness of the timed configuration on sampled strides (full check in tests)
         with ClockSampler(local) as clk:
             if world > 1:
                 dist.barrier()
             times = timed_scans(ctx, fid, args.steps, args.warmup, fused=args.fused)
         st = ctx.stats(stream)
         lat = ctx.latencies(stream)
-        cnt = out[0].cpu().numpy()
+        # the last timed step's results, checked stride for stride against the oracle below
+        last = tuple(t.cpu().numpy().copy() for t in out)
+        cnt = last[0]
         assert (cnt[:-1] == stride).all() and cnt[-1] == size - (nstr - 1) * stride, "scan returned short counts"
+        mapped = bool(ctx.fstat(fid).mapped)
         # e2e: the C-ABI call with host result buffers, wall clock, cache reset outside
         e2e_t = []
         for _ in range(max(1, min(args.steps, 3))):
@@ -763,14 +985,15 @@ def run_gfs(args):
             e2e_t.append(time.perf_counter() - t0)
     total = max_over_ranks(sum(times), dist if world > 1 else None, dev)
     value = job_rate(size, args.steps, world, total)
-    res["readahead"] = value
 
     extra = {}
+    binding, binding_src = None, None
     if rank == 0 and not args.quick:
         with gfs.Context(mode=gfs.MODE_ONDEMAND, **cfg) as ctx:
             fid = ctx.open(path)
-            od = timed_scans(ctx, fid, 1, 1)
+            od = timed_scans(ctx, fid, args.steps, args.warmup)
         extra["ondemand_gbps"] = round(size / (sum(od) / len(od)) / 1e9, 2)
+        extra["ondemand_steps"] = len(od)
         d_file = torch.empty(size, dtype=torch.uint8, device=dev)
         cpu_t = []
         for i in range(3):
@@ -788,15 +1011,25 @@ def run_gfs(args):
                                "pread_16thr_gbps": round(prd, 1), "gpu_read_host_gbps": round(pull, 1)}
         # the link the chosen transfer moves data over: mapped = GPU reads of host
         # memory; pull = host pread + GPU reads; dma = host pread + copy engine
-        if args.xfer == "mapped":
+        if args.xfer == "mapped" and mapped:
             binding, binding_src = pull, "GPU threads reading mapped host memory"
-        elif args.xfer == "pull":
+        elif args.xfer in ("mapped", "pull"):
             binding, binding_src = min(pull, prd), "min(GPU reads of host memory, 16-thread pread)"
         else:
             binding, binding_src = min(h2d, prd), "min(pinned H2D copy, 16-thread pread)"
-
-    else:
-        binding, binding_src = None, None
+        if args.xfer == "mapped":
+            oc = mapped_open_close(path)
+            e2e_mean = sum(e2e_t) / len(e2e_t)
+            oc["e2e_open_scan_close_gbps"] = round(size / (oc["open_s"] + e2e_mean + oc["close_s"]) / 1e9, 2)
+            extra["mapped_registration"] = oc
+        if not args.no_extras:
+            for key, fn in (("readahead_vs_ondemand", lambda: ra_vs_od_legs(args, stream)),
+                            ("host_merge", lambda: merge_legs(args, path, stream)),
+                            ("cold", lambda: cold_legs(args, stream))):
+                try:
+                    extra[key] = fn()
+                except Exception as e:  # a side measurement must not cost the bench line
+                    extra[key] = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank != 0:
         if world > 1:
@@ -814,26 +1047,27 @@ def run_gfs(args):
         "config": {"workload": args.workload, "file_bytes": size, "page_bytes": page, "cache_bytes": cache,
                    "blocks": blocks, "threads": args.threads, "stride_bytes": stride, "ra_cap_pages": args.ra_cap,
                    "host_threads": args.host_threads, "rpc_slots": args.rpc_slots, "fused": bool(args.fused),
-                   "xfer": args.xfer, "max_rpc_pages": args.max_rpc_pages,
-                   "l2": "inputs larger than L2 (8 GiB file); no flush", "parallelism": "replicas" if world > 1 else "1gpu"},
+                   "xfer": args.xfer, "mapped": mapped, "max_rpc_pages": args.max_rpc_pages,
+                   "l2": "inputs larger than L2 (%d MiB file); no flush" % (size // MiB),
+                   "parallelism": "replicas" if world > 1 else "1gpu"},
         "clocks": clocks,
         "e2e": {"value": round(size / (sum(e2e_t) / len(e2e_t)) / 1e9, 3), "unit": "GB/s",
                 "h2d_bytes_per_step": size, "d2h_bytes_per_step": nstr * 24},
         "gpu_launches": args.steps,
         "stats_last_step": {k: st[k] for k in ("rpcs", "pages_fetched", "hits", "misses", "coalesced_waits",
                                                "ra_pages_sync", "ra_pages_async", "evictions",
-                                               "unconsumed_evictions", "timeouts", "eio")},
+                                               "unconsumed_evictions", "timeouts", "eio", "host_merged")},
         "input_gen_s": round(gen_s, 1),
     }
     if len(lat):
-        import numpy as np
         line["gread_latency_us"] = {"p50": round(float(np.percentile(lat, 50)) / 1e3, 1),
                                     "p99": round(float(np.percentile(lat, 99)) / 1e3, 1),
                                     "greads": int(len(lat)), "read_len": stride}
     if binding:
         from paper_2109_05366_gb300 import build as _b
         traffic = None
-        if _b.kernel_digest() == NCU_DRAM["kernel_digest"] and args.xfer == "mapped" and not args.fused:
+        if (_b.kernel_digest() == NCU_DRAM["kernel_digest"] and args.xfer == "mapped" and mapped and not args.fused
+                and args.workload == DEFAULT_WORKLOAD):
             traffic = int(NCU_DRAM["bytes_per_file_byte"] * size)  # DRAM bytes per launch
         line["roofline"] = {"bound": "link", "achieved": round(value / world, 2), "peak": round(binding, 1),
                             "unit": "GB/s", "frac": round(value / world / binding, 3), "traffic": traffic,
@@ -844,18 +1078,20 @@ def run_gfs(args):
                                 "unit": "GB/s", "frac": round(nbytes_hbm / kt / 1e9 / hbm, 4),
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     line.update(extra)
+    serving_results = {}
     if rank == 0 and not args.quick and not args.no_serving:
-        xf = {"pull": gfs.XFER_PULL, "dma": gfs.XFER_DMA, "mapped": gfs.XFER_MAPPED}[args.xfer]
-        line["serving"] = {"workload": "64 scans, files 2^(24+8u) B (log-uniform 16 MiB-4 GiB), Poisson 20/s, "
-                                       "6 GiB cache, 296 CTAs, 1 MiB units",
-                           "readahead": serving_bench(args, xf, gfs.MODE_READAHEAD),
-                           "ondemand": serving_bench(args, xf, gfs.MODE_ONDEMAND)}
+        xf = xfer_code(args.xfer)
+        serv = {"workload": "64 scans, files 2^(24+8u) B (log-uniform 16 MiB-4 GiB), 6 GiB cache, 296 CTAs, "
+                            "1 MiB units; Poisson 20/s, and all 64 at once (saturating)"}
+        for label, mode, rate in (("readahead_poisson20", gfs.MODE_READAHEAD, 20.0),
+                                  ("ondemand_poisson20", gfs.MODE_ONDEMAND, 20.0),
+                                  ("readahead_saturating", gfs.MODE_READAHEAD, None),
+                                  ("ondemand_saturating", gfs.MODE_ONDEMAND, None)):
+            serv[label], serving_results[label] = serving_bench(args, xf, mode, rate)
+        line["serving"] = serv
     if not args.quick and not args.no_cpu_baseline:
-        size_, seed_, page_, cache_, blocks_, stride_ = WORKLOADS[args.workload]
-        b, t, n = oracle_sample(path, page_, cache_ // page_, blocks_, stride_, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": "first %d strides (%d MiB) of the canonical trace, %.1f s" % (
-                                    n, b // MiB, t)}
+        line["cpu_baseline"], line["parity"] = oracle_checks(path, stride, last, serving_results, args.cpu_seconds,
+                                                             args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -881,6 +1117,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the readahead-vs-on-demand, host-merge and cold legs")
     ap.add_argument("--sweep", choices=["cfg3", "cfg4", "cold", "paper", "random", "queue"], default=None,
                     help="run a sweep instead of the bench line")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

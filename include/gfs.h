@@ -52,6 +52,12 @@ extern "C" {
 /* Open flags (Section 4.4, "Page cache coherency": readahead for read-only opens only). */
 #define GFS_RDONLY 0
 #define GFS_RDWR 2 /* accepted for the hint semantics only; the path never writes */
+#define GFS_DIRECT 0x100 /* or-ed into the flags of gfs_open: the host I/O threads read the file with
+                          * O_DIRECT, bypassing the host page cache (a cold read from storage every
+                          * time, Section 6: the paper flushes the page cache before each run).  The
+                          * file is never mapped (GFS_XFER_MAPPED serves it by pread staging);
+                          * gfs_open returns the error of open(2) where the file system refuses
+                          * O_DIRECT (tmpfs, for one) */
 
 /* fadvise hints (Section 4.4: the user may turn the prefetcher off). */
 #define GFS_ADV_NORMAL 0

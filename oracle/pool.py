@@ -62,24 +62,33 @@ def scan_plain_parallel(path: str, stride: int, read_len: int | None = None, pro
 def range_checksums(path: str, off: int, length: int, procs: int | None = None, piece: int = 64 << 20):
     """(count, sum, hash) of the plain gread of [off, off + length): the per-piece values of
     the plain definition added mod 2^64 (pieces of `piece` bytes starting at off)."""
-    size = os.path.getsize(path)
-    if off >= size or length <= 0:
-        return 0, 0, 0
-    end = min(off + length, size)
-    jobs = []
-    p = off
-    while p < end:
-        q = min(end, p + piece)
-        jobs.append((path, p, q - p))
-        p = q
+    return many_range_checksums([(path, off, length)], procs, piece)[0]
+
+
+def many_range_checksums(ranges, procs: int | None = None, piece: int = 64 << 20):
+    """range_checksums for every (path, off, length) of `ranges`, on one pool of processes."""
+    jobs, owner = [], []
+    for k, (path, off, length) in enumerate(ranges):
+        size = os.path.getsize(path)
+        end = min(off + length, size) if length > 0 else off
+        p = off
+        while p < end:
+            q = min(end, p + piece)
+            jobs.append((path, p, q - p))
+            owner.append(k)
+            p = q
     n = workers(procs)
-    if n == 1 or len(jobs) == 1:
+    if n == 1 or len(jobs) <= 1:
         res = list(map(_piece, jobs))
     else:
         with ProcessPoolExecutor(max_workers=min(n, len(jobs)), mp_context=mp.get_context("spawn")) as ex:
-            res = list(ex.map(_piece, jobs))
-    cnt = sum(r[0] for r in res)
-    return cnt, sum(r[1] for r in res) & U64_MASK, sum(r[2] for r in res) & U64_MASK
+            res = list(ex.map(_piece, jobs, chunksize=1))
+    out = [[0, 0, 0] for _ in ranges]
+    for k, (c, s, h) in zip(owner, res):
+        out[k][0] += c
+        out[k][1] = (out[k][1] + s) & U64_MASK
+        out[k][2] = (out[k][2] + h) & U64_MASK
+    return [tuple(o) for o in out]
 
 
 def _piece(args):

@@ -209,6 +209,7 @@ bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
   out->fd = f.fd;
   out->size = f.size;
   out->dev_map = f.dev_map;
+  out->direct = f.direct;
   return true;
 }
 
@@ -834,6 +835,8 @@ int gfs_set_faults(gfs_ctx* ctx, uint32_t eio_every, uint32_t short_every, uint3
 int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
   if (!ctx || !path || !fid) return -EINVAL;
   if ((flags & 3) != GFS_RDONLY && (flags & 3) != GFS_RDWR) return -EINVAL;
+  if (flags & ~(3 | GFS_DIRECT)) return -EINVAL;
+  const bool direct = (flags & GFS_DIRECT) != 0;
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->cfg.device));
   auto pick = [ctx]() {
@@ -859,7 +862,7 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
     slot = pick();
     if (slot < 0) return -EMFILE;
   }
-  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  int fd = open(path, O_RDONLY | O_CLOEXEC | (direct ? O_DIRECT : 0));
   if (fd < 0) {
     const int e = errno;
     std::lock_guard<std::mutex> fl(ctx->files_mu);
@@ -880,10 +883,12 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
     hf.fd = fd;
     hf.size = (uint64_t)st.st_size;
     hf.flags = flags;
+    hf.direct = direct;
     hf.advice = GFS_ADV_NORMAL;
     hf.path = path;
   }
-  if (ctx->cfg.xfer == GFS_XFER_MAPPED) map_file(hf);  // falls back to pread staging when it fails
+  // falls back to pread staging when it fails; a direct file is read from storage every time
+  if (ctx->cfg.xfer == GFS_XFER_MAPPED && !direct) map_file(hf);
   {
     const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
     hf.fetched_bytes = (size_t)((np + 31) / 32) * 4;

@@ -28,6 +28,7 @@ struct HostFile {
   uint32_t* d_fetched = nullptr;  // per-page fetched bits (device)
   size_t fetched_bytes = 0;
   int flags = 0;
+  bool direct = false;     // GFS_DIRECT: fd was opened with O_DIRECT
   int advice = GFS_ADV_NORMAL;
   bool open = false;
   std::string path;

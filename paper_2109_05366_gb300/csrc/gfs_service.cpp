@@ -113,7 +113,11 @@ void IoService::record_io(int idx, uint32_t fid, uint64_t off, uint64_t bytes, u
   r.t_ns = t_ns;
 }
 
-ssize_t IoService::do_pread(int idx, int fd, uint8_t* buf, size_t n, uint64_t off) {
+// Read n bytes at off into buf (looping over short reads; stops at EOF).  With
+// O_DIRECT the length is rounded up to whole 4 KiB blocks (offsets and staging
+// buffers are page aligned already; a read past EOF just returns less).
+ssize_t IoService::do_pread(int idx, const FileView& fv, uint8_t* buf, size_t n, uint64_t off) {
+  const int fd = fv.fd;
   const uint64_t k = pread_count_.fetch_add(1, std::memory_order_relaxed);
   const uint32_t eio = eio_every_.load(std::memory_order_relaxed);
   const uint32_t sh = short_every_.load(std::memory_order_relaxed);
@@ -132,23 +136,25 @@ ssize_t IoService::do_pread(int idx, int fd, uint8_t* buf, size_t n, uint64_t of
       b.fetch_add(d, std::memory_order_relaxed);
     }
   } acc{stats.ns_pread, tstats_[idx].pread_ns, t0};
+  const size_t want = n;
+  if (fv.direct) n = (n + 4095) & ~(size_t)4095;
   size_t got = 0;
   while (got < n) {
     ssize_t r = ::pread(fd, buf + got, n - got, (off_t)(off + got));
     if (r < 0) {
       if (errno == EINTR) continue;
-      return got ? (ssize_t)got : -errno;
+      return got ? (ssize_t)std::min(got, want) : -errno;
     }
     if (r == 0) break;  // EOF
     got += (size_t)r;
   }
-  return (ssize_t)got;
+  return (ssize_t)std::min(got, want);
 }
 
 void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames) {
   Sink* sink = w.sink;
   int& cur = w.cur;
-  FileView fv{-1, 0, 0};
+  FileView fv{-1, 0, 0, false};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
   const uint64_t off0 = page_lo << cfg_.page_shift;
@@ -166,7 +172,7 @@ void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages
     if (have && coff < fv.size) want = (size_t)std::min<uint64_t>((uint64_t)cn * P, fv.size - coff);
     ssize_t got = 0;
     if (want) {
-      got = do_pread(w.idx, fv.fd, buf, want, coff);
+      got = do_pread(w.idx, fv, buf, want, coff);
       stats.preads.fetch_add(1, std::memory_order_relaxed);
       if (got < 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);
@@ -208,7 +214,7 @@ void IoService::serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages
 void IoService::serve_pull(Worker& w, uint32_t fid, const Req* group, int ng) {
   const int idx = w.idx;
   uint32_t& cur = w.pull_cur;
-  FileView fv{-1, 0, 0};
+  FileView fv{-1, 0, 0, false};
   const bool have = files_(fid, &fv);
   const uint64_t P = cfg_.page_size;
   const uint64_t off0 = group[0].page_lo << cfg_.page_shift;
@@ -281,7 +287,7 @@ void IoService::serve_pull(Worker& w, uint32_t fid, const Req* group, int ng) {
     ssize_t got = 0;
     long long err = 0;
     if (want) {
-      got = do_pread(idx, fv.fd, buf, want, coff);
+      got = do_pread(idx, fv, buf, want, coff);
       stats.preads.fetch_add(1, std::memory_order_relaxed);
       if (got < 0) {
         stats.errors.fetch_add(1, std::memory_order_relaxed);

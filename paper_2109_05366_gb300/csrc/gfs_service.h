@@ -43,6 +43,7 @@ struct FileView {
   int fd;
   uint64_t size;
   uint64_t dev_map;  // device address of the file's registered mapping, 0 if not mapped
+  bool direct;       // fd was opened with O_DIRECT: reads are whole 4 KiB blocks into aligned buffers
 };
 
 struct ServiceConfig {
@@ -153,7 +154,7 @@ class IoService {
   int gather(Worker& w, uint32_t fid, Req* group, uint32_t max_pages_each);
   void serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
   void serve_pull(Worker& w, uint32_t fid, const Req* group, int ng);
-  ssize_t do_pread(int idx, int fd, uint8_t* buf, size_t n, uint64_t off);
+  ssize_t do_pread(int idx, const FileView& fv, uint8_t* buf, size_t n, uint64_t off);
   void record_io(int idx, uint32_t fid, uint64_t off, uint64_t bytes, uint64_t t_ns);
   void polled_empty(int idx, uint64_t idle_ns);
   void took_request(int idx);

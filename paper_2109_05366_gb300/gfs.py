@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-RDONLY, RDWR = 0, 2
+RDONLY, RDWR, DIRECT = 0, 2, 0x100
 MODE_READAHEAD, MODE_ONDEMAND, MODE_PAPER = 0, 1, 2
 REPL_FIFO, REPL_TB_LRA = 0, 1
 ADV_NORMAL, ADV_SEQUENTIAL, ADV_RANDOM = 0, 1, 2

@@ -314,6 +314,58 @@ def test_mapped_transfer_skips_files_not_in_the_host_page_cache(torch_cuda, gfs,
         assert ctx.fstat(ctx.open(full)).mapped == 1
 
 
+@pytest.mark.parametrize("xfer", XFERS)
+def test_direct_io_reads_from_storage_exact(torch_cuda, gfs, tmp_path, xfer):
+    """GFS_DIRECT: the host I/O threads read with O_DIRECT (cold reads from storage, as the
+    paper's runs after flushing the page cache); the file is never mapped, ragged ends
+    (sizes and reads not multiples of 4 KiB) are exact."""
+    path = str(tmp_path / "direct.bin")
+    size = 24 * MiB + 4321
+    inputs.write_file(path, 15, size)
+    fd = os.open(path, os.O_RDONLY)
+    os.fsync(fd)
+    os.close(fd)
+    with gfs.Context(cache_bytes=8 * MiB, page_size=256 * KiB, xfer=xfer, max_rpc_pages=16) as ctx:
+        try:
+            fid = ctx.open(path, gfs.RDONLY | gfs.DIRECT)
+        except gfs.GfsError as e:
+            pytest.skip("no O_DIRECT on this file system (%s)" % e)
+        assert ctx.fstat(fid).mapped == 0
+        for stride in (MiB, 300 * KiB + 7):
+            ctx.reset_cache()
+            out = ctx.scan(fid, stride, blocks=16, threads=256)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, stride, *out)
+            st = ctx.stats()
+            assert st["host_preads"] > 0 and st["timeouts"] == 0 and st["eio"] == 0
+
+
+@pytest.mark.parametrize("xfer", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_merged_host_reads_exact(torch_cuda, gfs, datadir, xfer, mode):
+    """Host threads that pread (dma, pull) serve requests waiting behind their own that
+    continue the same file range with one read; with two host threads and 64 KiB pages
+    requests back up, so merging happens; every stride stays exact, and each page is
+    still fetched once while the file fits."""
+    size = 48 * MiB + 777
+    path = _file(datadir, 16, size)
+    npages = (size + 64 * KiB - 1) // (64 * KiB)
+    for merge in (0, 1):
+        with gfs.Context(cache_bytes=64 * MiB, page_size=64 * KiB, xfer=xfer, mode=mode, host_threads=2,
+                         max_rpc_pages=16, rpc_slots=256, host_merge_pages=merge, debug_counts=1) as ctx:
+            fid = ctx.open(path)
+            out = ctx.scan(fid, MiB, blocks=96, threads=256)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            assert st["timeouts"] == 0 and st["eio"] == 0
+            assert (ctx.fetch_counts(npages) == 1).all()
+            if merge == 1:
+                assert st["host_merged"] == 0
+            else:
+                assert st["host_merged"] > 0 and st["host_preads"] < st["host_requests"]
+
+
 def _golden(name):
     params, rows = {}, []
     for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):

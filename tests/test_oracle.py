@@ -297,6 +297,9 @@ def test_pool_range_checksums_brute_force(tmp_path):
         s = sum(data) % (1 << 64)
         h = sum(b * (off + i + 1) for i, b in enumerate(data)) % (1 << 64)
         assert pool.range_checksums(path, off, ln, procs=2, piece=P + 3) == (len(data), s, h)
+    ranges = [(path, 0, size), (path, 7, 2 * P), (path, size + 5, 9)]
+    want = [pool.range_checksums(path, o, n, procs=1) for _, o, n in ranges]
+    assert pool.many_range_checksums(ranges, procs=3, piece=P) == want
 
 
 # ---------------------------------------------------------------- policy: hand-derived traces
