@@ -23,9 +23,10 @@ LIB = os.path.join(PKG, "libgfs.so")
 DEVLIB = os.path.join(PKG, "libgfs_device.a")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gfs_kernels.cu", "gfs_serve.cu", "gfs_apps.cu", "gfs_host.cpp", "gfs_service.cpp"]
+SOURCES = ["gfs_scan_wide.cu", "gfs_scan_narrow.cu", "gfs_kernels.cu", "gfs_serve.cu", "gfs_apps.cu", "gfs_host.cpp",
+           "gfs_service.cpp"]
 DEVAPI_SOURCE = "gfs_devapi.cu"  # relocatable device code: libgfs_device.a
-HEADERS = ["gfs_internal.h", "gfs_device.cuh", "gfs_host.h", "gfs_service.h", "gfs_serve.h"]
+HEADERS = ["gfs_internal.h", "gfs_device.cuh", "gfs_scan.cuh", "gfs_host.h", "gfs_service.h", "gfs_serve.h"]
 
 
 def _nvcc() -> str:
@@ -49,7 +50,8 @@ def _digest() -> str:
 
 # The sources the stride-scan kernel is compiled from (its device code); profiles
 # taken on one build stay valid while these are unchanged.
-KERNEL_SOURCES = ["gfs_kernels.cu", "gfs_device.cuh", "gfs_internal.h"]
+KERNEL_SOURCES = ["gfs_scan.cuh", "gfs_scan_wide.cu", "gfs_scan_narrow.cu", "gfs_kernels.cu", "gfs_device.cuh",
+                  "gfs_internal.h"]
 
 
 def _code_only(text: bytes) -> bytes:

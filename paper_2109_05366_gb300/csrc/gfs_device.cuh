@@ -107,6 +107,14 @@ __device__ __forceinline__ void st_sys64(unsigned long long* p, unsigned long lo
   asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Four consecutive table entries (32 bytes, 32-byte aligned), one load.
+__device__ __forceinline__ void ld_rlx_v4(const unsigned long long* p, unsigned long long* v) {
+  asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3])
+               : "l"(p)
+               : "memory");
+}
+
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int bcast(int v) { return __shfl_sync(kFull, v, 0); }
 __device__ __forceinline__ unsigned long long bcast64(unsigned long long v) { return __shfl_sync(kFull, v, 0); }
@@ -284,6 +292,111 @@ static __device__ void tab_remove(const DevHandle& g, unsigned long long key, ui
   __syncwarp();
 }
 
+// ---------------------------------------------------------------- lane-level table updates
+// One lane, one key: the counterparts of tab_remove and tab_insert for the pages
+// of a run, which update the table a lane per page instead of one page at a
+// time.  A lane reads a whole bucket with eight 32-byte loads.  A lane holds at
+// most one bucket lock at a time (lanes whose keys share a home bucket take it
+// in turn, and independent thread scheduling lets the holder go on), so no two
+// lanes or warps ever wait on each other in a cycle.
+
+// One lane's view of bucket b: the first entry for `key` (hit, its slot, -1 if
+// none) and the first empty slot (-1 if none).
+struct LaneScan {
+  int hit, empty;
+  unsigned long long entry;
+};
+static __device__ __noinline__ LaneScan lane_scan(const DevHandle& g, uint32_t b, unsigned long long key) {
+  const unsigned long long* base = &g.tab[(size_t)b * BUCKET];
+  LaneScan r{-1, -1, 0ull};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // two halves of 16 slots, four loads in flight each
+    unsigned long long v[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ld_rlx_v4(base + 16 * h + 4 * q, v + 4 * q);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const unsigned long long e = v[i];
+      if (r.hit < 0 && e != ENTRY_EMPTY && (e >> FRAME_BITS) == key) {
+        r.hit = 16 * h + i;
+        r.entry = e;
+      }
+      if (r.empty < 0 && e == ENTRY_EMPTY) r.empty = 16 * h + i;
+    }
+  }
+  return r;
+}
+
+// Remove the mapping key -> f if present (one lane).  No lock: the entry's value
+// is unique to (key, frame), so one compare-and-swap on its slot removes exactly
+// it, and an insert holding the bucket's lock only ever fills empty slots.
+static __device__ void lane_tab_remove(const DevHandle& g, unsigned long long key, uint32_t f) {
+  const unsigned long long entry = (key << FRAME_BITS) | f;
+  uint32_t b = bucket_of(key, g.nbuckets);
+  for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {
+    const LaneScan r = lane_scan(g, b, key);
+    if (r.hit >= 0 && r.entry == entry) {
+      atomicCAS(&g.tab[(size_t)b * BUCKET + r.hit], entry, ENTRY_EMPTY);
+      return;
+    }
+    if (r.hit >= 0) {  // another mapping of the key first: look at every slot of the bucket
+      for (uint32_t i = 0; i < BUCKET; ++i)
+        if (ld_rlx64(&g.tab[(size_t)b * BUCKET + i]) == entry) {
+          atomicCAS(&g.tab[(size_t)b * BUCKET + i], entry, ENTRY_EMPTY);
+          return;
+        }
+    }
+    if (ld_rlx(&g.tovf[b]) == 0u) return;
+    b = (b + 1) & (g.nbuckets - 1);
+  }
+}
+
+// Map key -> f unless key is already mapped (one lane; tab_insert's rule under
+// the home bucket's lock).  Returns the frame now mapped for the key (f if this
+// call inserted it), -ETIMEDOUT or -ENOMEM.
+static __device__ __noinline__ int lane_tab_insert(const DevHandle& g, unsigned long long key, uint32_t f,
+                                                   unsigned long long deadline) {
+  const uint32_t home = bucket_of(key, g.nbuckets);
+  if (!bucket_lock(g, home, deadline)) return -kETIMEDOUT;
+  int result = -kENOMEM;
+  int first_b = -1, first_i = -1;  // the first empty slot from the home bucket on
+  uint32_t b = home;
+  for (uint32_t probe = 0; probe < g.nbuckets; ++probe) {  // already present?
+    const LaneScan r = lane_scan(g, b, key);
+    if (r.hit >= 0) {
+      result = (int)(r.entry & MAX_FRAMES);
+      break;
+    }
+    if (first_b < 0 && r.empty >= 0) {
+      first_b = (int)b;
+      first_i = r.empty;
+    }
+    if (ld_rlx(&g.tovf[b]) == 0u) break;
+    b = (b + 1) & (g.nbuckets - 1);
+  }
+  if (result < 0) {
+    const unsigned long long entry = (key << FRAME_BITS) | f;
+    // an insert under another home's lock may fill an empty slot of an overflow
+    // bucket first: a failed CAS moves on to the next empty slot
+    if (first_b >= 0 && atomicCAS(&g.tab[(size_t)first_b * BUCKET + first_i], ENTRY_EMPTY, entry) == ENTRY_EMPTY)
+      result = (int)f;
+    b = home;
+    for (uint32_t probe = 0; probe < g.nbuckets && result < 0; ++probe) {
+      for (uint32_t i = 0; i < BUCKET && result < 0; ++i) {
+        unsigned long long* slot = &g.tab[(size_t)b * BUCKET + i];
+        if (ld_rlx64(slot) == ENTRY_EMPTY && atomicCAS(slot, ENTRY_EMPTY, entry) == ENTRY_EMPTY) result = (int)f;
+      }
+      if (result < 0) {  // bucket full: later lookups must continue past it
+        atomicExch(&g.tovf[b], 1u);
+        __threadfence();
+        b = (b + 1) & (g.nbuckets - 1);
+      }
+    }
+  }
+  bucket_unlock(g, home);
+  return result;
+}
+
 // ---------------------------------------------------------------- consumed FIFO
 // Bounded MPMC queue over fifo_cap cells; each frame is in it at most once.  Cell
 // t % cap holds (seq << FRAME_BITS) | frame: seq = t while free for the push of
@@ -419,6 +532,54 @@ static __device__ void evict_key(const DevHandle& g, int f, unsigned long long n
         r.reserved = 0;
         r.old_page = key_page(old);
         r.new_page = key_page(new_key);
+        g.trace_evict[i] = r;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Warp: unmap the old pages of the n claimed frames[0 .. n) and record the
+// evictions, a lane per frame; frame j is about to hold page q0 + j of fid.  The
+// eviction records keep frame order (one ticket add per 32 frames), so a run
+// records exactly what one evict_key per frame, in order, would.
+static __device__ void evict_run(const DevHandle& g, const uint32_t* frames, uint32_t n, uint32_t fid,
+                                 unsigned long long q0) {
+  const int lane = lane_id();
+  for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+    const uint32_t j = j0 + (uint32_t)lane;
+    unsigned long long old = KEY_NONE;
+    uint32_t f = 0, consumed = 0, valid = 0;
+    if (j < n) {
+      f = frames[j];
+      old = ld_rlx64(&g.fkey[f]);
+      consumed = ld_rlx(&g.fconsumed[f]);
+      valid = ld_rlx(&g.fvalid[f]);
+    }
+    const bool has = j < n && old != KEY_NONE;
+    if (has) {
+      lane_tab_remove(g, old, f);
+      st_rlx64(&g.fkey[f], KEY_NONE);
+    }
+    const unsigned hm = __ballot_sync(kFull, has);
+    const unsigned um = __ballot_sync(kFull, has && (consumed < valid || valid == 0));
+    if (lane == 0) {
+      stat_add(g, ST_EVICT, (unsigned long long)__popc(hm));
+      stat_add(g, ST_EVICT_UNCONSUMED, (unsigned long long)__popc(um));
+    }
+    if (g.trace_cap && hm) {
+      unsigned long long t0 = 0;
+      if (lane == 0) t0 = atomicAdd(&g.ctrl->trace_evict_n.v, (unsigned long long)__popc(hm));
+      t0 = bcast64(t0);
+      const unsigned long long i = t0 + (unsigned long long)__popc(hm & ((1u << lane) - 1u));
+      if (has && i < g.trace_cap) {
+        gfs_evict_rec r;
+        r.frame = f;
+        r.old_fid = key_fid(old);
+        r.new_fid = fid;
+        r.reserved = 0;
+        r.old_page = key_page(old);
+        r.new_page = key_page(make_key(fid, q0 + j));
         g.trace_evict[i] = r;
       }
     }
@@ -990,6 +1151,11 @@ static __device__ uint32_t take_run(const DevHandle& g, uint32_t L, uint32_t dem
   return got;
 }
 
+static __device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p,
+                                     uint32_t n, uint32_t demand, uint32_t window, uint32_t kind,
+                                     unsigned long long mark_end, int mark_idx, const uint32_t* s_frames,
+                                     unsigned long long deadline);
+
 // Warp: pages 1 .. of a request whose page 0 is installed (page i is p + i, a
 // readahead page when i >= demand).  The run is cut, as one page at a time would
 // cut it, at EOF, at the first page already in the table and at the first
@@ -1024,7 +1190,7 @@ static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const F
   }
   L = take_run(g, L, demand, deadline, s_frames);
   if (L == 0) return 0;
-  for (uint32_t j = 1; j <= L; ++j) evict_key(g, (int)s_frames[j], make_key(fid, p + j), deadline);
+  evict_run(g, s_frames + 1, L, fid, p + 1);
   unsigned long long a0 = 0;
   if (lane == 0) a0 = atomicAdd(&g.ctrl->alloc_counter.v, (unsigned long long)L);
   a0 = bcast64(a0);
@@ -1042,23 +1208,47 @@ static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const F
   __threadfence();
   for (uint32_t j = 1 + (uint32_t)lane; j <= L; j += 32) st_rel(&g.fstate[s_frames[j]], FR_FILLING);
   __syncwarp();
-  for (uint32_t j = 1; j <= L; ++j) {
-    const uint32_t f = s_frames[j];
-    const int r = tab_insert(g, make_key(fid, p + j), f, deadline);
-    if (r != (int)f) {  // inserted by someone else meanwhile: this frame and the rest go back
-      if (lane == 0)
-        for (uint32_t jj = j; jj <= L; ++jj) frame_return(g, (int)s_frames[jj], false, deadline);
-      __syncwarp();
-      L = j - 1;
-      break;
+  // the table entries, a lane per page; a page another gread mapped meanwhile
+  // (its insert finds the key) cuts the request there and its frame goes back
+  uint32_t cut = L + 1;  // the first page, from 1 on, whose insert failed
+  for (uint32_t j0 = 1; j0 <= L; j0 += 32) {
+    const uint32_t j = j0 + (uint32_t)lane;
+    bool ok = true;
+    if (j <= L) {
+      const uint32_t f = s_frames[j];
+      ok = lane_tab_insert(g, make_key(fid, p + j), f, deadline) == (int)f;
+      if (!ok) frame_return(g, (int)f, false, deadline);  // never reachable: not in the table
+      else {
+        const unsigned long long q = p + j;
+        if (fi.fetched) atomicOr(&fi.fetched[q >> 5], 1u << (q & 31));
+        if (g.fetch_count && fid == 0 && q < g.debug_pages) atomicAdd(&g.fetch_count[q], 1u);
+      }
     }
-  }
-  for (uint32_t j = 1 + (uint32_t)lane; j <= L; j += 32) {
-    const unsigned long long q = p + j;
-    if (fi.fetched) atomicOr(&fi.fetched[q >> 5], 1u << (q & 31));
-    if (g.fetch_count && fid == 0 && q < g.debug_pages) atomicAdd(&g.fetch_count[q], 1u);
+    const unsigned bad = __ballot_sync(kFull, !ok);
+    if (bad && cut > L) cut = j0 + (uint32_t)(__ffs(bad) - 1);
+    if (j <= L && !ok) s_frames[j] |= 0x80000000u;  // marks the page as not mapped
   }
   __syncwarp();
+  if (cut <= L) {
+    // Pages after the cut that did go into the table are mapped and FILLING:
+    // readers may already wait for them, so each maximal run of them is requested
+    // on its own (only concurrent greads race like this; one gread at a time never does).
+    uint32_t a = cut + 1;
+    while (a <= L) {
+      if (s_frames[a] & 0x80000000u) {
+        ++a;
+        continue;
+      }
+      uint32_t e = a;
+      while (e + 1 <= L && !(s_frames[e + 1] & 0x80000000u)) ++e;
+      const uint32_t n = e - a + 1;
+      const uint32_t kind = a < demand ? (uint32_t)GFS_KIND_DEMAND
+                                       : (demand == 0 ? (uint32_t)GFS_KIND_ASYNC_RA : (uint32_t)GFS_KIND_SYNC_RA);
+      finish_request(g, fid, fi, p + a, n, a < demand ? demand - a : 0u, n, kind, 0, -1, s_frames + a, deadline);
+      a = e + 1;
+    }
+    L = cut - 1;
+  }
   return L;
 }
 

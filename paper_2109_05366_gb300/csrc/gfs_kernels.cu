@@ -1,107 +1,18 @@
-// Kernels of the GPU file-read path: the stride scan (Section 6.1 microbenchmark
-// shape: block b greads strides b, b+B, ... and checksums each), independent
-// greads, cache reset, and the checksum kernel of the CPU-I/O baseline.
+// Kernels of the GPU file-read path: independent greads, the scan with the file
+// opened on the device, cache purge, drain and reset, the checksum kernel of the
+// CPU-I/O baseline, the link probe, and the launch of the stride scan (whose
+// instances are compiled in gfs_scan_wide.cu and gfs_scan_narrow.cu).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <errno.h>
 
 #include <mutex>
 
-#include "gfs_device.cuh"
-#include "gfs_host.h"
+#include "gfs_scan.cuh"
 
 namespace gfs {
 
-using dev::Sums;
-
-// Checksums of n bytes at p (file offset `off` of p[0]); p is 16-byte aligned.
-__device__ __forceinline__ void checksum_range(const uint8_t* __restrict__ p, unsigned long long n,
-                                               unsigned long long off, Sums& acc) {
-  const uint32_t tid = threadIdx.x, nt = blockDim.x;
-  const unsigned long long n16 = n >> 4;
-  const uint4* p4 = reinterpret_cast<const uint4*>(p);
-  unsigned long long i = tid;
-  for (; i + 3 * nt < n16; i += 4 * nt) {
-    uint4 a = p4[i], b = p4[i + nt], c = p4[i + 2 * nt], d = p4[i + 3 * nt];
-    dev::sums_add16(acc, a, off + 16 * i);
-    dev::sums_add16(acc, b, off + 16 * (i + nt));
-    dev::sums_add16(acc, c, off + 16 * (i + 2 * nt));
-    dev::sums_add16(acc, d, off + 16 * (i + 3 * nt));
-  }
-  for (; i < n16; i += nt) dev::sums_add16(acc, p4[i], off + 16 * i);
-  for (unsigned long long j = 16 * n16 + tid; j < n; j += nt) dev::sums_add1(acc, p[j], off + j);
-}
-
-// Serialized mode: wait (helping in pull mode) until no frame is being filled.
-__device__ void block_quiesce(const DevHandle& g) {
-  const unsigned long long dl = dev::now_ns() + g.timeout_ns;
-  __shared__ int s_late;
-  for (;;) {
-    bool busy = false;
-    for (uint32_t f = threadIdx.x; f < g.n_frames && !busy; f += blockDim.x) {
-      const uint32_t st = dev::ld_acq(&g.fstate[f]);
-      busy = st == FR_FILLING || st == FR_COPYING;
-    }
-    if (threadIdx.x == 0) s_late = dev::now_ns() > dl;
-    const int any_busy = __syncthreads_or(busy);
-    const int late = s_late;
-    __syncthreads();
-    if (!any_busy || late) break;
-    if (g.xfer != GFS_XFER_DMA && dev::block_help(g, -1, true)) continue;
-    if (threadIdx.x == 0) __nanosleep(256);
-  }
-  __syncthreads();
-}
-
-// Pull mode, before a block exits: copy out served requests nobody waits for
-// (asynchronous readahead at the end of a scan) so their ring slots free up.
-__device__ void block_help_drain(const DevHandle& g) {
-  if (g.xfer == GFS_XFER_DMA) return;
-  for (int i = 0; i < 4096; ++i)
-    if (!dev::block_help(g, -1, true)) break;
-}
-
-template <bool FUSED>
-__global__ void __launch_bounds__(512) k_scan(DevHandle g, int fid, unsigned long long stride,
-                                               unsigned long long read_len, unsigned long long nstrides, int serialize,
-                                               uint8_t* bufs, unsigned long long buf_stride, long long* cnt,
-                                               unsigned long long* sum, unsigned long long* hash) {
-  const uint32_t b = blockIdx.x, tid = threadIdx.x;
-  uint8_t* buf = bufs + (size_t)b * buf_stride;
-  for (unsigned long long s = b; s < nstrides; s += gridDim.x) {
-    const unsigned long long off = s * stride;
-    if (serialize) {  // one gread at a time, in stride order
-      if (tid == 0) {
-        const unsigned long long dl = dev::now_ns() + g.timeout_ns;
-        while (dev::ld_acq64(&g.ctrl->ticket.v) != s) {
-          if (dev::now_ns() > dl) {
-            dev::stat_add(g, ST_TIMEOUTS, 1);
-            break;
-          }
-          __nanosleep(128);
-        }
-      }
-      __syncthreads();
-    }
-    Sums acc{0ull, 0ull};
-    long long r = dev::gread_impl<FUSED>(g, (int)b, fid, off, read_len, buf, acc);
-    if (serialize) {  // wait until every request of this gread has been served
-      block_quiesce(g);
-      if (tid == 0) dev::st_rel64(&g.ctrl->ticket.v, s + 1);
-    }
-    if (!FUSED && r > 0) checksum_range(buf, (unsigned long long)r, off, acc);
-    dev::block_sum2(acc.sum, acc.hash);
-    if (tid == 0) {
-      cnt[s] = r;
-      sum[s] = r > 0 ? acc.sum : 0ull;
-      hash[s] = r > 0 ? acc.hash : 0ull;
-    }
-    __syncthreads();
-  }
-  block_help_drain(g);
-}
-
-__global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_t n, const uint64_t* off,
+__global__ void __launch_bounds__(512, 1) k_read_many(DevHandle g, int fid, uint32_t n, const uint64_t* off,
                                                     const uint64_t* len, const uint64_t* dst, uint8_t* buf,
                                                     long long* ret) {
   for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
@@ -116,7 +27,7 @@ __global__ void __launch_bounds__(512) k_read_many(DevHandle g, int fid, uint32_
 // open, read and close files through GPUfs calls): every block gopens `path`,
 // reads its strides with the fused checksum, and gcloses.  A block whose gopen
 // fails reports the error for each of its strides.
-__global__ void __launch_bounds__(512) k_scan_path(DevHandle g, const __grid_constant__ PathArg path,
+__global__ void __launch_bounds__(512, 1) k_scan_path(DevHandle g, const __grid_constant__ PathArg path,
                                                     unsigned long long stride,
                                                     unsigned long long read_len, unsigned long long nstrides,
                                                     uint8_t* bufs, unsigned long long buf_stride, long long* cnt,
@@ -253,16 +164,27 @@ int launch_drain(const DevHandle& g, cudaStream_t s) {
   return cuda_err(cudaGetLastError());
 }
 
+// Which instance a launch uses: 0 = <512, 1> (512 threads, or at most two
+// blocks per SM); 1 = <256, 4> (256 threads or fewer, more blocks).
+static int scan_variant(uint32_t threads, uint32_t blocks, int device) {
+  static int sms[64] = {};
+  if (threads > 256) return 0;
+  int n = device >= 0 && device < 64 ? sms[device] : 0;
+  if (n == 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) return 1;
+    if (device >= 0 && device < 64) sms[device] = n;
+  }
+  return blocks <= 2u * (uint32_t)n ? 0 : 1;
+}
+
 int launch_scan(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
                 uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s) {
-  if (a.fused)
-    k_scan<true><<<a.blocks, a.threads, 0, s>>>(g, fid, a.stride, a.read_len, nstrides, (int)a.serialize, bufs,
-                                                buf_stride, (long long*)d_count, (unsigned long long*)d_sum,
-                                                (unsigned long long*)d_hash);
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return -19;
+  if (scan_variant(a.threads, a.blocks, device) == 0)
+    launch_scan_wide(g, fid, a, nstrides, bufs, buf_stride, d_count, d_sum, d_hash, s);
   else
-    k_scan<false><<<a.blocks, a.threads, 0, s>>>(g, fid, a.stride, a.read_len, nstrides, (int)a.serialize, bufs,
-                                                 buf_stride, (long long*)d_count, (unsigned long long*)d_sum,
-                                                 (unsigned long long*)d_hash);
+    launch_scan_narrow(g, fid, a, nstrides, bufs, buf_stride, d_count, d_sum, d_hash, s);
   return cuda_err(cudaGetLastError());
 }
 
@@ -304,12 +226,19 @@ int launch_pull_probe(const uint8_t* src, uint8_t* dst, uint64_t n, cudaStream_t
 
 int scan_max_resident_blocks(uint32_t threads, bool fused, int device, int* out) {
   int per_sm = 0, sms = 0;
-  cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<true>, (int)threads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<false>, (int)threads, 0);
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return cuda_err(e);
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  // the largest grid that is resident at once with the instance launch_scan picks for it
+  e = scan_occupancy_wide(fused, (int)threads, &per_sm);
   if (e != cudaSuccess) return cuda_err(e);
-  *out = per_sm * sms;
+  int best = per_sm * sms;
+  if (threads <= 256) {
+    if (best > 2 * sms) best = 2 * sms;  // larger grids use <256, 4>
+    e = scan_occupancy_narrow(fused, (int)threads, &per_sm);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (per_sm * sms > best) best = per_sm * sms;
+  }
+  *out = best;
   return 0;
 }
 

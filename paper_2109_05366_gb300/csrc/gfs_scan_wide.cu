@@ -1,0 +1,17 @@
+// The stride-scan kernel instance <512, 1>: 512-thread blocks, or grids of at most two blocks per SM.
+#include "gfs_scan.cuh"
+
+namespace gfs {
+
+void launch_scan_wide(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
+                    uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s) {
+  if (a.fused) launch_scan_as<true, 512, 1>(g, fid, a, nstrides, bufs, buf_stride, d_count, d_sum, d_hash, s);
+  else launch_scan_as<false, 512, 1>(g, fid, a, nstrides, bufs, buf_stride, d_count, d_sum, d_hash, s);
+}
+
+cudaError_t scan_occupancy_wide(bool fused, int threads, int* per_sm) {
+  return fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_scan<true, 512, 1>, threads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_scan<false, 512, 1>, threads, 0);
+}
+
+}  // namespace gfs

@@ -429,31 +429,34 @@ void IoService::run_static(Worker& w) {
 
 int IoService::gather(Worker& w, uint32_t fid, Req* group, uint32_t max_pages_each) {
   if (cfg_.queue != GFS_QUEUE_SHARED || cfg_.merge_pages <= 1) return 1;
-  int ng = 1;
-  uint64_t total = group[0].npages;
-  uint64_t next = group[0].page_lo + group[0].npages;
-  while (ng < kMaxGroup && total < cfg_.merge_pages) {
-    const uint64_t h2 = group[ng - 1].ticket + 1;
-    RingSlot* s2 = (RingSlot*)(cfg_.ring + (size_t)(h2 % cfg_.slots) * cfg_.slot_stride);
-    if (__atomic_load_n(&s2->seq, __ATOMIC_ACQUIRE) != h2 + 1) break;  // not published (yet)
-    // Read before claiming: while no thread has taken ticket h2 the slot keeps its
+  // The requests waiting at the head of the ring: published, not drawn by any
+  // thread (idle threads draw tickets before they are published, so a waiting
+  // request means every thread is busy), reads of the same file.
+  const uint64_t u = head_.load(std::memory_order_acquire);
+  uint64_t pages = group[0].npages;
+  int k = 0;
+  while (1 + k < kMaxGroup) {
+    const uint64_t t = u + (uint64_t)k;
+    RingSlot* st = (RingSlot*)(cfg_.ring + (size_t)(t % cfg_.slots) * cfg_.slot_stride);
+    if (__atomic_load_n(&st->seq, __ATOMIC_ACQUIRE) != t + 1) break;  // not published (yet)
+    // Read before claiming: while no thread has drawn ticket t its slot keeps its
     // request; if one has, the claim below fails and what was read is dropped.
-    const volatile RingSlot* v2 = s2;
-    const uint32_t op = v2->op, f2 = v2->fid, n2 = v2->npages;
-    const uint64_t lo2 = v2->page_lo;
-    if (op != OP_READ || f2 != fid || lo2 != next || n2 == 0 || n2 > max_pages_each ||
-        total + n2 > cfg_.merge_pages)
-      break;
-    uint64_t expect = h2;
-    if (!head_.compare_exchange_strong(expect, h2 + 1, std::memory_order_acq_rel)) break;  // taken meanwhile
+    const volatile RingSlot* vt = st;
+    const uint32_t op = vt->op, f2 = vt->fid, n2 = vt->npages;
+    const uint64_t lo2 = vt->page_lo;
+    if (op != OP_READ || f2 != fid || n2 == 0 || n2 > max_pages_each || pages + n2 > cfg_.merge_pages) break;
+    group[1 + k] = Req{t, (uint32_t)(t % cfg_.slots), n2, lo2};
+    pages += n2;
+    ++k;
+  }
+  if (k == 0) return 1;
+  uint64_t expect = u;
+  if (!head_.compare_exchange_strong(expect, u + (uint64_t)k, std::memory_order_acq_rel)) return 1;  // drawn meanwhile
+  for (int i = 0; i < k; ++i) {
     took_request(w.idx);
     stats.requests.fetch_add(1, std::memory_order_relaxed);
-    stats.merged.fetch_add(1, std::memory_order_relaxed);
-    group[ng++] = Req{h2, (uint32_t)(h2 % cfg_.slots), n2, lo2};
-    total += n2;
-    next += n2;
   }
-  return ng;
+  return 1 + k;
 }
 
 void IoService::handle(Worker& w, uint64_t h, RingSlot* s) {
@@ -473,9 +476,30 @@ void IoService::handle(Worker& w, uint64_t h, RingSlot* s) {
   const uint32_t max_each = cfg_.pull_arena ? cfg_.max_pages : MAX_RPC_PAGES;
   Req group[kMaxGroup];
   group[0] = Req{h, (uint32_t)(h % cfg_.slots), std::min(npages, max_each), page_lo};
-  const int ng = (npages >= 1 && npages <= max_each) ? gather(w, fid, group, max_each) : 1;
+  FileView fv{-1, 0, 0, false};
+  // a mapped file has no host read to share: its requests are served one by one
+  const bool mergeable = npages >= 1 && npages <= max_each && files_(fid, &fv) && !fv.dev_map;
+  const int ng = mergeable ? gather(w, fid, group, max_each) : 1;
+  // in file order; each maximal run of requests whose pages continue one another is
+  // served with one host read per staging buffer
+  std::sort(group, group + ng, [](const Req& a, const Req& b) {
+    return a.page_lo != b.page_lo ? a.page_lo < b.page_lo : a.ticket < b.ticket;
+  });
+  auto for_runs = [&](auto&& serve_run) {
+    for (int i = 0; i < ng;) {
+      int j = i + 1;
+      while (j < ng && group[j].npages && group[j - 1].npages &&
+             group[j - 1].page_lo + group[j - 1].npages == group[j].page_lo)
+        ++j;
+      if (group[i].npages) {
+        if (j - i > 1) stats.merged.fetch_add((uint64_t)(j - i - 1), std::memory_order_relaxed);
+        serve_run(i, j);
+      }
+      i = j;
+    }
+  };
   if (cfg_.pull_arena) {  // the GPU frees the slots once it has copied the pages
-    serve_pull(w, fid, group, ng);
+    for_runs([&](int i, int j) { serve_pull(w, fid, group + i, j - i); });
     served_.fetch_add((uint64_t)ng, std::memory_order_release);
     return;
   }
@@ -484,21 +508,38 @@ void IoService::handle(Worker& w, uint64_t h, RingSlot* s) {
   for (int k = 0; k < ng; ++k) total += group[k].npages;
   if (w.frames.size() < total) w.frames.resize(total);
   uint32_t* frames = w.frames.data();
-  bool bad = npages == 0 || npages > MAX_RPC_PAGES;
-  uint64_t at = 0;
+  uint64_t at[kMaxGroup];
+  uint64_t pos = 0;
   for (int k = 0; k < ng; ++k) {
     RingSlot* sk = (RingSlot*)(cfg_.ring + (size_t)group[k].slot * cfg_.slot_stride);
     const volatile RingSlot* vk = sk;
-    for (uint32_t i = 0; i < group[k].npages; ++i) frames[at + i] = vk->frames[i];
+    const uint32_t nk = group[k].npages;
+    bool bad = nk == 0 || (group[k].ticket == h && (npages == 0 || npages > MAX_RPC_PAGES));
+    for (uint32_t i = 0; i < nk; ++i) frames[pos + i] = vk->frames[i];
     __atomic_store_n(&sk->seq, group[k].ticket + cfg_.slots, __ATOMIC_RELEASE);  // slot free for the next lap
-    for (uint32_t i = 0; i < group[k].npages && !bad; ++i) bad = frames[at + i] >= cfg_.n_frames;
-    at += group[k].npages;
+    for (uint32_t i = 0; i < nk && !bad; ++i) bad = frames[pos + i] >= cfg_.n_frames;
+    if (bad) {
+      stats.errors.fetch_add(1, std::memory_order_relaxed);
+      group[k].npages = 0;  // not served: its pages stay FILLING until the device deadline
+    }
+    at[k] = pos;
+    pos += nk;
   }
-  if (bad) {
-    stats.errors.fetch_add(1, std::memory_order_relaxed);
-  } else {
-    serve(w, fid, page_lo, (uint32_t)total, frames);
-  }
+  for_runs([&](int i, int j) {
+    // the run's frame lists, in page order (its requests are consecutive in `frames` only
+    // when no bad request sits between them, which for_runs guarantees)
+    uint32_t n = 0;
+    for (int k = i; k < j; ++k) n += group[k].npages;
+    if (j - i == 1) {
+      serve(w, fid, group[i].page_lo, n, frames + at[i]);
+      return;
+    }
+    if (w.run.size() < n) w.run.resize(n);
+    uint32_t q = 0;
+    for (int k = i; k < j; ++k)
+      for (uint32_t x = 0; x < group[k].npages; ++x) w.run[q++] = frames[at[k] + x];
+    serve(w, fid, group[i].page_lo, n, w.run.data());
+  });
   served_.fetch_add((uint64_t)ng, std::memory_order_release);
 }
 

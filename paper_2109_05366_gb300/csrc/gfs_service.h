@@ -67,9 +67,10 @@ struct ServiceConfig {
   // device opens: per-slot path buffers (host view), GFS_PATH_MAX bytes each
   const char* paths = nullptr;
   uint32_t queue = GFS_QUEUE_SHARED;  // GFS_QUEUE_*: how a thread finds its requests
-  // GFS_QUEUE_SHARED: a thread that takes a read also takes the next published,
-  // not yet taken tickets that continue the same file range, up to this many
-  // pages in all, and serves them with one read (<= 1: one request at a time)
+  // GFS_QUEUE_SHARED: a thread that takes a read also claims the requests waiting
+  // at the head of the ring (published, drawn by no thread) that read the same
+  // file, up to this many pages in all, and serves each run of them whose pages
+  // continue one another with one read (<= 1: one request at a time)
   uint32_t merge_pages = 1;
   uint64_t io_trace_cap = 0;          // host I/O trace entries kept (0 = off)
   // at t % cancel_n: t + 1 for a ticket t its producer gave up (skipped once the slot
@@ -130,6 +131,7 @@ class IoService {
     int cur;
     uint32_t pull_cur;
     std::vector<uint32_t> frames;  // frame lists of a merged group (copy-engine transfer)
+    std::vector<uint32_t> run;     // frame list of one run of it, in page order
     std::vector<uint8_t> full;     // per page of a staging chunk: delivered whole
   };
   // One read request of a merged group: ticket, slot, its first page and page count.
@@ -149,8 +151,8 @@ class IoService {
   // Skip ticket h if its producer gave it up and the slot is free for it.
   bool skip_cancelled(uint64_t h, RingSlot* s);
   void control(RingSlot* s, uint32_t slot, uint32_t op, uint32_t fid);
-  // Take the published tickets after group[0] that continue its file range (see
-  // merge_pages); returns the group's request count.
+  // Claim the requests waiting at the head of the ring for the same file as
+  // group[0] (see merge_pages) into group[1 ..]; returns the group's request count.
   int gather(Worker& w, uint32_t fid, Req* group, uint32_t max_pages_each);
   void serve(Worker& w, uint32_t fid, uint64_t page_lo, uint32_t npages, const uint32_t* frames);
   void serve_pull(Worker& w, uint32_t fid, const Req* group, int ng);

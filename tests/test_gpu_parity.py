@@ -343,27 +343,31 @@ def test_direct_io_reads_from_storage_exact(torch_cuda, gfs, tmp_path, xfer):
 @pytest.mark.parametrize("xfer", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_merged_host_reads_exact(torch_cuda, gfs, datadir, xfer, mode):
-    """Host threads that pread (dma, pull) serve requests waiting behind their own that
-    continue the same file range with one read; with two host threads and 64 KiB pages
-    requests back up, so merging happens; every stride stays exact, and each page is
-    still fetched once while the file fits."""
+    """Host threads that pread (dma, pull) claim the requests waiting at the head of the
+    ring and serve each run of them whose pages continue one another with one read.  With
+    64 KiB strides of 64 KiB pages neighbouring blocks ask for neighbouring pages at once,
+    and two host threads let requests back up, so merging happens; every stride stays
+    exact, and each page is still fetched once while the file fits."""
     size = 48 * MiB + 777
     path = _file(datadir, 16, size)
-    npages = (size + 64 * KiB - 1) // (64 * KiB)
+    page = 64 * KiB
+    npages = (size + page - 1) // page
     for merge in (0, 1):
-        with gfs.Context(cache_bytes=64 * MiB, page_size=64 * KiB, xfer=xfer, mode=mode, host_threads=2,
+        with gfs.Context(cache_bytes=64 * MiB, page_size=page, xfer=xfer, mode=mode, host_threads=2,
                          max_rpc_pages=16, rpc_slots=256, host_merge_pages=merge, debug_counts=1) as ctx:
             fid = ctx.open(path)
-            out = ctx.scan(fid, MiB, blocks=96, threads=256)
-            torch_cuda.cuda.synchronize()
-            _check_scan(gfs, path, MiB, *out)
-            st = ctx.stats()
-            assert st["timeouts"] == 0 and st["eio"] == 0
-            assert (ctx.fetch_counts(npages) == 1).all()
-            if merge == 1:
-                assert st["host_merged"] == 0
-            else:
-                assert st["host_merged"] > 0 and st["host_preads"] < st["host_requests"]
+            for stride in (page, MiB):
+                ctx.reset_cache()
+                out = ctx.scan(fid, stride, blocks=128, threads=256)
+                torch_cuda.cuda.synchronize()
+                _check_scan(gfs, path, stride, *out)
+                st = ctx.stats()
+                assert st["timeouts"] == 0 and st["eio"] == 0
+                assert (ctx.fetch_counts(npages) == 1).all()
+                if merge == 1:
+                    assert st["host_merged"] == 0
+                elif stride == page:
+                    assert st["host_merged"] > 0 and st["host_preads"] < st["host_requests"]
 
 
 def _golden(name):

@@ -9,10 +9,11 @@ finds its ticket cancelled and its slot free for it clears the cancellation and 
 the slot for the next lap.  A served request's slot is freed later by whoever copies
 its pages (the GPU in the pull and mapped transfers), modelled as a separate actor.
 
-A host thread that has served a request may also take the next ticket when its request
-is already published and no host thread has drawn it yet (`IoService::gather`: it reads
-the slot's sequence word, then claims the ticket by compare-and-swap on the shared head),
-and serve both with one host read; the model explores that step too.
+A host thread that has a request may also take the ticket at the head of the ring (the
+next one no host thread has drawn) when its request is already published
+(`IoService::gather`: it reads the head, then the slot's sequence word, then claims the
+ticket by compare-and-swap on the head), and serve both with one host read; the model
+explores that step too, one claimed ticket at a time.
 
 Every step below is one access to shared state, as in the code; a producer may run out
 of time at any wait.  For every interleaving of small scenarios the test checks that
@@ -77,8 +78,10 @@ class Ring:
             if pc == "serve":  # publish the pages; their copier frees the slot later
                 nxt = ("host", "mcheck", t) if self.merge else ("host", "draw", None)
                 return [((seq, cancel, head, tail, pending | {t}, served | {t}, skipped, dup or t in served), nxt)]
-            if pc == "mcheck":  # is the next ticket's request already published?
-                return [(sh, ("host", "mclaim" if seq[(t + 1) % R] == t + 2 else "draw", t + 1))]
+            if pc == "mcheck":  # read the head: the first ticket no host thread has drawn
+                return [(sh, ("host", "mseq", head))]
+            if pc == "mseq":  # is that ticket's request already published?
+                return [(sh, ("host", "mclaim" if t < self.P and seq[t % R] == t + 1 else "draw", t))]
             if pc == "mclaim":
                 if self.merge == "cas":  # head: t -> t + 1 only if no host thread drew t meanwhile
                     if head != t:
@@ -207,10 +210,11 @@ def test_merge_claim_must_be_one_compare_and_swap():
 
 
 def test_merging_happens_in_some_schedule():
-    """With one host thread behind two published requests, the thread serves the second
-    one merged with the first (the head moves past it by the claim, not by a draw)."""
-    ring = Ring(3, cancel_n=5, tickets=2, merge="cas")
-    threads = [("prod", "draw", None)] * 2 + [("host", "draw", None)]
+    """With a host thread behind published requests no other thread has drawn, the thread
+    serves the one at the head merged with its own (the head moves past it by the claim,
+    not by a draw)."""
+    ring = Ring(3, cancel_n=5, tickets=3, merge="cas")
+    threads = [("prod", "draw", None)] * 3 + [("host", "draw", None)] * 2
     seen, edges, finals = _explore(ring, threads)
     merged = any(th[1] == "mclaim" and sh[0][th[2] % 3] == th[2] + 1 and sh[2] == th[2]
                  for sh, ths in seen for th in ths if th[0] == "host")
