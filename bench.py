@@ -789,22 +789,24 @@ def ra_vs_od_legs(args, stream):
 
 def merge_legs(args, path, stream):
     """Host reads merged across requests against one request per read, for the transfers whose
-    host threads pread (pull, dma), on the 8 GiB file: the bench's pages with readahead, and
-    64 KiB pages on demand (one page per request)."""
+    host threads pread (pull, dma), on the 8 GiB file: the bench's shape (512 KiB pages,
+    readahead, 1 MiB strides), and 64 KiB pages on demand with 64 KiB strides, where
+    neighbouring threadblocks ask for neighbouring pages at once (one page per request)."""
     from paper_2109_05366_gb300 import gfs
     size = os.path.getsize(path)
     res = {}
     for xname in ("pull", "dma"):
-        for page, mode, mname, mx in ((512 * KiB, gfs.MODE_READAHEAD, "readahead", 16),
-                                     (64 * KiB, gfs.MODE_ONDEMAND, "ondemand", 16)):
-            key = "%s_page%dKiB_%s" % (xname, page // KiB, mname)
+        for page, stride, mode, mname in ((512 * KiB, MiB, gfs.MODE_READAHEAD, "readahead"),
+                                          (64 * KiB, 64 * KiB, gfs.MODE_ONDEMAND, "ondemand")):
+            key = "%s_page%dKiB_stride%dKiB_%s" % (xname, page // KiB, stride // KiB, mname)
             entry = {}
             for label, merge in (("one_request_per_read", 1), ("merged", 0)):
-                r = scan_leg(path, MiB, 296, 2, 1, stream, cache_bytes=GiB, page_size=page, mode=mode,
-                             xfer=xfer_code(xname), ra_cap_pages=8, max_rpc_pages=mx, rpc_slots=512,
+                r = scan_leg(path, stride, 296, 2, 1, stream, cache_bytes=GiB, page_size=page, mode=mode,
+                             xfer=xfer_code(xname), ra_cap_pages=8, max_rpc_pages=16, rpc_slots=512,
                              host_merge_pages=merge)
                 r["host_preads_per_GiB"] = round(r["host_preads"] / (size / GiB), 1)
                 entry[label] = r
+            entry["merged_over_one_per_read"] = round(entry["merged"]["gbps"] / entry["one_request_per_read"]["gbps"], 3)
             res[key] = entry
     return res
 

@@ -1169,7 +1169,9 @@ static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const F
   const int lane = lane_id();
   unsigned long long lim = want - 1ull;
   if (p + 1 + lim > fi.npages) lim = fi.npages > p + 1 ? fi.npages - p - 1 : 0;
-  uint32_t L = 0;
+  // pages 1 .. demand-1 are the demand run that R2 just found absent (a page
+  // another gread maps meanwhile is caught by its insert below)
+  uint32_t L = demand > 1 ? (demand - 1 < lim ? demand - 1 : (uint32_t)lim) : 0u;
   while (L < lim) {
     const uint32_t k = lim - L < 32ull ? (uint32_t)(lim - L) : 32u;
     const uint32_t a = absent_prefix(g, fid, p + 1 + L, k);
