@@ -9,9 +9,16 @@ cache.  The file (8 GiB) is far larger than L2, so no L2 flush is needed
 between steps.
 
 Reported beside the readahead path, in the same run: the on-demand path (one
-page per request), the CPU-I/O baseline (host pread threads + cudaMemcpyAsync +
-the same checksum kernel), the host-link probes that bound the path (pinned
-H2D copy and multi-thread pread), and the CPU oracle on a bounded sample.
+page per request, the same steps), the CPU-I/O baseline (host pread threads +
+cudaMemcpyAsync + the same checksum kernel), the host-link probes that bound
+the path (pinned H2D copy, multi-thread pread, GPU reads of mapped host
+memory), the mapped transfer's registration cost, readahead against on-demand
+where requests cost something (4 KiB pages; 64 KiB pages with pread staging),
+merged against one-request-per-read host service, cold reads (page cache
+dropped, O_DIRECT), and the serving loop (Poisson and saturating arrivals).
+Last, after every GPU measurement, the CPU-baseline leg: the CPU oracle timed
+on a bounded sample, and parity -- every stride of the last timed step and
+every serving completion compared with the oracle's plain definition.
 
 `--impl reference` times the CPU oracle itself (the reference arm).
 """
@@ -149,8 +156,8 @@ def data_dir():
 # DRAM bytes per scanned file byte of k_scan, from an ncu capture of the 2 GiB
 # quarter-scale case (traffic grows with the bytes scanned), valid only while the
 # kernel's sources are those it was taken on.
-NCU_DRAM = {"kernel_digest": "5550a86d83b8ba230fa9250701d29308befd21e929ea73648f5916d39ea11802",
-            "bytes_per_file_byte": (2.968324e9 + 4.351640e9) / (2 * GiB),
+NCU_DRAM = {"kernel_digest": "985c6c6535223c9cbc9f02dc77c7f2a0e3894dd478d7fe83847d603c65bd89c6",
+            "bytes_per_file_byte": (2.905914e9 + 4.244475e9) / (2 * GiB),
             "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 2 GiB case scaled by bytes scanned"}
 
 
