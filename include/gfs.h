@@ -75,17 +75,24 @@ extern "C" {
  * and copies run concurrently. */
 #define GFS_XFER_DMA 0  /* host: pread -> pinned staging -> cudaMemcpyAsync -> stream write of the frame state */
 #define GFS_XFER_PULL 1 /* host: pread -> pinned staging; GPU copies staging -> frames over the host link */
-#define GFS_XFER_MAPPED 2 /* default.  The file's page cache is mapped for the GPU (shared mapping
-                           * registered with CUDA); the host serves a request by publishing where its
-                           * pages are and the GPU copies them into frames over the host link.  Only a
-                           * file whose pages are all resident in the host page cache at gfs_open is
-                           * mapped (registration pins every page; a page not yet read would be read
-                           * from storage inside gfs_open).  The mapping is opened read-write, because
-                           * read-only registration is not available on every platform; the library
-                           * never writes through it.  A file that is not fully resident, cannot be
-                           * opened read-write (permissions) or cannot be registered (file systems
-                           * whose pages cannot be pinned) is served as in GFS_XFER_PULL;
-                           * gfs_stat.mapped tells which. */
+#define GFS_XFER_MAPPED 2 /* default.  The file's page cache is mapped for the GPU; the host serves a
+                           * request by publishing where its pages are and the GPU copies them into
+                           * frames over the host link.  Only a file whose pages are all resident in
+                           * the host page cache at gfs_open is mapped (else a page not yet read would
+                           * be read from storage where no read is timed).  Where the device reads
+                           * pageable host memory through the host's page tables (device attribute
+                           * cudaDevAttrPageableMemoryAccessUsesHostPageTables; GB300 with Grace), the
+                           * mapping is read-only, of the read-only descriptor, and nothing is pinned
+                           * (gfs_stat.mapped = 2); files on any file system qualify, and files opened
+                           * on the device (gopen) are mapped too.  Elsewhere, or with
+                           * gfs_config.map_pinned, the mapping is registered with CUDA, which pins
+                           * every page inside gfs_open (gfs_stat.mapped = 1); registration of
+                           * read-only mappings is not available on every platform, so that mapping
+                           * is opened read-write (the library never writes through it), and file
+                           * systems whose pages cannot be pinned (other than tmpfs) refuse it.  A
+                           * file that is not mapped (gfs_stat.mapped = 0) is served as in
+                           * GFS_XFER_PULL.  Do not truncate a file while it is open: the GPU reads
+                           * its pages where they were mapped, as any reader of a mapping does. */
 
 /* How requests are placed in the ring and how host threads find them (gfs_config.queue). */
 #define GFS_QUEUE_SHARED 0 /* one shared ring: the GPU takes the next ticket, any host thread serves any
@@ -129,7 +136,9 @@ typedef struct gfs_config {
                               * up to this many pages in all, and serves them with one read into staging
                               * (Section 4.1's several pages from one pread, across threadblocks).
                               * 0 = one staging buffer's worth; 1 = one request at a time */
-  uint32_t reserved[3];
+  uint32_t map_pinned;     /* GFS_XFER_MAPPED: 1 = always register (pin) the mapping; 0 = read it through
+                            * the host page tables where the device can (see GFS_XFER_MAPPED) */
+  uint32_t reserved[2];
 } gfs_config;
 
 typedef struct gfs_stat {
@@ -137,7 +146,8 @@ typedef struct gfs_stat {
   uint32_t page_size; /* cache page size */
   uint32_t flags;     /* open flags */
   uint32_t advice;    /* current fadvise hint */
-  uint32_t mapped;    /* 1 if the file's page cache is mapped for the GPU (GFS_XFER_MAPPED) */
+  uint32_t mapped;    /* GFS_XFER_MAPPED: 0 not mapped (pread staging), 1 mapped and pinned, 2 mapped
+                       * read-only through the host page tables (nothing pinned) */
 } gfs_stat;
 
 /* Counters since the last gfs_reset_cache (device side and host side). */
@@ -218,9 +228,9 @@ int gfs_shutdown(gfs_ctx* ctx);
 
 /* Open `path` read-only; *fid (0 .. max_files-1) names it on host and device.
  * Readahead applies only with GFS_RDONLY (Section 4.4).  With GFS_XFER_MAPPED
- * the open also maps and registers the file when it is fully resident in the
- * host page cache (see GFS_XFER_MAPPED): that pins the whole file, which takes
- * time in proportion to its size, and gfs_close unpins it. */
+ * the open also maps the file when it is fully resident in the host page cache
+ * (see GFS_XFER_MAPPED); where the mapping is pinned, that takes time in
+ * proportion to the file's size, and gfs_close unpins it. */
 int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid);
 
 /* Close a file id and drop its cached pages, so that a file opened later under

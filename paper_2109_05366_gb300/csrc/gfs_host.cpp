@@ -213,19 +213,37 @@ bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
   return true;
 }
 
-// GFS_XFER_MAPPED: map the file shared and register the mapping with CUDA so the
-// GPU can read its page-cache pages.  Registration of read-only mappings is not
-// available on every platform, so the mapping is read-write; nothing ever writes
-// through it.  Only a file whose pages are all in the host page cache is mapped:
-// registration pins every page, so a page not yet read would be read from storage
-// inside the open, where no read is timed.  Returns false (and leaves the file
-// unmapped: its requests are then served by pread into staging) when the file is
-// not fully resident or any step fails.
-bool map_file(HostFile& hf) {
+// GFS_XFER_MAPPED: map the file shared so the GPU can read its page-cache pages.
+// Only a file whose pages are all in the host page cache is mapped: a page not
+// yet read would be read from storage where no read is timed (inside the open
+// when the mapping is pinned, on the GPU's first touch otherwise).  Two ways:
+//   * host page tables (device attribute PageableMemoryAccessUsesHostPageTables):
+//     a read-only mapping of the read-only descriptor, nothing pinned; the GPU
+//     reads it at its host virtual address.  Any file system.
+//   * registration: the mapping is registered with CUDA (pinned).  Read-only
+//     registration is not available on every platform, so the mapping is
+//     read-write (nothing ever writes through it); file systems whose pages
+//     cannot be pinned refuse it (tmpfs accepts).
+// Returns false (and leaves the file unmapped: its requests are then served by
+// pread into staging) when the file is not fully resident or a step fails.
+bool map_file(HostFile& hf, bool host_page_tables) {
   if (hf.size == 0) return false;
+  const size_t len = (hf.size + 4095) & ~(size_t)4095;
+  if (host_page_tables) {
+    void* m = mmap(nullptr, len, PROT_READ, MAP_SHARED, hf.fd, 0);
+    if (m == MAP_FAILED) return false;
+    if (!fully_resident(m, len)) {
+      munmap(m, len);
+      return false;
+    }
+    hf.map = m;
+    hf.map_len = len;
+    hf.dev_map = (uint64_t)(uintptr_t)m;
+    hf.map_pinned = false;
+    return true;
+  }
   int rw = open(hf.path.c_str(), O_RDWR | O_CLOEXEC);
   if (rw < 0) return false;
-  const size_t len = (hf.size + 4095) & ~(size_t)4095;
   void* m = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_SHARED, rw, 0);
   close(rw);
   if (m == MAP_FAILED) return false;
@@ -248,16 +266,18 @@ bool map_file(HostFile& hf) {
   hf.map = m;
   hf.map_len = len;
   hf.dev_map = (uint64_t)(uintptr_t)dp;
+  hf.map_pinned = true;
   return true;
 }
 
 void unmap_file(HostFile& hf) {
   if (!hf.map) return;
-  cudaHostUnregister(hf.map);
+  if (hf.map_pinned) cudaHostUnregister(hf.map);
   munmap(hf.map, hf.map_len);
   hf.map = nullptr;
   hf.map_len = 0;
   hf.dev_map = 0;
+  hf.map_pinned = false;
 }
 
 FileDev make_filedev(gfs_ctx* ctx, const HostFile& hf) {
@@ -269,7 +289,7 @@ FileDev make_filedev(gfs_ctx* ctx, const HostFile& hf) {
   fd.fetched = hf.open ? hf.d_fetched : nullptr;
   fd.flags = (uint32_t)hf.flags;
   fd.advice = (uint32_t)hf.advice;
-  fd.mapped = hf.open && hf.map ? 1u : 0u;
+  fd.mapped = hf.open && hf.map ? (hf.map_pinned ? 1u : 2u) : 0u;
   return fd;
 }
 
@@ -431,6 +451,14 @@ void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const
     return give_back(-e);
   }
   const uint64_t size = (uint64_t)st.st_size;
+  // mapped for the GPU only through the host page tables: registration (pinning)
+  // is a CUDA call, which must not wait behind the kernels that wait for this answer
+  HostFile mapping;
+  if (ctx->cfg.xfer == GFS_XFER_MAPPED && ctx->host_page_tables && !ctx->cfg.map_pinned) {
+    mapping.fd = fd;
+    mapping.size = size;
+    map_file(mapping, true);
+  }
   const uint64_t np = (size + P - 1) >> ctx->dev.page_shift;
   const size_t fbytes = (size_t)((np + 31) / 32) * 4;
   uint32_t* bits = nullptr;
@@ -444,6 +472,7 @@ void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const
         cudaFreeAsync(bits, ctx->ctl_stream);
         cudaStreamSynchronize(ctx->ctl_stream);
       }
+      unmap_file(mapping);
       close(fd);
       return give_back(-ENOMEM);
     }
@@ -453,6 +482,10 @@ void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const
     HostFile& hf = ctx->files[slot];
     hf.fd = fd;
     hf.size = size;
+    hf.map = mapping.map;
+    hf.map_len = mapping.map_len;
+    hf.dev_map = mapping.dev_map;
+    hf.map_pinned = mapping.map_pinned;
     hf.flags = (int)arg;
     hf.advice = GFS_ADV_NORMAL;
     hf.path = path;
@@ -599,6 +632,15 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   gfs_ctx* ctx = new (std::nothrow) gfs_ctx();
   if (!ctx) return -ENOMEM;
   ctx->cfg = c;
+  {  // can the GPU read pageable host memory through the host's page tables?
+    int pageable = 0, hpt = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&hpt, cudaDevAttrPageableMemoryAccessUsesHostPageTables, c.device) != cudaSuccess) {
+      cudaGetLastError();
+      pageable = hpt = 0;
+    }
+    ctx->host_page_tables = pageable && hpt;
+  }
   DevHandle& g = ctx->dev;
   const uint32_t F = (uint32_t)F64;
   g.timeout_ns = c.timeout_ns;
@@ -888,7 +930,7 @@ int gfs_open(gfs_ctx* ctx, const char* path, int flags, int* fid) {
     hf.path = path;
   }
   // falls back to pread staging when it fails; a direct file is read from storage every time
-  if (ctx->cfg.xfer == GFS_XFER_MAPPED && !direct) map_file(hf);
+  if (ctx->cfg.xfer == GFS_XFER_MAPPED && !direct) map_file(hf, ctx->host_page_tables && !ctx->cfg.map_pinned);
   {
     const uint64_t np = (hf.size + ctx->cfg.page_size - 1) >> ctx->dev.page_shift;
     hf.fetched_bytes = (size_t)((np + 31) / 32) * 4;
@@ -964,7 +1006,7 @@ int gfs_fstat(gfs_ctx* ctx, int fid, gfs_stat* st) {
   st->page_size = ctx->cfg.page_size;
   st->flags = (uint32_t)ctx->files[fid].flags;
   st->advice = (uint32_t)ctx->files[fid].advice;
-  st->mapped = ctx->files[fid].map ? 1u : 0u;
+  st->mapped = ctx->files[fid].map ? (ctx->files[fid].map_pinned ? 1u : 2u) : 0u;
   return 0;
 }
 

@@ -22,9 +22,10 @@ namespace gfs {
 struct HostFile {
   int fd = -1;
   uint64_t size = 0;
-  void* map = nullptr;     // GFS_XFER_MAPPED: shared mapping registered with CUDA
+  void* map = nullptr;     // GFS_XFER_MAPPED: shared mapping of the file the GPU reads
   size_t map_len = 0;
   uint64_t dev_map = 0;    // its device address
+  bool map_pinned = false; // registered with CUDA (pinned); else read through the host page tables
   uint32_t* d_fetched = nullptr;  // per-page fetched bits (device)
   size_t fetched_bytes = 0;
   int flags = 0;
@@ -104,6 +105,7 @@ struct gfs_ctx {
   void* h_ctl_fd = nullptr;           // pinned FileDev staging of those copies
   unsigned long long* h_cancel = nullptr;   // mapped pinned: per-slot ticket cancellations
   unsigned long long* h_skipped = nullptr;  // mapped pinned: tickets the host skipped
+  bool host_page_tables = false;   // the GPU reads pageable host memory through the host page tables
   std::mutex mu;
   std::mutex files_mu;             // HostFile fields read by the host I/O threads
   std::mutex dev_open_mu;          // device opens and closes, one at a time

@@ -271,15 +271,20 @@ def test_host_read_errors_surface_as_eio(torch_cuda, gfs, datadir, xfer):
         assert cnt.tolist() == c and sm.tolist() == s and hs.tolist() == h
 
 
-def test_mapped_file_is_mapped_and_exact(torch_cuda, gfs, datadir):
-    """GFS_XFER_MAPPED on a tmpfs file: the GPU reads the page cache directly."""
+@pytest.mark.parametrize("map_pinned", [0, 1])
+def test_mapped_file_is_mapped_and_exact(torch_cuda, gfs, datadir, map_pinned):
+    """GFS_XFER_MAPPED on a tmpfs file: the GPU reads the page cache directly, through the
+    host page tables (read-only, nothing pinned) where the device can, or through a pinned
+    registration (map_pinned=1, and on devices that cannot)."""
     if not datadir.startswith("/dev/shm"):
         pytest.skip("no tmpfs for a mappable file")
     size = 96 * MiB + 333
     path = _file(datadir, 8, size)
-    with gfs.Context(cache_bytes=16 * MiB, page_size=512 * KiB, xfer=2, max_rpc_pages=16, debug_counts=1) as ctx:
+    with gfs.Context(cache_bytes=16 * MiB, page_size=512 * KiB, xfer=2, max_rpc_pages=16, debug_counts=1,
+                     map_pinned=map_pinned) as ctx:
         fid = ctx.open(path)
-        assert ctx.fstat(fid).mapped == 1
+        mapped = ctx.fstat(fid).mapped
+        assert mapped == 1 if map_pinned else mapped in (1, 2)
         for _ in range(2):
             out = ctx.scan(fid, MiB, blocks=48, threads=256)
             torch_cuda.cuda.synchronize()
@@ -288,6 +293,35 @@ def test_mapped_file_is_mapped_and_exact(torch_cuda, gfs, datadir):
             assert st["host_preads"] == 0 and st["timeouts"] == 0
             ctx.reset_cache()
         ctx.close(fid)
+
+
+def test_mapped_through_host_page_tables_any_file_system(torch_cuda, gfs, tmp_path, datadir):
+    """Where the GPU reads pageable host memory through the host page tables, a warm file
+    on a disk file system (whose pages cannot be pinned) is mapped read-only too, and so is
+    a file opened on the device (gopen: no CUDA call is needed to map it)."""
+    path = str(tmp_path / "disk.bin")
+    size = 40 * MiB + 99
+    inputs.write_file(path, 17, size)
+    with open(path, "rb") as f:  # warm: every page in the host page cache
+        while f.read(1 << 24):
+            pass
+    with gfs.Context(cache_bytes=16 * MiB, page_size=512 * KiB, max_rpc_pages=16) as ctx:
+        fid = ctx.open(path)
+        if ctx.fstat(fid).mapped != 2:
+            pytest.skip("the device does not read pageable memory through the host page tables")
+        out = ctx.scan(fid, MiB, blocks=32, threads=256)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, MiB, *out)
+        st = ctx.stats()
+        assert st["host_preads"] == 0 and st["timeouts"] == 0
+        ctx.close(fid)
+        dev_path = _file(datadir, 18, 24 * MiB + 5)
+        ctx.reset_cache()
+        out = ctx.scan_path(dev_path, MiB, blocks=16)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, dev_path, MiB, *out)
+        st = ctx.stats()
+        assert st["host_controls"] > 0 and st["host_preads"] == 0 and st["timeouts"] == 0
 
 
 def test_mapped_transfer_skips_files_not_in_the_host_page_cache(torch_cuda, gfs, datadir):
@@ -311,7 +345,7 @@ def test_mapped_transfer_skips_files_not_in_the_host_page_cache(torch_cuda, gfs,
     full = _file(datadir, 8, 4 * MiB)
     with gfs.Context(cache_bytes=16 * MiB, page_size=256 * KiB, max_rpc_pages=16) as ctx:  # the default transfer
         assert ctx.cfg.xfer == gfs.XFER_MAPPED
-        assert ctx.fstat(ctx.open(full)).mapped == 1
+        assert ctx.fstat(ctx.open(full)).mapped in (1, 2)
 
 
 @pytest.mark.parametrize("xfer", XFERS)
