@@ -60,7 +60,10 @@ typedef struct gfs_dev {
  * the host like a read).  path: NUL-terminated, readable by the device, shorter
  * than GFS_PATH_MAX.  flags: GFS_RDONLY (readahead on, Section 4.4) or GFS_RDWR
  * (readahead off; the path never writes).  Blocks that open a path already open
- * on the device with the same flags share its file id (reference counted).
+ * on the device with the same flags share its file id (reference counted); a
+ * path whose last reference was closed gets its id back as long as the host has
+ * not dropped that id's pages yet (gfs_reset_cache), so blocks that open and
+ * close one file at different times still share one id.
  * Returns the file id (>= 0) or -EINVAL, -ENAMETOOLONG, -EMFILE (every id in
  * use), -ENOTSUP (GFS_MODE_PAPER), an error of the host open (-ENOENT, ...),
  * -ETIMEDOUT. */
@@ -84,8 +87,8 @@ __device__ long long gread_as(const gfs_dev* h, int reader, int fid, unsigned lo
 
 /* Close a file id opened with gopen (Section 2.2).  After the last reference
  * the id reads as closed; its pages stay cached, unreachable, until the host
- * drops them (gfs_reset_cache, or reuse of the id).  Returns 0, -EBADF,
- * -ETIMEDOUT. */
+ * drops them (gfs_reset_cache, or reuse of the id) or a gopen of the same path
+ * opens the id again.  Returns 0, -EBADF, -ETIMEDOUT. */
 __device__ int gclose(const gfs_dev* h, int fid);
 
 /* Size, page size, open flags, hint and mapping of an open file id (no request

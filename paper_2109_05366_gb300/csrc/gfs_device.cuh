@@ -2265,7 +2265,8 @@ static __device__ int block_control(const DevHandle& g, uint32_t op, uint32_t fi
 // Threadblock-collective open (every thread, same arguments).  `path` is a
 // NUL-terminated string the device can read, shorter than GFS_PATH_MAX.
 // Opening a path that blocks already hold open on the device (same flags)
-// returns the same fid and adds a reference.  Returns the fid or -errno
+// returns the same fid and adds a reference; so does opening a path whose id
+// the last gclose retired, until the host drops its pages.  Returns the fid or -errno
 // (-EINVAL, -ENAMETOOLONG, -EMFILE, -ENOTSUP in GFS_MODE_PAPER, host open
 // errors, -ETIMEDOUT).
 static __device__ int gopen(const DevHandle& g, const char* path, int flags) {
@@ -2287,7 +2288,8 @@ static __device__ int gopen(const DevHandle& g, const char* path, int flags) {
 
 // Threadblock-collective close of a fid opened with gopen.  After the last
 // reference the fid reads as closed; its pages stay cached, unreachable, until
-// the host drops them (gfs_reset_cache, or reuse of the fid).  Returns 0 or
+// the host drops them (gfs_reset_cache, or reuse of the fid) or a gopen of the
+// same path opens the fid again.  Returns 0 or
 // -errno (-EBADF for a fid not opened on the device).
 static __device__ int gclose(const DevHandle& g, int fid) {
   if (fid < 0 || (uint32_t)fid >= g.max_files) return -kEBADF;

@@ -414,6 +414,7 @@ void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const
   }
   const uint32_t P = ctx->cfg.page_size;
   int slot = -1;
+  int revive = -1;
   {
     std::lock_guard<std::mutex> lk(ctx->files_mu);
     for (size_t i = 0; i < ctx->files.size(); ++i) {
@@ -424,7 +425,19 @@ void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const
         return;
       }
     }
-    for (size_t i = 0; i < ctx->files.size(); ++i) {
+    // A block may close the path's last reference before another block's open of
+    // it gets here: the retired id still holds the file (descriptor, mapping and
+    // cached pages of the same read-only file), so it is opened again.
+    for (size_t i = 0; i < ctx->files.size() && revive < 0; ++i) {
+      HostFile& hf = ctx->files[i];
+      if (hf.retired && hf.by_device && hf.path == path && (uint32_t)hf.flags == arg) {
+        hf.retired = false;
+        hf.open = true;
+        hf.dev_refs = 1;
+        revive = (int)i;
+      }
+    }
+    for (size_t i = 0; i < ctx->files.size() && revive < 0; ++i) {
       HostFile& hf = ctx->files[i];
       if (!hf.open && !hf.retired && !hf.opening) {
         hf.opening = true;
@@ -432,6 +445,18 @@ void device_control(gfs_ctx* ctx, uint32_t op, uint32_t fid, uint32_t arg, const
         break;
       }
     }
+  }
+  if (revive >= 0) {
+    const int rc = push_file_async(ctx, revive);
+    if (rc) {  // the id stays retired: its device state is unknown
+      std::lock_guard<std::mutex> lk(ctx->files_mu);
+      ctx->files[revive].open = false;
+      ctx->files[revive].retired = true;
+      m->status = rc;
+      return;
+    }
+    m->status = revive;
+    return;
   }
   if (slot < 0) {
     m->status = -EMFILE;

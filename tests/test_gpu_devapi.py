@@ -136,14 +136,19 @@ def test_scan_path_with_static_queue_and_per_block_lra(torch_cuda, gfs, datadir,
 def test_scan_path_ids_retire_until_reset(torch_cuda, gfs, datadir):
     a = _file(datadir, 26, 2 * MiB + 5)
     b = _file(datadir, 27, 2 * MiB + 9)
+    c = _file(datadir, 28, 2 * MiB + 11)
     with gfs.Context(cache_bytes=32 * MiB, page_size=256 * KiB, max_files=2) as ctx:
         for p in (a, b):                                  # each run leaves its id retired
             out = ctx.scan_path(p, MiB, blocks=4)
             torch_cuda.cuda.synchronize()
             _check_scan(gfs, p, MiB, *out)
-        cnt, _, _ = ctx.scan_path(a, MiB, blocks=4)       # no id left
+        cnt, _, _ = ctx.scan_path(c, MiB, blocks=4)       # no id left for a third path
         torch_cuda.cuda.synchronize()
         assert (cnt.cpu().numpy()[:3] == -errno.EMFILE).all()
+        for p in (a, b, a, b):                            # a retired path's id is opened again
+            out = ctx.scan_path(p, MiB, blocks=8)         # (more blocks than strides: some close at once)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, p, MiB, *out)
         ctx.reset_cache()                                 # drops the retired ids' pages
         out = ctx.scan_path(b, MiB, blocks=4)
         torch_cuda.cuda.synchronize()
