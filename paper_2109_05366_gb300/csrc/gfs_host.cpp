@@ -213,6 +213,23 @@ bool file_lookup(gfs_ctx* ctx, uint32_t fid, FileView* out) {
   return true;
 }
 
+// Give every page of the mapping [m, m + len) its page-table entry now, on the
+// host.  A fresh mapping has none: the GPU's first touch of each page would take
+// the I/O page-fault path, and hundreds of concurrent first touches there can
+// wait out a scan's device deadline.  The pages are resident, so nothing is read
+// from storage.
+void populate(void* m, size_t len) {
+#ifdef MADV_POPULATE_READ
+  if (madvise(m, len, MADV_POPULATE_READ) == 0) return;
+#endif
+  const long pg = sysconf(_SC_PAGESIZE);
+  const size_t step = pg > 0 ? (size_t)pg : 4096;
+  const volatile unsigned char* p = (const volatile unsigned char*)m;
+  unsigned char acc = 0;
+  for (size_t off = 0; off < len; off += step) acc ^= p[off];
+  (void)acc;
+}
+
 // GFS_XFER_MAPPED: map the file shared so the GPU can read its page-cache pages.
 // Only a file whose pages are all in the host page cache is mapped: a page not
 // yet read would be read from storage where no read is timed (inside the open
@@ -236,6 +253,7 @@ bool map_file(HostFile& hf, bool host_page_tables) {
       munmap(m, len);
       return false;
     }
+    populate(m, len);
     hf.map = m;
     hf.map_len = len;
     hf.dev_map = (uint64_t)(uintptr_t)m;
