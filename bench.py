@@ -661,7 +661,7 @@ def run_queue(args):
                     cfg = dict(cache_bytes=GiB, page_size=page, xfer=xfer, queue=queue, rpc_slots=1024,
                                host_threads=16, max_rpc_pages=min(256, MiB // page * 2), ra_cap_pages=MiB // page,
                                trace_capacity=(1 << 20) if queue == gfs.QUEUE_SHARED else 0,
-                               timeout_ns=30 * 10**9)
+                               timeout_ns=30 * 10**9, self_serve=0)  # the study is of host service
                     with gfs.Context(**cfg) as ctx:
                         fid = ctx.open(path)
                         best = None

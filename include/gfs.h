@@ -138,7 +138,12 @@ typedef struct gfs_config {
                               * 0 = one staging buffer's worth; 1 = one request at a time */
   uint32_t map_pinned;     /* GFS_XFER_MAPPED: 1 = always register (pin) the mapping; 0 = read it through
                             * the host page tables where the device can (see GFS_XFER_MAPPED) */
-  uint32_t reserved[2];
+  uint32_t self_serve;     /* GFS_XFER_MAPPED: 1 (default) = a request for a mapped file is served by the
+                            * threadblock that makes it, which copies the pages from the mapping into
+                            * their frames itself (no host thread, no ring slot); 0 = by the host I/O
+                            * threads like any other.  Off while host faults are injected
+                            * (gfs_set_faults), which only reach requests the host serves */
+  uint32_t reserved[1];
 } gfs_config;
 
 typedef struct gfs_stat {
@@ -214,7 +219,8 @@ typedef struct gfs_scan_args {
 /* Fill *cfg with defaults: 1 GiB cache, 512 KiB pages, readahead, Wmax 8,
  * async readahead on, 128 slots, 64 pages per request, 16 host threads,
  * 4 MiB staging, 4096 streams, 16 files, no trace, mapped transfer
- * (GFS_XFER_MAPPED, falling back to pread staging per file), device 0. */
+ * (GFS_XFER_MAPPED, falling back to pread staging per file) with requests for
+ * mapped files served by the GPU itself, device 0. */
 int gfs_config_default(gfs_config* cfg);
 
 /* Create a context: allocates the cache frames and metadata in device memory,
@@ -248,7 +254,9 @@ int gfs_fstat(gfs_ctx* ctx, int fid, gfs_stat* st);
 
 /* Host-side fault injection for tests (never a device fault): every
  * eio_every-th pread fails with EIO, every short_every-th returns half of what
- * was asked, every pread first sleeps delay_us.  0 disables each. */
+ * was asked, every pread first sleeps delay_us.  0 disables each.  While any is
+ * set, requests for mapped files are served by the host too (gfs_config.self_serve),
+ * from the next launch on. */
 int gfs_set_faults(gfs_ctx* ctx, uint32_t eio_every, uint32_t short_every, uint32_t delay_us);
 
 /* Drop every cached page, clear the counters, traces and stream history.

@@ -152,6 +152,7 @@ __device__ __forceinline__ FileDev load_file(const DevHandle& g, int fid) {
   f.advice = ld_rlx(&p->advice);
   f.mapped = ld_rlx(&p->mapped);
   f.pad = 0;
+  f.dev_map = ld_rlx64(&p->dev_map);
   return f;
 }
 
@@ -1022,6 +1023,40 @@ static __device__ int ring_acquire(const DevHandle& g, unsigned long long* t_out
   }
 }
 
+// Count a request and record it in the RPC trace (one thread).
+static __device__ void rpc_record(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n,
+                                  uint32_t kind) {
+  stat_add(g, ST_RPCS, 1);
+  if (g.trace_cap) {
+    unsigned long long i = atomicAdd(&g.ctrl->trace_rpc_n.v, 1ull);
+    if (i < g.trace_cap) {
+      gfs_rpc_rec r;
+      r.fid = fid;
+      r.kind = kind;
+      r.npages = n;
+      r.reserved = 0;
+      r.page_lo = page_lo;
+      g.trace_rpc[i] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- requests the GPU serves itself
+// With GFS_XFER_MAPPED a mapped file's pages sit in host memory the GPU reads,
+// at dev_map + page * P: serving a request needs no host read and no host
+// thread, only the copy.  The block that makes such a request copies its pages
+// into their frames right after warp 0 has installed them (block_self_serve);
+// readers of those pages meanwhile wait on the frames' state words, as for any
+// page being filled.  At most one such request is pending per block.
+struct SelfJob {
+  unsigned long long page_lo;
+  uint32_t n;
+};
+__device__ __forceinline__ SelfJob& self_job() {
+  __shared__ SelfJob j;
+  return j;
+}
+
 static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long long page_lo, uint32_t n, uint32_t kind,
                           const uint32_t* s_frames, unsigned long long deadline, unsigned long long* ticket_out = nullptr) {
   const int lane = lane_id();
@@ -1067,19 +1102,7 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
   if (ticket_out) *ticket_out = t;
   if (lane == 0) {
     st_rel_sys64(&s->seq, t + 1);
-    stat_add(g, ST_RPCS, 1);
-    if (g.trace_cap) {
-      unsigned long long i = atomicAdd(&g.ctrl->trace_rpc_n.v, 1ull);
-      if (i < g.trace_cap) {
-        gfs_rpc_rec r;
-        r.fid = fid;
-        r.kind = kind;
-        r.npages = n;
-        r.reserved = 0;
-        r.page_lo = page_lo;
-        g.trace_rpc[i] = r;
-      }
-    }
+    rpc_record(g, fid, page_lo, n, kind);
   }
   __syncwarp();
   return 0;
@@ -1154,7 +1177,7 @@ static __device__ uint32_t take_run(const DevHandle& g, uint32_t L, uint32_t dem
 static __device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p,
                                      uint32_t n, uint32_t demand, uint32_t window, uint32_t kind,
                                      unsigned long long mark_end, int mark_idx, const uint32_t* s_frames,
-                                     unsigned long long deadline);
+                                     unsigned long long deadline, bool allow_self);
 
 // Warp: pages 1 .. of a request whose page 0 is installed (page i is p + i, a
 // readahead page when i >= demand).  The run is cut, as one page at a time would
@@ -1246,7 +1269,8 @@ static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const F
       const uint32_t n = e - a + 1;
       const uint32_t kind = a < demand ? (uint32_t)GFS_KIND_DEMAND
                                        : (demand == 0 ? (uint32_t)GFS_KIND_ASYNC_RA : (uint32_t)GFS_KIND_SYNC_RA);
-      finish_request(g, fid, fi, p + a, n, a < demand ? demand - a : 0u, n, kind, 0, -1, s_frames + a, deadline);
+      finish_request(g, fid, fi, p + a, n, a < demand ? demand - a : 0u, n, kind, 0, -1, s_frames + a, deadline,
+                     false);
       a = e + 1;
     }
     L = cut - 1;
@@ -1338,10 +1362,13 @@ static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid
   return (int)n;
 }
 
-// Finish a request: record windows and the readahead mark, send it, count it.
+// Finish a request: record windows and the readahead mark, send it (or, with
+// allow_self, leave it to the requesting block when the file is mapped and no
+// other such request is pending: its frame list must stay in s_frames until the
+// block copies it), count it.
 static __device__ int finish_request(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p, uint32_t n,
                               uint32_t demand, uint32_t window, uint32_t kind, unsigned long long mark_end,
-                              int mark_idx, const uint32_t* s_frames, unsigned long long deadline) {
+                              int mark_idx, const uint32_t* s_frames, unsigned long long deadline, bool allow_self) {
   const int lane = lane_id();
   for (uint32_t i = lane; i < n; i += 32) st_rlx(&g.fwindow[s_frames[i]], window);
   if (lane == 0) {
@@ -1355,7 +1382,46 @@ static __device__ int finish_request(const DevHandle& g, uint32_t fid, const Fil
     __threadfence();
   }
   __syncwarp();
+  int self = 0;
+  if (lane == 0 && allow_self && g.self_serve && fi.dev_map && self_job().n == 0) {
+    self_job().page_lo = p;
+    self_job().n = n;
+    rpc_record(g, fid, p, n, kind);
+    self = 1;
+  }
+  if (bcast(self)) return 0;
   return rpc_submit(g, fid, p, n, kind, s_frames, deadline);
+}
+
+// Whole block: copy the pages of the pending self-served request (frames in
+// frames[0 .. n), pages page_lo ..) from the file's mapping into their frames and
+// publish them READY.  No-op when none is pending.  Block-uniform.
+static __device__ void block_self_serve(const DevHandle& g, const FileDev& fi, const uint32_t* frames) {
+  SelfJob& j = self_job();
+  const uint32_t n = j.n;
+  if (n == 0) return;
+  const unsigned long long p0 = j.page_lo;
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  if (g.page_size <= (16u << 10)) {  // small pages: a warp per page, many in flight
+    const uint32_t w = tid >> 5, nw = nt >> 5, lane = tid & 31u;
+    for (uint32_t i = w; i < n; i += nw) {
+      const uint32_t f = frames[i];
+      copy_in((const uint8_t*)(fi.dev_map + ((p0 + i) << g.page_shift)), g.frames + ((size_t)f << g.page_shift),
+              ld_rlx(&g.fvalid[f]), lane, 32);
+    }
+  } else {
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint32_t f = frames[i];
+      copy_in((const uint8_t*)(fi.dev_map + ((p0 + i) << g.page_shift)), g.frames + ((size_t)f << g.page_shift),
+              ld_rlx(&g.fvalid[f]), tid, nt);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += nt) st_rel(&g.fstate[frames[i]], FR_READY);
+  __syncthreads();
+  if (tid == 0) j.n = 0;
+  __syncthreads();
 }
 
 // R4: asynchronous readahead of [end, end + min(Wmax, 2T)) from a readahead mark.
@@ -1370,7 +1436,7 @@ static __device__ void async_readahead(const DevHandle& g, int stream, uint32_t 
   int n = request_range(g, stream, fid, fi, end, want, 0, false, seq0, deadline, s_frames);
   if (n <= 0) return;
   finish_request(g, fid, fi, end, (uint32_t)n, 0, (uint32_t)n, GFS_KIND_ASYNC_RA, end + (uint32_t)n, 0, s_frames,
-                 deadline);
+                 deadline, true);
 }
 
 // R1-R3: a miss on page p (p1 = last page of the gread).  Returns the pinned,
@@ -1423,7 +1489,8 @@ static __device__ int handle_miss(const DevHandle& g, int stream, uint32_t fid, 
   int f0 = 0;
   if (lane == 0) f0 = (int)s_frames[0];
   f0 = bcast(f0);
-  int r = finish_request(g, fid, fi, p, (uint32_t)n, d, window, kind, p + (uint32_t)n, mark_idx, s_frames, deadline);
+  int r = finish_request(g, fid, fi, p, (uint32_t)n, d, window, kind, p + (uint32_t)n, mark_idx, s_frames, deadline,
+                         true);
   if (r < 0) {
     if (lane == 0) frame_unpin(g, f0);
     return r;
@@ -2109,7 +2176,10 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
         continue;
       }
     }
-    if (tid == 0) s_job.kind = PJ_NONE;
+    if (tid == 0) {
+      s_job.kind = PJ_NONE;
+      self_job().n = 0;
+    }
     __syncthreads();
     if (tid < 32) {
       int st = 0;
@@ -2124,6 +2194,7 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
     int st = s_state;
     const PaperJob job = s_job;
     __syncthreads();
+    block_self_serve(g, fi, s_frames);  // the request the miss just made, when its pages are the block's to copy
     if (f < 0) {
       err = f;
       break;
@@ -2140,6 +2211,8 @@ __device__ long long gread_impl(const DevHandle& g, int stream, int fid, unsigne
       break;
     }
     if (tid < 32) check_mark(g, stream, (uint32_t)fid, fi, f, seq0, deadline, s_frames);
+    __syncthreads();
+    block_self_serve(g, fi, s_frames);  // the asynchronous window check_mark requested, if any
     const unsigned long long base = p << g.page_shift;
     const unsigned long long lo = (off > base ? off : base) - base;
     const unsigned long long hi = (end < base + g.page_size ? end : base + g.page_size) - base;

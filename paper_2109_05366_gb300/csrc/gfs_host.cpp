@@ -308,6 +308,7 @@ FileDev make_filedev(gfs_ctx* ctx, const HostFile& hf) {
   fd.flags = (uint32_t)hf.flags;
   fd.advice = (uint32_t)hf.advice;
   fd.mapped = hf.open && hf.map ? (hf.map_pinned ? 1u : 2u) : 0u;
+  fd.dev_map = hf.open && hf.map ? hf.dev_map : 0ull;
   return fd;
 }
 
@@ -610,6 +611,7 @@ int gfs_config_default(gfs_config* c) {
   c->max_files = 16;
   c->trace_capacity = 0;
   c->xfer = GFS_XFER_MAPPED;
+  c->self_serve = 1;
   c->debug_counts = 0;
   c->device = 0;
   return 0;
@@ -704,6 +706,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.slot_stride = slot_stride(c.max_rpc_pages);
   g.fifo_cap = std::max<uint32_t>(F, 2);  // same sequence rule as the ring
   g.xfer = c.xfer;
+  g.self_serve = (c.xfer == GFS_XFER_MAPPED && c.self_serve) ? 1u : 0u;
   g.repl = c.replacement;
   g.paper_streams = 0;
   g.nbufs = nbufs;
@@ -914,6 +917,10 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
 int gfs_set_faults(gfs_ctx* ctx, uint32_t eio_every, uint32_t short_every, uint32_t delay_us) {
   if (!ctx || !ctx->io) return -EINVAL;
   ctx->io->set_faults(eio_every, short_every, delay_us);
+  // injected host faults only reach requests the host serves: while any is set,
+  // requests for mapped files go to the host too (from the next launch on)
+  const bool faults = eio_every || short_every || delay_us;
+  ctx->dev.self_serve = (!faults && ctx->cfg.self_serve) ? 1u : 0u;
   return 0;
 }
 

@@ -103,10 +103,11 @@ struct FileDev {
   uint32_t* fetched; // one bit per page: fetched since the last reset (readahead skips those)
   uint32_t flags;    // open flags
   uint32_t advice;   // GFS_ADV_*
-  uint32_t mapped;   // 1 if the file's page cache is mapped for the GPU
+  uint32_t mapped;   // the file's page cache is mapped for the GPU: 1 pinned, 2 through the host page tables
   uint32_t pad;
+  unsigned long long dev_map;  // device address of that mapping (0: not mapped)
 };
-static_assert(sizeof(FileDev) == 48, "FileDev");
+static_assert(sizeof(FileDev) == 56, "FileDev");
 
 // One request-ring slot in mapped pinned memory (64-byte header + frame list).
 // Vyukov bounded MPMC protocol on `seq`: slot i starts at seq = i; the GPU
@@ -224,6 +225,9 @@ struct DevHandle {
   uint32_t* lra;                  // paper_streams * quota frames, ring per stream
   uint32_t* lra_head;             // per stream: ring position of the oldest frame
   uint32_t* lra_len;              // per stream: frames in the ring
+  // a request for a mapped file is served by the requesting block (it copies the
+  // pages from the mapping itself) instead of by the host I/O threads
+  uint32_t self_serve;
 };
 
 }  // namespace gfs

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
                 ("max_rpc_pages", u32), ("host_threads", u32), ("staging_bytes", u32), ("max_streams", u32),
                 ("max_files", u32), ("trace_capacity", u32), ("xfer", u32), ("debug_counts", u32),
                 ("device", i32), ("latency_capacity", u32), ("replacement", u32), ("queue", u32),
-                ("host_merge_pages", u32), ("map_pinned", u32), ("reserved", u32 * 2)]
+                ("host_merge_pages", u32), ("map_pinned", u32), ("self_serve", u32), ("reserved", u32 * 1)]
 
 
 class Stat(ctypes.Structure):

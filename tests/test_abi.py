@@ -96,7 +96,7 @@ def test_struct_layouts_match_header(tmp_path):
     import ctypes
     import subprocess
     checks = [("gfs_config", gfs.Config, ["cache_bytes", "page_size", "device", "latency_capacity", "replacement",
-                                          "queue", "host_merge_pages", "map_pinned", "reserved"]),
+                                          "queue", "host_merge_pages", "map_pinned", "self_serve", "reserved"]),
               ("gfs_thread_stat", gfs.ThreadStat, ["requests", "first_request_ns", "bytes"]),
               ("gfs_io_rec", gfs.IoRec, ["offset", "bytes", "fid", "thread", "t_ns"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),

@@ -61,7 +61,9 @@ def test_two_slot_ring_backpressure(datadir, xfer):
     path = _file(datadir, 23, 20 * MiB + 77)
     with pytest.raises(gfs.GfsError):
         gfs.Context(rpc_slots=1)               # a ring needs two slots (sequence rule)
-    with gfs.Context(cache_bytes=16 * MiB, page_size=128 * KiB, xfer=xfer, rpc_slots=2, max_rpc_pages=16) as ctx:
+    # self_serve=0: mapped files' requests go through the two-slot ring too
+    with gfs.Context(cache_bytes=16 * MiB, page_size=128 * KiB, xfer=xfer, rpc_slots=2, max_rpc_pages=16,
+                     self_serve=0) as ctx:
         fid = ctx.open(path)
         _exact(path, 512 * KiB, *ctx.scan_host(fid, 512 * KiB, blocks=32, threads=128))
         assert ctx.stats()["timeouts"] == 0

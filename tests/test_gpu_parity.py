@@ -404,6 +404,44 @@ def test_merged_host_reads_exact(torch_cuda, gfs, datadir, xfer, mode):
                     assert st["host_merged"] > 0 and st["host_preads"] < st["host_requests"]
 
 
+@pytest.mark.parametrize("page", [4 * KiB, 512 * KiB])
+def test_requests_for_mapped_files_served_by_the_gpu(torch_cuda, gfs, datadir, page):
+    """With the mapped transfer a request for a mapped file is served by the block that
+    makes it (it copies the pages from the mapping): no host request at all, every
+    stride exact, every page fetched once while the file fits, and the serialized request
+    and eviction logs still equal the oracle's (the policy does not change)."""
+    if not datadir.startswith("/dev/shm"):
+        pytest.skip("no tmpfs for a mappable file")
+    size = 24 * MiB + 12345
+    path = _file(datadir, 19, size)
+    npages = (size + page - 1) // page
+    with gfs.Context(cache_bytes=32 * MiB, page_size=page, xfer=2, max_rpc_pages=64, ra_cap_pages=15,
+                     debug_counts=1) as ctx:
+        fid = ctx.open(path)
+        assert ctx.fstat(fid).mapped in (1, 2)
+        for fused in (False, True):
+            ctx.reset_cache()
+            out = ctx.scan(fid, MiB, blocks=48, threads=256, fused=fused)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, MiB, *out)
+            st = ctx.stats()
+            assert st["rpcs"] > 0 and st["host_requests"] == 0 and st["timeouts"] == 0
+            assert (ctx.fetch_counts(npages) == 1).all()
+    frames, blocks, stride = 40, 4, 3 * page + 7
+    path2 = _file(datadir, 20, 96 * page + 3)
+    reserve = policy.default_reserve(blocks, stride, page)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, xfer=2, trace_capacity=1 << 16,
+                     reserve_frames=reserve, max_rpc_pages=16) as ctx:
+        fid = ctx.open(path2)
+        out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path2, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+        assert ctx.stats()["host_requests"] == 0
+    sim, res = policy.run_scan(path2, page, frames, stride, blocks, reserve=reserve, max_rpc_pages=16)
+    assert rpc == sim.rpc_log and ev == sim.evict_log
+
+
 def _golden(name):
     params, rows = {}, []
     for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):

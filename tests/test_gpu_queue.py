@@ -48,7 +48,7 @@ def _check_scan(gfs, path, stride, cnt, sm, hs):
 def test_scan_exact_with_either_queue(torch_cuda, gfs, datadir, xfer, queue):
     path = _file(datadir, 41, 96 * MiB + 333)
     with gfs.Context(cache_bytes=32 * MiB, page_size=256 * KiB, xfer=xfer, queue=queue, rpc_slots=64,
-                     host_threads=4, max_rpc_pages=16) as ctx:
+                     host_threads=4, max_rpc_pages=16, self_serve=0) as ctx:  # mapped: served by the host
         fid = ctx.open(path)
         for _ in range(2):
             out = ctx.scan(fid, MiB, blocks=96, threads=256)
@@ -87,7 +87,7 @@ def test_io_trace_covers_the_file_and_replays(torch_cuda, gfs, datadir, xfer):
     path = _file(datadir, 43, 40 * MiB + 4321)
     size = os.path.getsize(path)
     with gfs.Context(cache_bytes=64 * MiB, page_size=256 * KiB, xfer=xfer, trace_capacity=1 << 14,
-                     max_rpc_pages=16) as ctx:
+                     max_rpc_pages=16, self_serve=0) as ctx:  # the host I/O trace: requests the host serves
         fid = ctx.open(path)
         out = ctx.scan(fid, MiB, blocks=32, threads=256)
         torch_cuda.cuda.synchronize()
