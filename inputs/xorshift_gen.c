@@ -121,7 +121,9 @@ int xs_write_file(const char* path, uint64_t seed, uint64_t size, int threads) {
   if (size && ftruncate(fd, (off_t)size) != 0) { int e = errno; close(fd); return -e; }
   pthread_t tid[64];
   gen_job jobs[64];
-  uint64_t per = (size / (uint64_t)threads + (1ull << 20) - 1) & ~((1ull << 20) - 1);
+  /* each thread's range: the ceiling of size / threads, rounded up to whole MiB,
+     so that the ranges cover every byte */
+  uint64_t per = ((size + (uint64_t)threads - 1) / (uint64_t)threads + (1ull << 20) - 1) & ~((1ull << 20) - 1);
   if (per == 0) per = 1ull << 20;
   int started = 0, spawn_err = 0;
   for (int t = 0; t < threads; ++t) {
@@ -225,7 +227,9 @@ static int write_typed(const char* path, uint64_t seed, uint64_t n, int threads,
   if (n && ftruncate(fd, (off_t)(n * 4)) != 0) { int e = errno; close(fd); free(cdf); return -e; }
   pthread_t tid[64];
   typed_job jobs[64];
-  uint64_t per = (n / (uint64_t)threads + (1u << 20) - 1) & ~(uint64_t)((1u << 20) - 1);
+  /* each thread's range of values: the ceiling of n / threads, rounded up to whole
+     Mi values, so that the ranges cover every value */
+  uint64_t per = ((n + (uint64_t)threads - 1) / (uint64_t)threads + (1u << 20) - 1) & ~(uint64_t)((1u << 20) - 1);
   if (per == 0) per = 1u << 20;
   int started = 0, err = 0;
   for (int t = 0; t < threads; ++t) {

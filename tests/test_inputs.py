@@ -88,3 +88,45 @@ def test_zipf_stream_definition(tmp_path):
     assert np.array_equal(z, inputs.zipf_values(8, 4000, 1 << 20, 1.1))
     # P(0) = 1 / H(2^20, 1.1); H(2^20, 1.1) is about 7.9, so the top bin holds ~12.6 %
     assert 0.09 < (z == 0).mean() < 0.16 and z.min() >= 0 and z.max() < (1 << 20)
+
+
+@pytest.mark.parametrize("size,threads", [((48 << 20) + 3, 16), ((48 << 20) + 3, 8), ((6 << 20) + 5, 3),
+                                          ((16 << 20) + 1, 16)])
+def test_every_byte_written_whatever_the_split(tmp_path, size, threads):
+    """The writer splits the file among threads in whole-MiB ranges; the ranges must
+    cover every byte even when size / threads is a whole number of MiB with a remainder
+    (a file whose last bytes were never written is a hole of zeros, not the stream)."""
+    path = str(tmp_path / "f.bin")
+    inputs.write_file(path, 7, size, threads)
+    assert os.path.getsize(path) == size
+    k = 4096
+    with open(path, "rb") as f:
+        f.seek(size - k)
+        tail = f.read(k)
+    assert tail == inputs.fill(7, size - k, k)
+    per = size // threads
+    with open(path, "rb") as f:  # the edges of every thread's range
+        for t in range(1, threads):
+            off = min(size - 16, t * per)
+            f.seek(off)
+            assert f.read(16) == inputs.fill(7, off, 16)
+
+
+def test_every_zipf_value_written_whatever_the_split(tmp_path):
+    """The same for the Zipf writer: value i comes from stream word i, so the last values
+    can be recomputed from the words after a jump ahead."""
+    import bisect
+
+    import numpy as np
+    path = str(tmp_path / "z.i32")
+    n = (3 << 20) + 3
+    inputs.write_zipf(path, 9, n, 1 << 10, 1.1, 3)
+    x = np.fromfile(path, dtype=np.int32)
+    assert len(x) == n
+    cdf = list(inputs.zipf_cdf(1 << 10, 1.1))
+    st = inputs.state_after(9, n - 8)
+    want = []
+    for _ in range(8):
+        st = inputs.xorshift64_step(st)
+        want.append(bisect.bisect_right(cdf, (st >> 11) * 2.0 ** -53))
+    assert list(x[-8:]) == want
