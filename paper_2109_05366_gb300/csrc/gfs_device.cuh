@@ -639,12 +639,13 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
   // (3) only for the page a gread waits for (later pages of a demand run end the
   //     request instead of evicting unconsumed pages): the least recently
   //     allocated unconsumed frame that this gread did not allocate.  A cache of
-  //     at most kLraWindow frames is scanned
-  //     whole.  A larger one is scanned a window of kLraWindow frames at a time,
+  //     at most kLraWindow frames, or any cache when greads run one at a time
+  //     (exact_lra), is scanned whole.  A larger one is scanned a window of
+  //     kLraWindow frames at a time,
   //     from a place that depends on the gread, and the oldest frame of the first
   //     window that has one is taken: concurrent greads then pick different
   //     victims instead of all racing for the single oldest frame.
-  const uint32_t W = g.n_frames < kLraWindow ? g.n_frames : kLraWindow;
+  const uint32_t W = (g.exact_lra || g.n_frames < kLraWindow) ? g.n_frames : kLraWindow;
   const uint32_t nwin = (g.n_frames + W - 1) / W;
   uint32_t base = 0;
   if (nwin > 1) {

@@ -1258,6 +1258,7 @@ static int scan_prepare(gfs_ctx* ctx, int fid, const gfs_scan_args* a, uint64_t*
     if (prc) return prc;
   }
   *g = ctx->dev;
+  g->exact_lra = a->serialize ? 1u : 0u;
   const uint64_t pages_per_read = (a->read_len >> ctx->dev.page_shift) + ((a->read_len & (ctx->cfg.page_size - 1)) != 0);
   g->reserve = ctx->cfg.reserve_frames ? ctx->cfg.reserve_frames
                                        : (uint32_t)(pages_per_read >= 0xffffffffull / a->blocks ? 0xffffffffull

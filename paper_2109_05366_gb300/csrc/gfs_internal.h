@@ -228,6 +228,9 @@ struct DevHandle {
   // a request for a mapped file is served by the requesting block (it copies the
   // pages from the mapping itself) instead of by the host I/O threads
   uint32_t self_serve;
+  // 1: one gread at a time (serialized scan): the demand fallback takes the exact
+  // least recently allocated frame of the whole cache, not of a window
+  uint32_t exact_lra;
 };
 
 }  // namespace gfs

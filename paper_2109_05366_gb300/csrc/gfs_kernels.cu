@@ -320,6 +320,7 @@ extern "C" int gfs_scan_static(gfs_ctx* ctx, int fid, const gfs_scan_args* a, in
   int rc = static_scratch(ctx->cfg.device, &scratch);
   if (rc) return rc;
   gfs::DevHandle g = ctx->dev;
+  g.exact_lra = a->serialize ? 1u : 0u;
   const uint64_t pages_per_read = (a->read_len >> ctx->dev.page_shift) + ((a->read_len & (ctx->cfg.page_size - 1)) != 0);
   g.reserve = ctx->cfg.reserve_frames
                   ? ctx->cfg.reserve_frames

@@ -116,6 +116,32 @@ def test_serialized_logs_match_oracle(torch_cuda, gfs, datadir, size, page, fram
     assert ev == sim.evict_log
 
 
+@pytest.mark.parametrize("xfer", [1, 2])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_serialized_least_recently_allocated_beyond_1024_frames(torch_cuda, gfs, datadir, mode, xfer):
+    """Above 1024 frames concurrent greads take the demand fallback's victim from a window
+    of the cache; one gread at a time takes the exact least recently allocated frame of the
+    whole cache, as the oracle does.  Reads of a page and 100 bytes of the next leave every
+    second page unconsumed, so the fallback runs hundreds of times (1100 frames)."""
+    page, frames, blocks, stride, read_len = 4 * KiB, 1100, 4, 8 * KiB, 4 * KiB + 100
+    path = _file(datadir, 33, 3000 * page + 17)
+    reserve = policy.default_reserve(blocks, stride, page)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=mode, xfer=xfer, trace_capacity=1 << 16,
+                     reserve_frames=reserve, max_rpc_pages=16) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, read_len=read_len, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out, read_len=read_len)
+        rpc, ev, nr, ne = ctx.trace()
+        st = ctx.stats()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode=("ondemand" if mode else "readahead"),
+                               read_len=read_len, reserve=reserve, max_rpc_pages=16)
+    assert sim.stats.unconsumed_evictions > 300 and st["unconsumed_evictions"] == sim.stats.unconsumed_evictions
+    assert nr == len(sim.rpc_log) and ne == len(sim.evict_log)
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
 # ------------------------------------------------ concurrent: larger than the cache
 @pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("page", [4 * KiB, 16 * KiB])
