@@ -1096,9 +1096,10 @@ def run_gfs(args):
     if rank == 0 and not args.quick and not args.no_serving:
         xf = xfer_code(args.xfer)
         serv = {"workload": "64 scans, files 2^(24+8u) B (log-uniform 16 MiB-4 GiB), 6 GiB cache, 296 CTAs, "
-                            "1 MiB units; Poisson 20/s, and all 64 at once (saturating)"}
+                            "1 MiB units; Poisson 20/s and 200/s, and all 64 at once (saturating)"}
         for label, mode, rate in (("readahead_poisson20", gfs.MODE_READAHEAD, 20.0),
                                   ("ondemand_poisson20", gfs.MODE_ONDEMAND, 20.0),
+                                  ("readahead_poisson200", gfs.MODE_READAHEAD, 200.0),
                                   ("readahead_saturating", gfs.MODE_READAHEAD, None),
                                   ("ondemand_saturating", gfs.MODE_ONDEMAND, None)):
             serv[label], serving_results[label] = serving_bench(args, xf, mode, rate)

@@ -169,7 +169,9 @@ typedef struct gfs_stats {
   uint64_t buffer_hits;       /* GFS_MODE_PAPER: misses served from the private buffer */
   uint64_t host_controls;     /* opens and closes requested by the device (gopen, gclose) */
   uint64_t host_merged;       /* requests a host thread served together with the request before them */
-  uint64_t reserved[2];
+  uint64_t run_cuts;          /* requests cut short because another gread mapped one of their pages
+                               * while they were being installed (the rest requested separately) */
+  uint64_t reserved[1];
 } gfs_stats;
 
 /* Per host I/O thread counters since the last gfs_reset_cache (Section 3.2: the

@@ -1256,6 +1256,7 @@ static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const F
   }
   __syncwarp();
   if (cut <= L) {
+    if (lane == 0) stat_add(g, ST_RUN_CUTS, 1);
     // Pages after the cut that did go into the table are mapped and FILLING:
     // readers may already wait for them, so each maximal run of them is requested
     // on its own (only concurrent greads race like this; one gread at a time never does).

@@ -1120,6 +1120,7 @@ int gfs_get_stats(gfs_ctx* ctx, gfs_stats* o, void* stream) {
   o->buffer_hits = st[ST_BUFHITS];
   o->host_controls = ctx->io->stats.controls.load();
   o->host_merged = ctx->io->stats.merged.load();
+  o->run_cuts = st[ST_RUN_CUTS];
   return 0;
 }
 

@@ -48,7 +48,7 @@ GFS_HD inline uint64_t key_page(uint64_t key) { return key & 0xffffffffull; }
 // Statistic slots in the device counter block (order = gfs_stats fields).
 enum : int {
   ST_GREADS = 0, ST_HITS, ST_MISSES, ST_COALESCED, ST_RPCS, ST_PAGES, ST_BYTES, ST_RA_SYNC, ST_RA_ASYNC,
-  ST_EVICT, ST_EVICT_UNCONSUMED, ST_RETRIES, ST_TIMEOUTS, ST_EIO, ST_ENOMEM, ST_BUFHITS, ST_COUNT
+  ST_EVICT, ST_EVICT_UNCONSUMED, ST_RETRIES, ST_TIMEOUTS, ST_EIO, ST_ENOMEM, ST_BUFHITS, ST_RUN_CUTS, ST_COUNT
 };
 
 // Control counters in device memory (one 128-byte line per hot counter).

@@ -45,11 +45,11 @@ STATS_FIELDS = ["greads", "hits", "misses", "coalesced_waits", "rpcs", "pages_fe
                 "ra_pages_sync", "ra_pages_async", "evictions", "unconsumed_evictions", "retries", "timeouts",
                 "eio", "enomem", "host_requests", "host_preads", "host_bytes", "host_copies", "host_errors",
                 "trace_rpc_count", "trace_evict_count", "host_ns_pread", "host_ns_wait_buf", "host_ns_idle",
-                "buffer_hits", "host_controls", "host_merged"]
+                "buffer_hits", "host_controls", "host_merged", "run_cuts"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 2)]
+    _fields_ = [(n, u64) for n in STATS_FIELDS] + [("reserved", u64 * 1)]
 
 
 class ThreadStat(ctypes.Structure):

@@ -100,7 +100,7 @@ def test_struct_layouts_match_header(tmp_path):
               ("gfs_thread_stat", gfs.ThreadStat, ["requests", "first_request_ns", "bytes"]),
               ("gfs_io_rec", gfs.IoRec, ["offset", "bytes", "fid", "thread", "t_ns"]),
               ("gfs_stat", gfs.Stat, ["size", "advice", "mapped"]),
-              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "host_controls", "host_merged", "reserved"]),
+              ("gfs_stats", gfs.Stats, ["greads", "host_errors", "trace_evict_count", "host_ns_idle", "buffer_hits", "host_controls", "host_merged", "run_cuts", "reserved"]),
               ("gfs_rpc_rec", gfs.RpcRec, ["npages", "page_lo"]),
               ("gfs_evict_rec", gfs.EvictRec, ["new_fid", "new_page"]),
               ("gfs_scan_args", gfs.ScanArgs, ["read_len", "fused", "reserved"])]

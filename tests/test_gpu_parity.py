@@ -173,6 +173,32 @@ def test_small_pages_streaming_and_cached_exact(torch_cuda, gfs, datadir, page, 
 
 
 
+@pytest.mark.parametrize("xfer", [1, 2])
+@pytest.mark.parametrize("page", [4 * KiB, 16 * KiB])
+def test_overlapping_greads_race_for_the_same_pages_exact(torch_cuda, gfs, datadir, xfer, page):
+    """Greads of 256 KiB every 16 KiB: sixteen blocks read every page at about the same
+    time, so runs being installed meet pages other greads map meanwhile (the request is cut
+    there and the pages after it are requested on their own).  Every stride stays exact,
+    and while the file fits each page is fetched exactly once."""
+    size = 12 * MiB + 333
+    path = _file(datadir, 34, size)
+    npages = (size + page - 1) // page
+    with gfs.Context(cache_bytes=32 * MiB, page_size=page, xfer=xfer, max_rpc_pages=64, ra_cap_pages=63,
+                     debug_counts=1) as ctx:
+        fid = ctx.open(path)
+        cuts = 0
+        for rep in range(3):
+            ctx.reset_cache()
+            out = ctx.scan(fid, 16 * KiB, read_len=256 * KiB, blocks=128, threads=256, fused=rep == 1)
+            torch_cuda.cuda.synchronize()
+            _check_scan(gfs, path, 16 * KiB, *out, read_len=256 * KiB)
+            st = ctx.stats()
+            assert st["timeouts"] == 0 and st["eio"] == 0 and st["enomem"] == 0
+            assert (ctx.fetch_counts(npages) == 1).all()
+            cuts += st["run_cuts"]
+        print("requests cut by a concurrent install:", cuts)
+
+
 @pytest.mark.parametrize("xfer", XFERS)
 @pytest.mark.parametrize("threads", [256, 512])
 def test_streaming_big_file_exact(torch_cuda, gfs, datadir, threads, xfer):
