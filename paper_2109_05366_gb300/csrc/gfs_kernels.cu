@@ -1,7 +1,7 @@
-// Kernels of the GPU file-read path: independent greads, the scan with the file
-// opened on the device, cache purge, drain and reset, the checksum kernel of the
-// CPU-I/O baseline, the link probe, and the launch of the stride scan (whose
-// instances are compiled in gfs_scan_wide.cu and gfs_scan_narrow.cu).
+// Kernels of the GPU file-read path: the scan with the file opened on the device,
+// cache purge, drain and reset, the checksum kernel of the CPU-I/O baseline, the
+// link probe, and the launches of the stride scan and of independent greads
+// (whose instances are compiled in gfs_scan_wide.cu and gfs_scan_narrow.cu).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <errno.h>
@@ -11,17 +11,6 @@
 #include "gfs_scan.cuh"
 
 namespace gfs {
-
-__global__ void __launch_bounds__(512, 1) k_read_many(DevHandle g, int fid, uint32_t n, const uint64_t* off,
-                                                    const uint64_t* len, const uint64_t* dst, uint8_t* buf,
-                                                    long long* ret) {
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
-    long long r = dev::gread(g, (int)blockIdx.x, fid, off[i], len[i], buf + dst[i]);
-    if (threadIdx.x == 0) ret[i] = r;
-    __syncthreads();
-  }
-  block_help_drain(g);
-}
 
 // The stride scan with the file opened on the device (Section 2.2: GPU threads
 // open, read and close files through GPUfs calls): every block gopens `path`,
@@ -205,7 +194,12 @@ int launch_purge(const DevHandle& g, uint32_t fid, cudaStream_t s) {
 int launch_read_many(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
                      const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
                      cudaStream_t s) {
-  k_read_many<<<blocks, threads, 0, s>>>(g, fid, n, d_off, d_len, d_dst, d_buf, (long long*)d_ret);
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return -19;
+  if (scan_variant(threads, blocks, device) == 0)
+    launch_read_many_wide(g, fid, n, d_off, d_len, d_dst, d_buf, d_ret, blocks, threads, s);
+  else
+    launch_read_many_narrow(g, fid, n, d_off, d_len, d_dst, d_buf, d_ret, blocks, threads, s);
   return cuda_err(cudaGetLastError());
 }
 

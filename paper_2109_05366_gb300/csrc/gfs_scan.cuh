@@ -104,6 +104,22 @@ __global__ void __launch_bounds__(MAXT, MINB) k_scan(DevHandle g, int fid, unsig
   block_help_drain(g);
 }
 
+// Independent greads (Section 2.2): block b serves reads b, b + B, ...; read i
+// copies len[i] bytes at off[i] to buf + dst[i] and stores the return value in
+// ret[i].  MAXT, MINB as for k_scan: a small read costs a block mostly control-path
+// latency, so the reads in flight grow with the blocks resident per SM.
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_read_many(DevHandle g, int fid, uint32_t n, const uint64_t* off,
+                                                    const uint64_t* len, const uint64_t* dst, uint8_t* buf,
+                                                    long long* ret) {
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    long long r = dev::gread(g, (int)blockIdx.x, fid, off[i], len[i], buf + dst[i]);
+    if (threadIdx.x == 0) ret[i] = r;
+    __syncthreads();
+  }
+  block_help_drain(g);
+}
+
 template <bool FUSED, int MAXT, int MINB>
 inline void launch_scan_as(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides,
                            uint8_t* bufs, uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash,
@@ -113,8 +129,8 @@ inline void launch_scan_as(const DevHandle& g, int fid, const gfs_scan_args& a, 
                                                            (unsigned long long*)d_sum, (unsigned long long*)d_hash);
 }
 
-// Launchers and occupancy of the two instances (gfs_scan_wide.cu: <512, 1>;
-// gfs_scan_narrow.cu: <256, 4>).
+// Launchers and occupancy of the two instances of k_scan and k_read_many
+// (gfs_scan_wide.cu: <512, 1>; gfs_scan_narrow.cu: <256, 4>).
 void launch_scan_wide(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides, uint8_t* bufs,
                       uint64_t buf_stride, int64_t* d_count, uint64_t* d_sum, uint64_t* d_hash, cudaStream_t s);
 void launch_scan_narrow(const DevHandle& g, int fid, const gfs_scan_args& a, unsigned long long nstrides,
@@ -122,5 +138,11 @@ void launch_scan_narrow(const DevHandle& g, int fid, const gfs_scan_args& a, uns
                         cudaStream_t s);
 cudaError_t scan_occupancy_wide(bool fused, int threads, int* per_sm);
 cudaError_t scan_occupancy_narrow(bool fused, int threads, int* per_sm);
+void launch_read_many_wide(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                           const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
+                           cudaStream_t s);
+void launch_read_many_narrow(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                             const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
+                             cudaStream_t s);
 
 }  // namespace gfs

@@ -1,4 +1,5 @@
-// The stride-scan kernel instance <256, 4>: grids of more than two 256-thread blocks per SM.
+// The stride-scan and read kernel instances <256, 4>: grids of more than two blocks of at
+// most 256 threads per SM (four 256-thread or eight 128-thread blocks fit an SM).
 #include "gfs_scan.cuh"
 
 namespace gfs {
@@ -12,6 +13,12 @@ void launch_scan_narrow(const DevHandle& g, int fid, const gfs_scan_args& a, uns
 cudaError_t scan_occupancy_narrow(bool fused, int threads, int* per_sm) {
   return fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_scan<true, 256, 4>, threads, 0)
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_scan<false, 256, 4>, threads, 0);
+}
+
+void launch_read_many_narrow(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                      const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
+                      cudaStream_t s) {
+  k_read_many<256, 4><<<blocks, threads, 0, s>>>(g, fid, n, d_off, d_len, d_dst, d_buf, (long long*)d_ret);
 }
 
 }  // namespace gfs

@@ -1,4 +1,5 @@
-// The stride-scan kernel instance <512, 1>: 512-thread blocks, or grids of at most two blocks per SM.
+// The stride-scan and read kernel instances <512, 1>: 512-thread blocks, or grids of at
+// most two blocks per SM.
 #include "gfs_scan.cuh"
 
 namespace gfs {
@@ -12,6 +13,12 @@ void launch_scan_wide(const DevHandle& g, int fid, const gfs_scan_args& a, unsig
 cudaError_t scan_occupancy_wide(bool fused, int threads, int* per_sm) {
   return fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_scan<true, 512, 1>, threads, 0)
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_scan<false, 512, 1>, threads, 0);
+}
+
+void launch_read_many_wide(const DevHandle& g, int fid, uint32_t n, const uint64_t* d_off, const uint64_t* d_len,
+                      const uint64_t* d_dst, uint8_t* d_buf, int64_t* d_ret, uint32_t blocks, uint32_t threads,
+                      cudaStream_t s) {
+  k_read_many<512, 1><<<blocks, threads, 0, s>>>(g, fid, n, d_off, d_len, d_dst, d_buf, (long long*)d_ret);
 }
 
 }  // namespace gfs

@@ -53,7 +53,7 @@ def _tiles(size, n, seed, page):
     return offs, lens
 
 
-def _read_many(torch, gfs, ctx, fid, offs, lens, blocks=64, stream=None):
+def _read_many(torch, gfs, ctx, fid, offs, lens, blocks=64, stream=None, threads=256):
     dsts, pos = [], 0
     for ln in lens:
         dsts.append(pos)
@@ -65,7 +65,7 @@ def _read_many(torch, gfs, ctx, fid, offs, lens, blocks=64, stream=None):
     d_ret = torch.full((len(offs),), -999, dtype=torch.int64, device="cuda")
     if stream is not None:  # the inputs were written on the current stream
         stream.wait_stream(torch.cuda.current_stream())
-    ctx.read_many(fid, d_off, d_len, d_dst, d_buf, d_ret, blocks=blocks, threads=256, stream=stream)
+    ctx.read_many(fid, d_off, d_len, d_dst, d_buf, d_ret, blocks=blocks, threads=threads, stream=stream)
     return dsts, d_buf, d_ret
 
 
@@ -87,8 +87,9 @@ def _touched(offs, lens, size, page):
     return pages
 
 
-@pytest.mark.parametrize("xfer", [0, 1, 2])
-def test_small_pages_random_hint_fetches_only_touched_pages(torch_cuda, gfs, datadir, xfer):
+@pytest.mark.parametrize("xfer,blocks,threads", [(0, 64, 256), (1, 64, 256), (2, 64, 256), (0, 1216, 128),
+                                                  (2, 1216, 128)])
+def test_small_pages_random_hint_fetches_only_touched_pages(torch_cuda, gfs, datadir, xfer, blocks, threads):
     torch = torch_cuda
     P = 4 * KiB
     size = 32 * MiB + 999
@@ -98,7 +99,7 @@ def test_small_pages_random_hint_fetches_only_touched_pages(torch_cuda, gfs, dat
     with gfs.Context(cache_bytes=64 * MiB, page_size=P, xfer=xfer, max_rpc_pages=64, ra_cap_pages=63) as ctx:
         fid = ctx.open(path)
         ctx.fadvise(fid, gfs.ADV_RANDOM)
-        dsts, d_buf, d_ret = _read_many(torch, gfs, ctx, fid, offs, lens)
+        dsts, d_buf, d_ret = _read_many(torch, gfs, ctx, fid, offs, lens, blocks=blocks, threads=threads)
         torch.cuda.synchronize()
         _check(ref, offs, lens, dsts, d_buf, d_ret)
         st = ctx.stats()
@@ -156,14 +157,18 @@ def test_mixed_sequential_and_random_streams_exact(torch_cuda, gfs, datadir, xfe
         assert ctx.stats()["timeouts"] == 0
 
 
-@pytest.mark.parametrize("cache_mib", [64, 256])  # 1024 frames (scanned whole), 4096 (scanned by windows)
+@pytest.mark.parametrize("cache_mib,blocks,threads", [
+    (64, 296, 256),    # 1024 frames (scanned whole)
+    (256, 296, 256),   # 4096 frames (scanned by windows)
+    (256, 1216, 128),  # eight blocks per SM: the <256, 4> instance of the read kernel
+])
 @pytest.mark.parametrize("xfer", [0, 2])
-def test_thrashing_random_reads_many_blocks(torch_cuda, gfs, datadir, xfer, cache_mib):
-    """4 KiB reads at random places of a file 8x-32x the cache, 64 KiB pages, 296 blocks:
-    every miss needs the demand fallback (no page is ever consumed whole).  Every read
-    must succeed with the file's bytes: a reader waiting on its pinned page may see an
-    evictor's transient claim, and a gread may evict pages other greads allocated after
-    it started."""
+def test_thrashing_random_reads_many_blocks(torch_cuda, gfs, datadir, xfer, cache_mib, blocks, threads):
+    """4 KiB reads at random places of a file 8x-32x the cache, 64 KiB pages, 296 or 1216
+    blocks: every miss needs the demand fallback (no page is ever consumed whole).  Every
+    read must succeed with the file's bytes: a reader waiting on its pinned page may see
+    an evictor's transient claim, and a gread may evict pages other greads allocated
+    after it started."""
     torch = torch_cuda
     P, R = 64 * KiB, 4 * KiB
     size = 2048 * MiB if cache_mib == 256 else 512 * MiB
@@ -179,7 +184,7 @@ def test_thrashing_random_reads_many_blocks(torch_cuda, gfs, datadir, xfer, cach
         d_dst = torch.arange(n, dtype=torch.int64, device="cuda") * R
         d_buf = torch.zeros(n * R, dtype=torch.uint8, device="cuda")
         d_ret = torch.full((n,), -999, dtype=torch.int64, device="cuda")
-        ctx.read_many(fid, d_off, d_len, d_dst, d_buf, d_ret, blocks=296, threads=256)
+        ctx.read_many(fid, d_off, d_len, d_dst, d_buf, d_ret, blocks=blocks, threads=threads)
         torch.cuda.synchronize()
         st = ctx.stats()
         ret = d_ret.cpu().numpy()
