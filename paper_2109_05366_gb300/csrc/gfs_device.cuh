@@ -1180,15 +1180,23 @@ static __device__ int finish_request(const DevHandle& g, uint32_t fid, const Fil
                                      unsigned long long mark_end, int mark_idx, const uint32_t* s_frames,
                                      unsigned long long deadline, bool allow_self);
 
+static __device__ uint32_t take_run_lra(const DevHandle& g, int stream, uint32_t L, uint32_t* s_frames);
+
+// Whether the frames of `stream`'s requests come from its own LRA queue (Section 5.1).
+__device__ __forceinline__ bool own_queue(const DevHandle& g, int stream) {
+  return g.repl == GFS_REPL_TB_LRA && stream >= 0 && (uint32_t)stream < g.paper_streams;
+}
+
 // Warp: pages 1 .. of a request whose page 0 is installed (page i is p + i, a
 // readahead page when i >= demand).  The run is cut, as one page at a time would
 // cut it, at EOF, at the first page already in the table and at the first
 // readahead page fetched since the last reset (R8), then by take_run.  Victims
 // lose their old pages in page order, metadata is written a lane per page (one
-// sequence-number add), and the table entries go in in page order.  Returns how
+// sequence-number add), and the table entries go in in page order.  Frames come
+// from take_run, or from the stream's own LRA queue (take_run_lra).  Returns how
 // many pages from page 1 on were installed; their frames are in s_frames[1 ..].
-static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const FileDev& fi, unsigned long long p,
-                                       uint32_t want, uint32_t demand, unsigned long long seq0,
+static __device__ uint32_t install_run(const DevHandle& g, int stream, uint32_t fid, const FileDev& fi,
+                                       unsigned long long p, uint32_t want, uint32_t demand, unsigned long long seq0,
                                        unsigned long long deadline, uint32_t* s_frames) {
   const int lane = lane_id();
   unsigned long long lim = want - 1ull;
@@ -1214,7 +1222,7 @@ static __device__ uint32_t install_run(const DevHandle& g, uint32_t fid, const F
       }
     }
   }
-  L = take_run(g, L, demand, deadline, s_frames);
+  L = own_queue(g, stream) ? take_run_lra(g, stream, L, s_frames) : take_run(g, L, demand, deadline, s_frames);
   if (L == 0) return 0;
   evict_run(g, s_frames + 1, L, fid, p + 1);
   unsigned long long a0 = 0;
@@ -1293,8 +1301,7 @@ static __device__ int take_frame_lra(const DevHandle& g, int stream, bool for_ra
 // gread waits for, `awaited`).
 static __device__ int take_for(const DevHandle& g, int stream, bool for_ra, bool awaited, unsigned long long seq0,
                                unsigned long long new_key, unsigned long long deadline) {
-  if (g.repl == GFS_REPL_TB_LRA && stream >= 0 && (uint32_t)stream < g.paper_streams)
-    return take_frame_lra(g, stream, for_ra, seq0, new_key, deadline);
+  if (own_queue(g, stream)) return take_frame_lra(g, stream, for_ra, seq0, new_key, deadline);
   return take_frame(g, for_ra, seq0, new_key, deadline, awaited);
 }
 
@@ -1306,9 +1313,8 @@ static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid
   if (want > g.max_rpc_pages) want = g.max_rpc_pages;
   uint32_t n = 0;
   for (uint32_t i = 0; i < want; ++i) {
-    // with the consumed FIFO, the pages after the first are taken as one run
-    if (i == 1 && g.repl != GFS_REPL_TB_LRA)
-      return 1 + (int)install_run(g, fid, fi, p, want, demand, seq0, deadline, s_frames);
+    // the pages after the first are taken and installed as one run
+    if (i == 1) return 1 + (int)install_run(g, stream, fid, fi, p, want, demand, seq0, deadline, s_frames);
     const unsigned long long q = p + i;
     if (q >= fi.npages) break;
     const unsigned long long key = make_key(fid, q);
@@ -1577,6 +1583,56 @@ static __device__ int take_frame_lra(const DevHandle& g, int stream, bool for_ra
     }
   }
   return f;
+}
+
+// Warp: frames for pages 1 .. L of a request of `stream` from its own LRA queue
+// (Section 5.1), taken into s_frames[1 ..] exactly as one take_frame_lra per page
+// would take them after page 0: never-used frames while the queue is below its
+// quota (one fetch-and-add for the run), then the queue's frames oldest first,
+// each frame tried moving to the newest end.  A frame taken for an earlier page of
+// the run is in use (one take_frame_lra per page would have installed it), so it is
+// passed over.  The queue always holds page 0's frame here, so no frame is adopted.
+// Returns how many pages, from page 1 on, got a frame; claimed victims still hold
+// their old keys.
+static __device__ uint32_t take_run_lra(const DevHandle& g, int stream, uint32_t L, uint32_t* s_frames) {
+  const int lane = lane_id();
+  uint32_t got = 0;
+  if (lane == 0 && L > 0) {
+    const uint32_t base = (uint32_t)stream * g.quota;
+    uint32_t len = g.lra_len[stream], head = g.lra_head[stream];
+    unsigned long long u0 = 0, nu = 0;  // never-used frames u0 .. u0 + nu - 1 taken by this run
+    if (len < g.quota && ld_rlx64(&g.ctrl->next_unused.v) < g.n_frames) {
+      const uint32_t want = g.quota - len < L ? g.quota - len : L;
+      u0 = atomicAdd(&g.ctrl->next_unused.v, (unsigned long long)want);
+      if (u0 < g.n_frames) nu = g.n_frames - u0 < want ? g.n_frames - u0 : want;
+      for (uint32_t j = 0; j < (uint32_t)nu; ++j) {
+        g.lra[base + (head + len) % g.quota] = (uint32_t)(u0 + j);
+        ++len;
+        s_frames[1 + got++] = (uint32_t)(u0 + j);
+      }
+    }
+    while (got < L) {
+      int f = -1;
+      for (uint32_t k = 0; k < len; ++k) {
+        const uint32_t cand = g.lra[base + head];
+        const bool mine = cand >= u0 && cand < u0 + nu;
+        const int r = mine ? 0 : frame_claim_own(g, (int)cand);
+        g.lra[base + (head + len) % g.quota] = cand;  // oldest -> newest
+        head = (head + 1) % g.quota;
+        if (r == 1) {
+          f = (int)cand;
+          break;
+        }
+      }
+      if (f < 0) break;
+      s_frames[1 + got++] = (uint32_t)f;
+    }
+    g.lra_head[stream] = head;
+    g.lra_len[stream] = len;
+  }
+  got = (uint32_t)bcast((int)got);
+  __syncwarp();
+  return got;
 }
 
 // Section 4.1 miss: allocate a frame for p, then serve it from the stream's
