@@ -1025,9 +1025,13 @@ def run_gfs(args):
         h2d = gfs.probe_h2d(GiB, 16 * MiB, 3)
         h2d_page = gfs.probe_h2d(GiB, page, 3)
         prd = gfs.probe_pread(path, 16, 4 * MiB, 2)
+        # the same preads into 64 MiB buffers per thread (1 GiB in all, larger than the
+        # CPU's caches): what a pread costs when its destination lives in host DRAM
+        prd_dram = gfs.probe_pread(path, 16, 64 * MiB, 2)
         pull = gfs.probe_pull(GiB, 3)
         extra["link_probe"] = {"h2d_pinned_16MiB_gbps": round(h2d, 1), "h2d_pinned_page_gbps": round(h2d_page, 1),
-                               "pread_16thr_gbps": round(prd, 1), "gpu_read_host_gbps": round(pull, 1)}
+                               "pread_16thr_gbps": round(prd, 1), "pread_16thr_64MiB_buffers_gbps": round(prd_dram, 1),
+                               "gpu_read_host_gbps": round(pull, 1)}
         # the link the chosen transfer moves data over: mapped = GPU reads of host
         # memory; pull = host pread + GPU reads; dma = host pread + copy engine
         if args.xfer == "mapped" and mapped:

@@ -666,11 +666,12 @@ def test_readahead_per_block_lra_serialized_logs_match_oracle(torch_cuda, gfs, d
 
 
 @pytest.mark.parametrize("xfer", XFERS)
-def test_readahead_per_block_lra_concurrent_exact(torch_cuda, gfs, datadir, xfer):
+@pytest.mark.parametrize("page,ra_cap", [(64 * KiB, 15), (4 * KiB, 63)])  # 4 KiB: 64-page runs from each queue
+def test_readahead_per_block_lra_concurrent_exact(torch_cuda, gfs, datadir, xfer, page, ra_cap):
     size = 128 * MiB + 4096
     path = _file(datadir, 11, size)
-    with gfs.Context(cache_bytes=32 * MiB, page_size=64 * KiB, mode=0, replacement=1, ra_cap_pages=15,
-                     max_rpc_pages=32, xfer=xfer, timeout_ns=5 * 10**9) as ctx:
+    with gfs.Context(cache_bytes=32 * MiB, page_size=page, mode=0, replacement=1, ra_cap_pages=ra_cap,
+                     max_rpc_pages=64, xfer=xfer, timeout_ns=5 * 10**9) as ctx:
         fid = ctx.open(path)
         for _ in range(2):
             out = ctx.scan(fid, MiB, blocks=96, threads=256)
