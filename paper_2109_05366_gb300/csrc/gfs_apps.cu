@@ -73,6 +73,22 @@ __global__ void __launch_bounds__(kThreads) k_rowdot(DevHandle g, int fid, uint3
       if (!dev::block_help(g, -1, true)) break;
 }
 
+// One value of the histogram (warp-collective: every lane calls it, `have` says
+// whether the lane holds a value).  Bins below kSmemBins go to shared memory; the
+// rest to global memory, lanes holding the same value adding once; values at or
+// above nbins are counted in `bad`.
+__device__ __forceinline__ void count_value(uint32_t* sh, uint32_t* hist, uint32_t nbins, uint32_t v, bool have,
+                                            unsigned long long& bad) {
+  if (have && v < kSmemBins && v < nbins) atomicAdd(&sh[v], 1u);
+  if (have && v >= nbins) ++bad;
+  const bool far = have && v >= kSmemBins && v < nbins;
+  const unsigned fm = __ballot_sync(dev::kFull, far);
+  if (far) {
+    const unsigned same = __match_any_sync(fm, v);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(same) - 1)) atomicAdd(&hist[v], (uint32_t)__popc(same));
+  }
+}
+
 // Block b reads pieces b, b + B, ... of the int32 file and counts values.  Bins
 // below kSmemBins are counted in shared memory; the rest with warp-aggregated
 // global atomics (lanes holding the same value add once).
@@ -96,18 +112,27 @@ __global__ void __launch_bounds__(kThreads) k_histogram(DevHandle g, int fid, un
     }
     const uint32_t nv = (uint32_t)(n / 4);
     const uint32_t* vals = reinterpret_cast<const uint32_t*>(buf);
-    for (uint32_t base = 0; base < nv; base += blockDim.x) {
+    // 16-byte loads, two per thread in flight (the buffer is 256-byte aligned), then
+    // the values left over after the last whole 16 bytes one per thread; every
+    // trip count is block-uniform (the far-bin path is warp-collective)
+    const uint4* v4 = reinterpret_cast<const uint4*>(buf);
+    const uint32_t n4 = nv / 4, nt = blockDim.x;
+    for (uint32_t base = 0; base < n4; base += 2 * nt) {
+      const uint32_t i = base + threadIdx.x, j = i + nt;
+      const uint4 a = i < n4 ? v4[i] : make_uint4(0u, 0u, 0u, 0u);
+      const uint4 b = j < n4 ? v4[j] : make_uint4(0u, 0u, 0u, 0u);
+      count_value(sh, hist, nbins, a.x, i < n4, bad);
+      count_value(sh, hist, nbins, a.y, i < n4, bad);
+      count_value(sh, hist, nbins, a.z, i < n4, bad);
+      count_value(sh, hist, nbins, a.w, i < n4, bad);
+      count_value(sh, hist, nbins, b.x, j < n4, bad);
+      count_value(sh, hist, nbins, b.y, j < n4, bad);
+      count_value(sh, hist, nbins, b.z, j < n4, bad);
+      count_value(sh, hist, nbins, b.w, j < n4, bad);
+    }
+    for (uint32_t base = 4 * n4; base < nv; base += nt) {
       const uint32_t i = base + threadIdx.x;
-      const bool have = i < nv;
-      const uint32_t v = have ? vals[i] : 0u;
-      if (have && v < kSmemBins && v < nbins) atomicAdd(&sh[v], 1u);
-      if (have && v >= nbins) ++bad;
-      const bool far = have && v >= kSmemBins && v < nbins;
-      const unsigned fm = __ballot_sync(dev::kFull, far);
-      if (far) {
-        const unsigned same = __match_any_sync(fm, v);
-        if ((threadIdx.x & 31) == (uint32_t)(__ffs(same) - 1)) atomicAdd(&hist[v], (uint32_t)__popc(same));
-      }
+      count_value(sh, hist, nbins, i < nv ? vals[i] : 0u, i < nv, bad);
     }
     __syncthreads();
   }
