@@ -1,9 +1,11 @@
 // A kernel written the way a user of the library writes one: it includes the
 // public device API (include/gfs_device.h) and nothing else of the library, and
-// links libgfs_device.a (relocatable device code).  Every threadblock opens the
-// file (gopen), optionally sets an access hint (gfadvise), checks gfstat, reads
-// its strides with gread into its own buffer, sums the bytes, and closes the
-// file (gclose).  Built by tests/test_gpu_devapi.py with nvcc.
+// links libgfs_device.a (relocatable device code).  In user_scan every threadblock
+// opens the file (gopen), optionally sets an access hint (gfadvise), checks
+// gfstat, reads its strides with gread into its own buffer, sums the bytes, and
+// closes the file (gclose).  In user_replay one threadblock replays a list of
+// greads one at a time, each under its own reader identity (gread_as).  Built by
+// tests/test_gpu_devapi.py with nvcc.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -55,7 +57,35 @@ __global__ void __launch_bounds__(256) k_user(const __grid_constant__ gfs_dev g,
   }
 }
 
+// One threadblock: read i copies len[i] bytes at off[i] of file `fid` into
+// buf + dst[i] as reader reader[i], and stores the return value in ret[i].
+__global__ void __launch_bounds__(256) k_replay(const __grid_constant__ gfs_dev g, int fid, uint32_t n,
+                                                const int* reader, const unsigned long long* off,
+                                                const unsigned long long* len, const unsigned long long* dst,
+                                                uint8_t* buf, long long* ret) {
+  for (uint32_t i = 0; i < n; ++i) {
+    const long long r = gread_as(&g, reader[i], fid, off[i], len[i], buf + dst[i]);
+    if (threadIdx.x == 0) ret[i] = r;
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+// handle: the bytes gfs_device_handle wrote; fid: a file id open in the context;
+// reader, off, len, dst, ret: n entries each (device memory); buf: device memory
+// covering every dst[i] + len[i].  Returns a cudaError_t.
+extern "C" int user_replay(const void* handle, uint64_t handle_bytes, int fid, uint32_t n, const void* reader,
+                           const void* off, const void* len, const void* dst, void* buf, void* ret, void* stream) {
+  if (handle_bytes == 0 || handle_bytes > sizeof(gfs_dev)) return (int)cudaErrorInvalidValue;
+  gfs_dev g;
+  memset(&g, 0, sizeof(g));
+  memcpy(&g, handle, handle_bytes);
+  k_replay<<<1, 256, 0, (cudaStream_t)stream>>>(g, fid, n, (const int*)reader, (const unsigned long long*)off,
+                                                (const unsigned long long*)len, (const unsigned long long*)dst,
+                                                (uint8_t*)buf, (long long*)ret);
+  return (int)cudaGetLastError();
+}
 
 // handle: the bytes gfs_device_handle wrote; bufs: blocks * stride bytes;
 // cnt, sum: nstrides entries; info: 8 * blocks entries.  Returns a cudaError_t.

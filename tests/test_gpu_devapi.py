@@ -190,7 +190,74 @@ def user_lib(tmp_path_factory):
     lib.user_scan.restype = ctypes.c_int
     lib.user_scan.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_char_p, ctypes.c_int, ctypes.c_uint64,
                               ctypes.c_uint64, ctypes.c_uint32] + [ctypes.c_void_p] * 5
+    lib.user_replay.restype = ctypes.c_int
+    lib.user_replay.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32] + [ctypes.c_void_p] * 7
     return lib
+
+
+def _golden(name):
+    params, rows = {}, []
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        parts = line.split()
+        if parts[0] == "params":
+            params.update(kv.split("=") for kv in parts[1:])
+        else:
+            rows.append(parts)
+    return params, rows
+
+
+@pytest.mark.parametrize("xfer", [0, 1, 2])
+@pytest.mark.parametrize("name", ["policy_sequential_by_last_end.txt", "policy_reread_not_sequential.txt",
+                                  "policy_gread_keeps_own_frames.txt"])
+def test_user_kernel_replays_hand_derived_traces(torch_cuda, gfs, datadir, user_lib, name, xfer):
+    """The hand-derived traces over two readers and tiny caches (tests/golden/<name>),
+    replayed one gread at a time by a user kernel with gread_as: return values, the
+    delivered bytes of every successful gread, and the request and eviction logs
+    equal the derivation (R3's test on the reader's previous end, where a reader's
+    gread ends, and the class-3 rule that a gread never evicts its own frames, which
+    ends the too-wide gread with -ENOMEM at the device deadline)."""
+    torch = torch_cuda
+    params, rows = _golden(name)
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(datadir, int(params["seed"]), npg * page)
+    greads = [(int(r[1]), int(r[2]), int(r[3])) for r in rows if r[0] == "gread"]
+    rets = [int(r[1]) for r in rows if r[0] == "ret"]
+    kinds = {"DEMAND": 0, "SYNC_RA": 1, "ASYNC_RA": 2}
+    dst, pos = [], 0
+    for _, _, n in greads:
+        dst.append(pos)
+        pos += (n + 255) // 256 * 256
+    with gfs.Context(cache_bytes=int(params["frames"]) * page, page_size=page, mode=0,
+                     ra_cap_pages=int(params["ra_cap"]), async_ra=int(params["async_ra"]),
+                     reserve_frames=int(params["reserve"]), trace_capacity=256, max_rpc_pages=16, xfer=xfer,
+                     timeout_ns=300 * 10**6) as ctx:
+        fid = ctx.open(path)
+        h = ctx.device_handle(1, page)
+        d_rd = torch.tensor([s for s, _, _ in greads], dtype=torch.int32, device="cuda")
+        d_off = torch.tensor([o for _, o, _ in greads], dtype=torch.int64, device="cuda")
+        d_len = torch.tensor([n for _, _, n in greads], dtype=torch.int64, device="cuda")
+        d_dst = torch.tensor(dst, dtype=torch.int64, device="cuda")
+        buf = torch.zeros(pos, dtype=torch.uint8, device="cuda")
+        ret = torch.zeros(len(greads), dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        rc = user_lib.user_replay(h, len(h), fid, len(greads), d_rd.data_ptr(), d_off.data_ptr(), d_len.data_ptr(),
+                                  d_dst.data_ptr(), buf.data_ptr(), ret.data_ptr(), None)
+        assert rc == 0
+        torch.cuda.synchronize()
+        rpc, ev, nr, ne = ctx.trace()
+        st = ctx.stats()
+    assert ret.cpu().tolist() == rets
+    ref = np.fromfile(path, dtype=np.uint8)
+    got = buf.cpu().numpy()
+    for (_, o, n), d, r in zip(greads, dst, rets):
+        if r >= 0:
+            assert np.array_equal(got[d:d + r], ref[o:o + r])
+    assert rpc == [(0, int(r[1]), int(r[2]), kinds[r[3]]) for r in rows if r[0] == "rpc"]
+    assert ev == [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert st["unconsumed_evictions"] == int([r for r in rows if r[0] == "unconsumed_evictions"][0][1])
 
 
 @pytest.mark.parametrize("advice", [-1, 2])  # none, GFS_ADV_RANDOM

@@ -370,6 +370,38 @@ def test_golden_demand_run_awaited_page_only(tmp_path):
     sim.close_all()
 
 
+@pytest.mark.parametrize("name", [
+    "policy_sequential_by_last_end.txt",   # R3: sequential when the stream's last gread ended at p
+    "policy_reread_not_sequential.txt",    # R3: a stream's gread ends at the page after its last
+    "policy_gread_keeps_own_frames.txt",   # class 3 never takes a frame the same gread allocated
+])
+def test_golden_two_streams_and_own_frames(tmp_path, name):
+    """Hand-derived traces over two streams and tiny caches: returns, delivered bytes,
+    request and eviction logs (tests/golden/<name>)."""
+    params, rows = _parse(name)
+    page, npg = int(params["page_size"]), int(params["file_pages"])
+    path = _file(tmp_path, name[:-4], int(params["seed"]), npg * page)
+    sim = policy.PageCacheSim(page, int(params["frames"]), "readahead", ra_cap=int(params["ra_cap"]),
+                              reserve=int(params["reserve"]), async_ra=params["async_ra"] == "1")
+    sim.open(0, path)
+    ref = inputs.xorshift64_bytes(int(params["seed"]), npg * page)
+    greads = [(int(r[1]), int(r[2]), int(r[3])) for r in rows if r[0] == "gread"]
+    rets = [r for r in rows if r[0] == "ret"]
+    assert len(rets) == len(greads)
+    for (s, off, ln), r in zip(greads, rets):
+        n, data = sim.gread(s, 0, off, ln)
+        delivered = int(r[2]) if len(r) > 2 else int(r[1])
+        assert n == int(r[1])
+        assert data == ref[off:off + delivered]
+    want_rpc = [(0, int(r[1]), int(r[2]), _kind(r[3])) for r in rows if r[0] == "rpc"]
+    want_ev = [(int(r[1]), (0, int(r[2])), (0, int(r[3]))) for r in rows if r[0] == "evict"]
+    assert sim.rpc_log == want_rpc
+    assert sim.evict_log == want_ev
+    unc = int([r for r in rows if r[0] == "unconsumed_evictions"][0][1])
+    assert sim.stats.unconsumed_evictions == unc
+    sim.close_all()
+
+
 # ---------------------------------------------------------------- policy: invariants
 def test_fits_each_page_fetched_once(tmp_path):
     # config-1 shape scaled down: file fits the cache -> no eviction, no refetch
