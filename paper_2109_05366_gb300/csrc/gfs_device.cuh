@@ -1585,22 +1585,34 @@ static __device__ int take_frame_lra(const DevHandle& g, int stream, bool for_ra
   return f;
 }
 
+// Whether frame f could be claimed by frame_claim_own right now (no side effect).
+__device__ __forceinline__ bool lra_claimable(const DevHandle& g, uint32_t f) {
+  const uint32_t st = ld_acq(&g.fstate[f]);
+  if (!(st == FR_READY || st == FR_ERROR || (st == FR_EMPTY && ld_rlx64(&g.fkey[f]) == KEY_NONE))) return false;
+  return ld_rlx(&g.fpins[f]) == 0u;
+}
+
 // Warp: frames for pages 1 .. L of a request of `stream` from its own LRA queue
-// (Section 5.1), taken into s_frames[1 ..] exactly as one take_frame_lra per page
-// would take them after page 0: never-used frames while the queue is below its
-// quota (one fetch-and-add for the run), then the queue's frames oldest first,
-// each frame tried moving to the newest end.  A frame taken for an earlier page of
-// the run is in use (one take_frame_lra per page would have installed it), so it is
-// passed over.  The queue always holds page 0's frame here, so no frame is adopted.
-// Returns how many pages, from page 1 on, got a frame; claimed victims still hold
-// their old keys.
+// (Section 5.1), taken into s_frames[1 ..] as one take_frame_lra per page would
+// take them after page 0: never-used frames while the queue is below its quota
+// (one fetch-and-add for the run), then the queue's frames oldest first, each
+// frame tried moving to the newest end, a page giving up after trying every frame
+// of the queue once.  A frame taken for an earlier page of the run is in use, so it
+// is passed over.  The queue always holds page 0's frame here, so no frame is
+// adopted.  The queue is tried 32 entries at a time: every lane tests one entry
+// without side effects, lane 0 replays the one-page-at-a-time order on those
+// tests, and the entries it picks are claimed in parallel (a claim lost to another
+// block counts as a tried entry that was in use).  Returns how many pages, from
+// page 1 on, got a frame; claimed victims still hold their old keys.
 static __device__ uint32_t take_run_lra(const DevHandle& g, int stream, uint32_t L, uint32_t* s_frames) {
+  if (L == 0) return 0;
   const int lane = lane_id();
-  uint32_t got = 0;
-  if (lane == 0 && L > 0) {
-    const uint32_t base = (uint32_t)stream * g.quota;
-    uint32_t len = g.lra_len[stream], head = g.lra_head[stream];
-    unsigned long long u0 = 0, nu = 0;  // never-used frames u0 .. u0 + nu - 1 taken by this run
+  const uint32_t base = (uint32_t)stream * g.quota;
+  uint32_t len = 0, head = 0, got = 0;
+  unsigned long long u0 = 0, nu = 0;  // never-used frames u0 .. u0 + nu - 1 taken by this run
+  if (lane == 0) {
+    len = g.lra_len[stream];
+    head = g.lra_head[stream];
     if (len < g.quota && ld_rlx64(&g.ctrl->next_unused.v) < g.n_frames) {
       const uint32_t want = g.quota - len < L ? g.quota - len : L;
       u0 = atomicAdd(&g.ctrl->next_unused.v, (unsigned long long)want);
@@ -1610,27 +1622,57 @@ static __device__ uint32_t take_run_lra(const DevHandle& g, int stream, uint32_t
         ++len;
         s_frames[1 + got++] = (uint32_t)(u0 + j);
       }
+      g.lra_len[stream] = len;
     }
-    while (got < L) {
-      int f = -1;
-      for (uint32_t k = 0; k < len; ++k) {
-        const uint32_t cand = g.lra[base + head];
-        const bool mine = cand >= u0 && cand < u0 + nu;
-        const int r = mine ? 0 : frame_claim_own(g, (int)cand);
-        g.lra[base + (head + len) % g.quota] = cand;  // oldest -> newest
-        head = (head + 1) % g.quota;
-        if (r == 1) {
-          f = (int)cand;
+  }
+  len = (uint32_t)bcast((int)len);
+  head = (uint32_t)bcast((int)head);
+  got = (uint32_t)bcast((int)got);
+  u0 = bcast64(u0);
+  nu = bcast64(nu);
+  __syncwarp();
+  uint32_t streak = 0;  // entries tried since the last claim (the current page's tries)
+  while (got < L && len > 0 && streak < len) {
+    const uint32_t m = len < 32u ? len : 32u;
+    uint32_t cand = 0;
+    bool free_now = false;
+    if ((uint32_t)lane < m) {
+      cand = g.lra[base + (head + (uint32_t)lane) % g.quota];
+      free_now = !(cand >= u0 && cand < u0 + nu) && lra_claimable(g, cand);
+    }
+    const unsigned pm = __ballot_sync(kFull, free_now);
+    // lane 0 replays the order: the entries tried (0 .. end) and the ones to claim
+    unsigned want_mask = 0;
+    int end = (int)m - 1;
+    if (lane == 0) {
+      uint32_t k = got, st = streak;
+      for (uint32_t j = 0; j < m; ++j) {
+        if ((pm >> j) & 1u) {
+          want_mask |= 1u << j;
+          st = 0;
+          if (++k == L) {
+            end = (int)j;
+            break;
+          }
+        } else if (++st == len) {
+          end = (int)j;
           break;
         }
       }
-      if (f < 0) break;
-      s_frames[1 + got++] = (uint32_t)f;
     }
-    g.lra_head[stream] = head;
-    g.lra_len[stream] = len;
+    want_mask = (unsigned)bcast((int)want_mask);
+    end = bcast(end);
+    const bool claimed = ((want_mask >> lane) & 1u) && frame_claim_own(g, (int)cand) == 1;
+    const unsigned cm = __ballot_sync(kFull, claimed);
+    if (claimed) s_frames[1 + got + (uint32_t)__popc(cm & ((1u << lane) - 1u))] = cand;
+    // every entry tried moves to the newest end (a no-op when the queue is full)
+    if (len < g.quota && lane <= end) g.lra[base + (head + len + (uint32_t)lane) % g.quota] = cand;
+    for (int j = 0; j <= end; ++j) streak = ((cm >> j) & 1u) ? 0u : streak + 1u;
+    got += (uint32_t)__popc(cm);
+    head = (head + (uint32_t)end + 1u) % g.quota;
+    __syncwarp();
   }
-  got = (uint32_t)bcast((int)got);
+  if (lane == 0) g.lra_head[stream] = head;
   __syncwarp();
   return got;
 }
