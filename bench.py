@@ -944,6 +944,8 @@ def run_gfs(args):
     import torch
     import torch.distributed as dist
 
+    import inputs
+
     from paper_2109_05366_gb300 import gfs
 
     rank, world, local = dist_env()
@@ -1021,6 +1023,14 @@ def run_gfs(args):
         extra["cpuio_threads"] = args.host_threads
         one = gfs.cpuio_scan(path, stride, stride, 1, size, d_file, out, stream)
         extra["cpuio_naive_1thread_gbps"] = round(size / one / 1e9, 2)
+        # context: the same checksums on the host alone, every core (pread + sums, no GPU)
+        ncpu = os.cpu_count() or 1
+        cs = min(gfs.cpu_scan(path, stride, stride, ncpu)[3] for _ in range(2))
+        extra["cpu_scan"] = {"gbps": round(size / cs / 1e9, 2), "threads": ncpu,
+                             "kind": "host threads pread each stride and checksum it, no GPU (gfs_cpu_scan)"}
+        t0 = time.perf_counter()
+        extra["input_digest"] = {"file_bytes": size, "sha256_of_64MiB_piece_sha256s": inputs.file_digest(path),
+                                 "s": round(time.perf_counter() - t0, 2)}
         del d_file
         h2d = gfs.probe_h2d(GiB, 16 * MiB, 3)
         h2d_page = gfs.probe_h2d(GiB, page, 3)

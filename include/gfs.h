@@ -464,6 +464,18 @@ int gfs_cpuio_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_
                    uint64_t chunk, uint8_t* d_file, int64_t* d_count, uint64_t* d_sum,
                    uint64_t* d_hash, void* stream, double* seconds);
 
+/* CPU-only scan, a context figure beside the GPU path (no CUDA call): `threads`
+ * host threads pread strides of the file (stride s is [s*stride, s*stride +
+ * read_len), clipped at EOF; Section 6.1's per-stride checksums) and compute
+ * h_count[s], h_sum[s] (sum of the bytes mod 2^64) and h_hash[s] (sum of byte *
+ * (file offset + 1) mod 2^64), the same values the stride scan returns.
+ * h_count, h_sum, h_hash: caller-owned host arrays of ceil(size / stride)
+ * entries.  *seconds receives the wall time of the scan.  Returns 0, -EINVAL,
+ * -ENOMEM or the -errno of open / pread (h_count[s] = that -errno for a stride
+ * whose read failed). */
+int gfs_cpu_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t threads, int64_t* h_count,
+                 uint64_t* h_sum, uint64_t* h_hash, double* seconds);
+
 /* Host-link probes for the roofline: pinned host->device copy GB/s with
  * `chunk`-byte copies over `bytes`, and multi-thread pread GB/s of a file. */
 int gfs_probe_h2d(uint64_t bytes, uint64_t chunk, int reps, double* gbps);

@@ -180,3 +180,30 @@ def ensure_typed(path: str, kind: str, seed: int, n: int, **kw) -> str:
         if np.array_equal(head, ref):
             return path
     return write_f32(path, seed, n) if kind == "f32" else write_zipf(path, seed, n, **kw)
+
+
+def file_digest(path: str, piece: int = 64 << 20, threads: int | None = None) -> str:
+    """A record of a generated file's bytes: SHA-256 over the concatenated SHA-256
+    digests of its consecutive `piece`-byte pieces (the last one shorter), the pieces
+    hashed in parallel threads.  Hex string; an empty file digests zero pieces."""
+    import hashlib
+    from concurrent.futures import ThreadPoolExecutor
+    size = os.path.getsize(path)
+    offs = list(range(0, size, piece))
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        def one(off):
+            h = hashlib.sha256()
+            end = min(off + piece, size)
+            while off < end:
+                b = os.pread(fd, min(end - off, 8 << 20), off)
+                if not b:
+                    raise OSError("short read of %s at %d" % (path, off))
+                h.update(b)
+                off += len(b)
+            return h.digest()
+        with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+            parts = list(ex.map(one, offs))
+    finally:
+        os.close(fd)
+    return hashlib.sha256(b"".join(parts)).hexdigest()

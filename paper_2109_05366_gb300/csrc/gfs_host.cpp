@@ -1625,6 +1625,86 @@ int gfs_probe_pread(const char* path, uint32_t threads, uint64_t chunk, int reps
   return rc;
 }
 
+// ---------------------------------------------------------------- CPU-only scan
+// Checksums of n bytes at p, file offset `off` of p[0]: sum of the bytes and sum
+// of byte * (offset + 1), both mod 2^64.  Pieces of 2048 bytes keep the inner
+// sums in 32 bits (2048 * 255 * 2047 < 2^32), so the loops vectorise; each piece
+// adds (off + j0 + 1) * its byte sum + its sum of byte * local index.
+static void cpu_checksums(const uint8_t* p, uint64_t n, uint64_t off, uint64_t* sum, uint64_t* hash) {
+  uint64_t s = 0, h = 0;
+  for (uint64_t j0 = 0; j0 < n; j0 += 2048) {
+    const uint32_t m = (uint32_t)std::min<uint64_t>(2048, n - j0);
+    uint32_t ps = 0, pw = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+      ps += p[j0 + j];
+      pw += (uint32_t)p[j0 + j] * j;
+    }
+    s += ps;
+    h += (off + j0 + 1) * (uint64_t)ps + pw;
+  }
+  *sum += s;
+  *hash += h;
+}
+
+int gfs_cpu_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t threads, int64_t* h_count,
+                 uint64_t* h_sum, uint64_t* h_hash, double* seconds) {
+  if (!path || stride == 0 || read_len == 0 || threads == 0 || threads > 1024 || !h_count || !h_sum || !h_hash ||
+      !seconds)
+    return -EINVAL;
+  int fd = open(path, O_RDONLY | O_CLOEXEC);
+  if (fd < 0) return -errno;
+  struct stat st;
+  if (fstat(fd, &st) != 0) {
+    const int e = -errno;
+    close(fd);
+    return e;
+  }
+  const uint64_t size = (uint64_t)st.st_size;
+  const uint64_t ns = size ? (size + stride - 1) / stride : 0;
+  const uint64_t chunk = std::min<uint64_t>(read_len, 4ull << 20);
+  std::atomic<uint64_t> next{0};
+  std::atomic<int> fail{0};
+  const double t0 = now_s();
+  std::vector<std::thread> th;
+  for (uint32_t t = 0; t < threads; ++t)
+    th.emplace_back([&] {
+      std::vector<uint8_t> buf;
+      try {
+        buf.resize((size_t)chunk);
+      } catch (...) {
+        fail.store(-ENOMEM);
+        return;
+      }
+      for (;;) {
+        const uint64_t s = next.fetch_add(1);
+        if (s >= ns) break;
+        const uint64_t off = s * stride;
+        const uint64_t n = std::min<uint64_t>(read_len, size - off);
+        uint64_t sum = 0, hash = 0, got = 0;
+        int64_t cnt = 0;
+        while (got < n) {
+          const size_t want = (size_t)std::min<uint64_t>(chunk, n - got);
+          const ssize_t r = pread(fd, buf.data(), want, (off_t)(off + got));
+          if (r < 0 && errno == EINTR) continue;
+          if (r <= 0) {
+            cnt = r < 0 ? -errno : (int64_t)got;  // an error, or EOF (the file shrank)
+            break;
+          }
+          cpu_checksums(buf.data(), (uint64_t)r, off + got, &sum, &hash);
+          got += (uint64_t)r;
+          cnt = (int64_t)got;
+        }
+        h_count[s] = cnt;
+        h_sum[s] = sum;
+        h_hash[s] = hash;
+      }
+    });
+  for (auto& x : th) x.join();
+  *seconds = now_s() - t0;
+  close(fd);
+  return fail.load();
+}
+
 // ---------------------------------------------------------------- trace replay (Section 3.2)
 int gfs_replay_io(const char* path, const gfs_io_rec* recs, uint64_t n, uint32_t threads, double* seconds,
                   uint64_t* bytes) {

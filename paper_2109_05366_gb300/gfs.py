@@ -114,6 +114,7 @@ SIGNATURES = {
     "gfs_scan_graph": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ScanArgs), u32, vp, vp, vp, vp]),
     "gfs_cpuio_scan": (ctypes.c_int, [ctypes.c_char_p, u64, u64, u32, u64, vp, vp, vp, vp, vp,
                                       ctypes.POINTER(ctypes.c_double)]),
+    "gfs_cpu_scan": (ctypes.c_int, [ctypes.c_char_p, u64, u64, u32, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_h2d": (ctypes.c_int, [u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pread": (ctypes.c_int, [ctypes.c_char_p, u32, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gfs_probe_pull": (ctypes.c_int, [u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -429,6 +430,22 @@ def cpuio_scan(path: str, stride: int, read_len: int | None, threads: int, chunk
                                  _ptr(out[1]), _ptr(out[2]), _stream(stream), ctypes.byref(secs)),
            "gfs_cpuio_scan")
     return secs.value
+
+
+def cpu_scan(path: str, stride: int, read_len: int | None = None, threads: int = 0):
+    """CPU-only stride scan on `threads` host threads (0: every host core): (count, sum,
+    hash) numpy arrays of the per-stride checksums, and the seconds it took."""
+    read_len = stride if read_len is None else read_len
+    threads = threads or os.cpu_count() or 1
+    size = os.path.getsize(path)
+    ns = (size + stride - 1) // stride if size else 0
+    cnt = np.zeros(max(ns, 1), dtype=np.int64)
+    sm = np.zeros(max(ns, 1), dtype=np.uint64)
+    hs = np.zeros(max(ns, 1), dtype=np.uint64)
+    secs = ctypes.c_double(0.0)
+    _check(load().gfs_cpu_scan(path.encode(), stride, read_len, threads, cnt.ctypes.data, sm.ctypes.data,
+                               hs.ctypes.data, ctypes.byref(secs)), "gfs_cpu_scan")
+    return cnt[:ns], sm[:ns], hs[:ns], secs.value
 
 
 def probe_h2d(nbytes: int, chunk: int, reps: int = 3) -> float:

@@ -130,3 +130,19 @@ def test_every_zipf_value_written_whatever_the_split(tmp_path):
         st = inputs.xorshift64_step(st)
         want.append(bisect.bisect_right(cdf, (st >> 11) * 2.0 ** -53))
     assert list(x[-8:]) == want
+
+
+def test_file_digest_definition(tmp_path):
+    # SHA-256 over the pieces' SHA-256 digests, pieces in file order, the last one short
+    import hashlib
+    size, piece = 3 * 4096 + 17, 4096
+    path = str(tmp_path / "d.bin")
+    inputs.write_file(path, 5, size)
+    data = inputs.xorshift64_bytes(5, size)
+    want = hashlib.sha256(b"".join(hashlib.sha256(data[o:o + piece]).digest()
+                                   for o in range(0, size, piece))).hexdigest()
+    assert inputs.file_digest(path, piece=piece, threads=3) == want
+    assert inputs.file_digest(path, piece=piece, threads=1) == want
+    empty = str(tmp_path / "e.bin")
+    open(empty, "wb").close()
+    assert inputs.file_digest(empty) == hashlib.sha256(b"").hexdigest()
