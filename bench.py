@@ -726,8 +726,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "file_bytes": size, "page_bytes": page, "cache_bytes": cache,
                    "blocks": blocks, "stride_bytes": stride, "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": round(gbps, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "first %d strides of the canonical trace per step (%.0f s budget)" % (
+        "cpu_baseline": {"value": round(gbps, 4), "unit": "GB/s", "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle", "sample": "first %d strides of the canonical trace per step (%.0f s budget)" % (
                              strides // max(args.steps, 1), budget)},
         "e2e": {"value": round(gbps, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -914,7 +914,7 @@ def oracle_checks(path, stride, last, serving_results, cpu_seconds, workload):
     from oracle import pool
     size_, seed_, page_, cache_, blocks_, stride_ = WORKLOADS[workload]
     b, t, n = oracle_sample(path, page_, cache_ // page_, blocks_, stride_, cpu_seconds)
-    cpu = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+    cpu = {"value": round(b / t / 1e9, 4), "unit": "GB/s", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
            "sample": "first %d strides (%d MiB) of the canonical trace, %.1f s" % (n, b // MiB, t)}
     t0 = time.perf_counter()
     c, s, h = pool.scan_plain_parallel(path, stride)
