@@ -398,7 +398,7 @@ static __device__ __noinline__ int lane_tab_insert(const DevHandle& g, unsigned 
   return result;
 }
 
-// ---------------------------------------------------------------- consumed FIFO
+// ---------------------------------------------------------------- consumed FIFO, returned frames
 // Bounded MPMC queue over fifo_cap cells; each frame is in it at most once.  Cell
 // t % cap holds (seq << FRAME_BITS) | frame: seq = t while free for the push of
 // ticket t, t + 1 once that push landed, t + cap once popped (free for the next
@@ -408,34 +408,55 @@ static __device__ __noinline__ int lane_tab_insert(const DevHandle& g, unsigned 
 // draws that ticket sees a cell already past it and draws another.  Give-ups only
 // happen when the queue is empty, so the order of the frames in it is kept.
 
-// Store frame f into cell t, a ticket the caller took from fifo_tail (another if
-// a pop gave that one up).
-static __device__ bool fifo_put(const DevHandle& g, unsigned long long t, uint32_t f,
+// A ticket ring of frames: the consumed FIFO, or the ring of returned frames
+// (same protocol and capacity).
+struct FrameRing {
+  unsigned long long* cells;
+  unsigned long long* head;
+  unsigned long long* tail;
+};
+__device__ __forceinline__ FrameRing fifo_ring(const DevHandle& g) {
+  return FrameRing{g.fifo, &g.ctrl->fifo_head.v, &g.ctrl->fifo_tail.v};
+}
+__device__ __forceinline__ FrameRing ret_ring(const DevHandle& g) {
+  return FrameRing{g.ret, &g.ctrl->ret_head.v, &g.ctrl->ret_tail.v};
+}
+// Frames in a ring that no pop has drawn yet.
+__device__ __forceinline__ unsigned long long ring_size(const FrameRing& q) {  // one thread
+  const unsigned long long h = ld_rlx64(q.head), t = ld_rlx64(q.tail);
+  return t > h ? t - h : 0;
+}
+
+// Store frame f into cell t, a ticket the caller took from the ring's tail
+// (another if a pop gave that one up).
+static __device__ bool ring_put(const DevHandle& g, const FrameRing& q, unsigned long long t, uint32_t f,
                                 unsigned long long deadline) {  // one thread
   __threadfence();  // the frame's state before its entry
   for (;;) {
-    unsigned long long* c = &g.fifo[t % g.fifo_cap];
+    unsigned long long* c = &q.cells[t % g.fifo_cap];
     const unsigned long long v = ld_acq64(c), s = v >> FRAME_BITS;
     if (s == t) {  // a CAS: a pop may give this ticket up at the same time
       if (atomicCAS(c, v, ((t + 1) << FRAME_BITS) | f) == v) return true;
       continue;
     }
     if (s > t) {  // given up by a pop
-      t = atomicAdd(&g.ctrl->fifo_tail.v, 1ull);
+      t = atomicAdd(q.tail, 1ull);
       continue;
     }
     if (now_ns() > deadline) { stat_add(g, ST_TIMEOUTS, 1); return false; }
     __nanosleep(32);
   }
 }
-static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
-  return fifo_put(g, atomicAdd(&g.ctrl->fifo_tail.v, 1ull), f, deadline);
+static __device__ bool ring_push(const DevHandle& g, const FrameRing& q, uint32_t f,
+                                 unsigned long long deadline) {  // one thread
+  return ring_put(g, q, atomicAdd(q.tail, 1ull), f, deadline);
 }
 
-// The frame of ticket h, drawn by the caller from fifo_head: -1 when the ticket
-// was given up (no push held it), -ETIMEDOUT.
-static __device__ int fifo_take(const DevHandle& g, unsigned long long h, unsigned long long deadline) {  // one thread
-  unsigned long long* c = &g.fifo[h % g.fifo_cap];
+// The frame of ticket h, drawn by the caller from the ring's head: -1 when the
+// ticket was given up (no push held it), -ETIMEDOUT.
+static __device__ int ring_take(const DevHandle& g, const FrameRing& q, unsigned long long h,
+                                unsigned long long deadline) {  // one thread
+  unsigned long long* c = &q.cells[h % g.fifo_cap];
   const unsigned long long gone = ((h + g.fifo_cap) << FRAME_BITS) | MAX_FRAMES;
   for (;;) {
     const unsigned long long v = ld_acq64(c), s = v >> FRAME_BITS;
@@ -444,9 +465,9 @@ static __device__ int fifo_take(const DevHandle& g, unsigned long long h, unsign
       return (int)(v & MAX_FRAMES);
     }
     const bool late = now_ns() > deadline;
-    // not pushed: give the ticket up if no push holds it (the queue was empty),
+    // not pushed: give the ticket up if no push holds it (the ring was empty),
     // or when out of time
-    if (s == h && (late || ld_acq64(&g.ctrl->fifo_tail.v) <= h)) {
+    if (s == h && (late || ld_acq64(q.tail) <= h)) {
       if (atomicCAS(c, v, gone) == v) {
         if (!late) return -1;
         stat_add(g, ST_TIMEOUTS, 1);
@@ -460,9 +481,20 @@ static __device__ int fifo_take(const DevHandle& g, unsigned long long h, unsign
 }
 
 // Returns a frame, -1 when empty, -ETIMEDOUT.
-static __device__ int fifo_pop(const DevHandle& g, unsigned long long deadline) {  // one thread
-  if (ld_rlx64(&g.ctrl->fifo_head.v) >= ld_rlx64(&g.ctrl->fifo_tail.v)) return -1;
-  return fifo_take(g, atomicAdd(&g.ctrl->fifo_head.v, 1ull), deadline);
+static __device__ int ring_pop(const DevHandle& g, const FrameRing& q, unsigned long long deadline) {  // one thread
+  if (ld_rlx64(q.head) >= ld_rlx64(q.tail)) return -1;
+  return ring_take(g, q, atomicAdd(q.head, 1ull), deadline);
+}
+
+static __device__ bool fifo_put(const DevHandle& g, unsigned long long t, uint32_t f,
+                                unsigned long long deadline) {  // one thread
+  return ring_put(g, fifo_ring(g), t, f, deadline);
+}
+static __device__ bool fifo_push(const DevHandle& g, uint32_t f, unsigned long long deadline) {  // one thread
+  return ring_push(g, fifo_ring(g), f, deadline);
+}
+static __device__ int fifo_take(const DevHandle& g, unsigned long long h, unsigned long long deadline) {  // one thread
+  return ring_take(g, fifo_ring(g), h, deadline);
 }
 
 // ---------------------------------------------------------------- frames
@@ -588,13 +620,12 @@ static __device__ void evict_run(const DevHandle& g, const uint32_t* frames, uin
   __syncwarp();
 }
 
-// Readahead may only use free / consumed frames above the reserve (victim classes 1, 2).
+// Readahead may only use free / returned / consumed frames above the reserve
+// (victim classes 1, 2).
 static __device__ bool ra_allowed(const DevHandle& g) {  // one thread
   unsigned long long used = ld_rlx64(&g.ctrl->next_unused.v);
   unsigned long long never = used >= g.n_frames ? 0 : g.n_frames - used;
-  unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
-  unsigned long long consumed = t > h ? t - h : 0;
-  return never + consumed > g.reserve;
+  return never + ring_size(ret_ring(g)) + ring_size(fifo_ring(g)) > g.reserve;
 }
 
 // Victim selection (Section 5.1 restated; classes 1-3).  Returns a frame owned
@@ -616,23 +647,27 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
   }
   f = bcast(f);
   if (f >= 0) return f;
-  // (2) consumed FIFO, oldest first; a pinned entry goes back to the tail
-  for (uint32_t it = 0; it <= g.fifo_cap; ++it) {
-    int c = -1, claimed = -1;
-    if (lane == 0) {
-      c = fifo_pop(g, deadline);
-      if (c >= 0) {
-        claimed = frame_claim(g, c, true);
-        if (claimed == 0) fifo_push(g, (uint32_t)c, deadline);
+  // (1b) frames returned by greads that lost a page to another gread (keyless),
+  // then (2) the consumed FIFO, oldest first; a pinned entry goes back to its tail
+  for (int which = 0; which < 2; ++which) {
+    const FrameRing q = which == 0 ? ret_ring(g) : fifo_ring(g);
+    for (uint32_t it = 0; it <= g.fifo_cap; ++it) {
+      int c = -1, claimed = -1;
+      if (lane == 0) {
+        c = ring_pop(g, q, deadline);
+        if (c >= 0) {
+          claimed = frame_claim(g, c, true);
+          if (claimed == 0) ring_push(g, q, (uint32_t)c, deadline);
+        }
       }
-    }
-    c = bcast(c);
-    claimed = bcast(claimed);
-    if (c == -1) break;
-    if (c < 0) return c;
-    if (claimed == 1) {
-      evict_key(g, c, new_key, deadline);
-      return c;
+      c = bcast(c);
+      claimed = bcast(claimed);
+      if (c == -1) break;
+      if (c < 0) return c;
+      if (claimed == 1) {
+        evict_key(g, c, new_key, deadline);
+        return c;
+      }
     }
   }
   if (for_ra || !fallback) return -1;
@@ -690,12 +725,12 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
   return -kEAGAIN;
 }
 
-// Give a frame that lost an insert race back as a keyless FIFO entry.
+// Give a frame that lost an insert race back, keyless, to the returned-frame ring.
 static __device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned long long deadline) {  // one thread
   if (pinned) atomicSub(&g.fpins[f], 1u);
   st_rlx64(&g.fkey[f], KEY_NONE);
   st_rel(&g.fstate[f], FR_EMPTY);
-  fifo_push(g, (uint32_t)f, deadline);
+  ring_push(g, ret_ring(g), (uint32_t)f, deadline);  // taken again before any consumed page is evicted
 }
 
 // ---------------------------------------------------------------- pull transfer (GFS_XFER_PULL)
@@ -1112,10 +1147,10 @@ static __device__ int rpc_submit(const DevHandle& g, uint32_t fid, unsigned long
 // Warp: frames for pages 1 .. L of a request (page i of the request is a
 // readahead page when i >= demand), victim classes 1 and 2 only, taken in page
 // order into s_frames[1 ..] exactly as one take_frame per page would take them:
-// never-used frames first (one fetch-and-add for the run), then the consumed FIFO
-// (one ticket add per round).  A readahead page needs never + consumed > reserve
-// at its turn, and every page before it in the run has taken one frame since page
-// 0 did.  Returns how many pages, from page 1 on, got a frame; claimed victims
+// never-used frames first (one fetch-and-add for the run), then returned frames,
+// then the consumed FIFO (one ticket add per round).  A readahead page needs
+// never + returned + consumed > reserve at its turn, and every page before it in
+// the run has taken one frame since page 0 did.  Returns how many pages, from page 1 on, got a frame; claimed victims
 // still hold their old keys.
 static __device__ uint32_t take_run(const DevHandle& g, uint32_t L, uint32_t demand, unsigned long long deadline,
                                     uint32_t* s_frames) {
@@ -1126,8 +1161,7 @@ static __device__ uint32_t take_run(const DevHandle& g, uint32_t L, uint32_t dem
     if (lane == 0) {
       const unsigned long long used = ld_rlx64(&g.ctrl->next_unused.v);
       const unsigned long long never = used >= g.n_frames ? 0 : g.n_frames - used;
-      const unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
-      lim = (long long)(never + (t > h ? t - h : 0)) - (long long)g.reserve;
+      lim = (long long)(never + ring_size(ret_ring(g)) + ring_size(fifo_ring(g))) - (long long)g.reserve;
     }
     lim = (long long)bcast64((unsigned long long)lim);
     const long long last = lim > (long long)first_ra - 1 ? lim : (long long)first_ra - 1;
@@ -1144,31 +1178,34 @@ static __device__ uint32_t take_run(const DevHandle& g, uint32_t L, uint32_t dem
   got = (uint32_t)bcast((int)got);
   u0 = bcast64(u0);
   for (uint32_t j = lane; j < got; j += 32) s_frames[1 + j] = (uint32_t)(u0 + j);
-  // class 2: the consumed FIFO, oldest first; a pinned entry goes back to the tail
-  for (uint32_t round = 0; got < L && round < 8; ++round) {
-    unsigned long long h0 = 0;
-    uint32_t take = 0;
-    if (lane == 0) {
-      const unsigned long long h = ld_rlx64(&g.ctrl->fifo_head.v), t = ld_rlx64(&g.ctrl->fifo_tail.v);
-      const unsigned long long avail = t > h ? t - h : 0;
-      take = avail < L - got ? (uint32_t)avail : L - got;
-      if (take) h0 = atomicAdd(&g.ctrl->fifo_head.v, (unsigned long long)take);
-    }
-    take = (uint32_t)bcast((int)take);
-    h0 = bcast64(h0);
-    if (take == 0) break;
-    for (uint32_t j0 = 0; j0 < take; j0 += 32) {
-      int c = -1, claimed = -1;
-      if (j0 + lane < take) {
-        c = fifo_take(g, h0 + j0 + lane, deadline);
-        if (c >= 0) {
-          claimed = frame_claim(g, c, true);
-          if (claimed == 0) fifo_push(g, (uint32_t)c, deadline);
-        }
+  // class 1b: returned (keyless) frames, then class 2: the consumed FIFO, oldest
+  // first; a pinned entry goes back to its ring's tail
+  for (int which = 0; which < 2 && got < L; ++which) {
+    const FrameRing q = which == 0 ? ret_ring(g) : fifo_ring(g);
+    for (uint32_t round = 0; got < L && round < 8; ++round) {
+      unsigned long long h0 = 0;
+      uint32_t take = 0;
+      if (lane == 0) {
+        const unsigned long long avail = ring_size(q);
+        take = avail < L - got ? (uint32_t)avail : L - got;
+        if (take) h0 = atomicAdd(q.head, (unsigned long long)take);
       }
-      const unsigned m = __ballot_sync(kFull, claimed == 1);
-      if (claimed == 1) s_frames[1 + got + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
-      got += (uint32_t)__popc(m);
+      take = (uint32_t)bcast((int)take);
+      h0 = bcast64(h0);
+      if (take == 0) break;
+      for (uint32_t j0 = 0; j0 < take; j0 += 32) {
+        int c = -1, claimed = -1;
+        if (j0 + lane < take) {
+          c = ring_take(g, q, h0 + j0 + lane, deadline);
+          if (c >= 0) {
+            claimed = frame_claim(g, c, true);
+            if (claimed == 0) ring_push(g, q, (uint32_t)c, deadline);
+          }
+        }
+        const unsigned m = __ballot_sync(kFull, claimed == 1);
+        if (claimed == 1) s_frames[1 + got + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
+        got += (uint32_t)__popc(m);
+      }
     }
   }
   __syncwarp();
@@ -1720,7 +1757,7 @@ static __device__ int handle_miss_paper(const DevHandle& g, int stream, uint32_t
       atomicSub(&g.fpins[f], 1u);
       st_rlx64(&g.fkey[f], KEY_NONE);
       st_rel(&g.fstate[f], FR_EMPTY);
-      if (!own) fifo_push(g, (uint32_t)f, deadline);
+      if (!own) ring_push(g, ret_ring(g), (uint32_t)f, deadline);
     }
     __syncwarp();
     return r < 0 ? r : -kEAGAIN;

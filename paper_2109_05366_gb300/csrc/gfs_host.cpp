@@ -723,7 +723,8 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
                o_fcons = take((size_t)F * 4), o_fvalid = take((size_t)F * 4), o_fwin = take((size_t)F * 4),
                o_fmark = take((size_t)F * 4), o_faseq = take((size_t)F * 8),
                o_tab = take((size_t)g.nbuckets * BUCKET * 8), o_tlock = take((size_t)g.nbuckets * 4),
-               o_tovf = take((size_t)g.nbuckets * 4), o_fifo = take((size_t)std::max<uint32_t>(F, 2) * 8), o_ctrl = take(sizeof(Ctrl)),
+               o_tovf = take((size_t)g.nbuckets * 4), o_fifo = take((size_t)std::max<uint32_t>(F, 2) * 8),
+               o_ret = take((size_t)std::max<uint32_t>(F, 2) * 8), o_ctrl = take(sizeof(Ctrl)),
                o_files = take((size_t)c.max_files * sizeof(FileDev)),
                o_last = take((size_t)c.max_streams * c.max_files * 8),
                o_trpc = take((size_t)std::max<uint32_t>(1, c.trace_capacity) * sizeof(gfs_rpc_rec)),
@@ -754,6 +755,7 @@ int gfs_init(const gfs_config* cfg_in, gfs_ctx** out) {
   g.tlock = (uint32_t*)(a + o_tlock);
   g.tovf = (uint32_t*)(a + o_tovf);
   g.fifo = (unsigned long long*)(a + o_fifo);
+  g.ret = (unsigned long long*)(a + o_ret);
   g.ctrl = (Ctrl*)(a + o_ctrl);
   g.files = (FileDev*)(a + o_files);
   g.last_end = (unsigned long long*)(a + o_last);

@@ -58,6 +58,8 @@ struct Ctrl {
   Line alloc_counter;  // allocation sequence
   Line fifo_head;      // consumed FIFO pop position
   Line fifo_tail;      // consumed FIFO push position
+  Line ret_head;       // returned-frame ring pop position
+  Line ret_tail;       // returned-frame ring push position
   Line ring_tail;      // request ring: next ticket the GPU takes
   Line ticket;         // serialized mode: next stride allowed to gread
   Line trace_rpc_n;
@@ -181,6 +183,9 @@ struct DevHandle {
   uint32_t* tovf;
   // consumed FIFO cells: (position << 24 | frame)
   unsigned long long* fifo;
+  // returned-frame ring cells, same layout and capacity: frames a gread took for a
+  // page that another gread mapped first (only concurrent greads return one)
+  unsigned long long* ret;
   Ctrl* ctrl;
   FileDev* files;
   unsigned long long* last_end;  // per stream: (fid << 32 | end page), ~0 = none

@@ -84,7 +84,10 @@ __global__ void k_reset(DevHandle g) {
     g.tlock[i] = 0;
     g.tovf[i] = 0;
   }
-  for (size_t i = tid; i < g.fifo_cap; i += nt) g.fifo[i] = ((unsigned long long)i << FRAME_BITS) | MAX_FRAMES;
+  for (size_t i = tid; i < g.fifo_cap; i += nt) {
+    g.fifo[i] = ((unsigned long long)i << FRAME_BITS) | MAX_FRAMES;
+    g.ret[i] = ((unsigned long long)i << FRAME_BITS) | MAX_FRAMES;
+  }
   const size_t nle = (size_t)g.max_streams * g.max_files;
   for (size_t i = tid; i < nle; i += nt) g.last_end[i] = 0;
   if (g.fetch_count)
@@ -94,6 +97,8 @@ __global__ void k_reset(DevHandle g) {
     g.ctrl->alloc_counter.v = 0;
     g.ctrl->fifo_head.v = 0;
     g.ctrl->fifo_tail.v = 0;
+    g.ctrl->ret_head.v = 0;
+    g.ctrl->ret_tail.v = 0;
     g.ctrl->ticket.v = 0;
     g.ctrl->trace_rpc_n.v = 0;
     g.ctrl->trace_evict_n.v = 0;

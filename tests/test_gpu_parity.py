@@ -179,17 +179,17 @@ def test_overlapping_greads_race_for_the_same_pages_exact(torch_cuda, gfs, datad
     """Greads of 256 KiB every 16 KiB: sixteen blocks read every page at about the same
     time, so runs being installed meet pages other greads map meanwhile (the request is cut
     there and the pages after it are requested on their own).  Every stride stays exact and
-    every page is fetched.  The loser of a contested page gives its frame back (keyless, to
-    the consumed FIFO), so under this much overlap frames run short even though the file
-    fits, and some consumed pages are evicted and read again; the refetches stay few (how
-    many depends on how the races fall: 0-13 % of the pages in the runs seen)."""
+    every page is fetched.  The loser of a contested page gives its frame back, keyless, to
+    the returned-frame ring, which is taken before any consumed page is evicted: the file
+    fits, so (almost) no page is read twice.  (When lost frames went to the consumed FIFO
+    instead, 0-13 % of the pages were evicted and read again, as the races fell.)"""
     size = 12 * MiB + 333
     path = _file(datadir, 34, size)
     npages = (size + page - 1) // page
     with gfs.Context(cache_bytes=32 * MiB, page_size=page, xfer=xfer, max_rpc_pages=64, ra_cap_pages=63,
                      debug_counts=1) as ctx:
         fid = ctx.open(path)
-        cuts = 0
+        cuts = refetched = 0
         for rep in range(3):
             ctx.reset_cache()
             out = ctx.scan(fid, 16 * KiB, read_len=256 * KiB, blocks=128, threads=256, fused=rep == 1)
@@ -198,9 +198,10 @@ def test_overlapping_greads_race_for_the_same_pages_exact(torch_cuda, gfs, datad
             st = ctx.stats()
             assert st["timeouts"] == 0 and st["eio"] == 0 and st["enomem"] == 0
             counts = ctx.fetch_counts(npages)
-            assert (counts >= 1).all() and counts.sum() <= npages * 1.25
+            assert (counts >= 1).all() and counts.sum() <= npages + npages // 100
             cuts += st["run_cuts"]
-        print("requests cut by a concurrent install:", cuts)
+            refetched += int(counts.sum()) - npages
+        print("requests cut by a concurrent install:", cuts, "pages fetched again:", refetched, "of", 3 * npages)
 
 
 @pytest.mark.parametrize("xfer", XFERS)
