@@ -18,7 +18,9 @@ merged against one-request-per-read host service, cold reads (page cache
 dropped, O_DIRECT), and the serving loop (Poisson and saturating arrivals).
 Last, after every GPU measurement, the CPU-baseline leg: the CPU oracle timed
 on a bounded sample, and parity -- every stride of the last timed step and
-every serving completion compared with the oracle's plain definition.
+every serving completion compared with the oracle's plain definition.  These
+side measurements run at N = 1; with N > 1 (one replica per rank, each its own
+file) the line reports the replicas' rate, the link probes and the roofline.
 
 `--impl reference` times the CPU oracle itself (the reference arm).
 """
@@ -1009,29 +1011,36 @@ def run_gfs(args):
 
     extra = {}
     binding, binding_src = None, None
+    # the side measurements (baselines, other legs, serving, the CPU oracle) run at
+    # N = 1 only: with N > 1 the line carries the replicas' rate, the link probes and
+    # the roofline, and no rank's GPU is held while rank 0 measures more
+    side = world == 1
+    if rank == 0 and not args.quick and not side:
+        extra["side_measurements"] = "at N=1 only"
     if rank == 0 and not args.quick:
-        with gfs.Context(mode=gfs.MODE_ONDEMAND, **cfg) as ctx:
-            fid = ctx.open(path)
-            od = timed_scans(ctx, fid, args.steps, args.warmup)
-        extra["ondemand_gbps"] = round(size / (sum(od) / len(od)) / 1e9, 2)
-        extra["ondemand_steps"] = len(od)
-        d_file = torch.empty(size, dtype=torch.uint8, device=dev)
-        cpu_t = []
-        for i in range(3):
-            cpu_t.append(gfs.cpuio_scan(path, stride, stride, args.host_threads, 8 * MiB, d_file, out, stream))
-        extra["cpuio_gbps"] = round(size / min(cpu_t[1:]) / 1e9, 2)
-        extra["cpuio_threads"] = args.host_threads
-        one = gfs.cpuio_scan(path, stride, stride, 1, size, d_file, out, stream)
-        extra["cpuio_naive_1thread_gbps"] = round(size / one / 1e9, 2)
-        # context: the same checksums on the host alone, every core (pread + sums, no GPU)
-        ncpu = os.cpu_count() or 1
-        cs = min(gfs.cpu_scan(path, stride, stride, ncpu)[3] for _ in range(2))
-        extra["cpu_scan"] = {"gbps": round(size / cs / 1e9, 2), "threads": ncpu,
-                             "kind": "host threads pread each stride and checksum it, no GPU (gfs_cpu_scan)"}
-        t0 = time.perf_counter()
-        extra["input_digest"] = {"file_bytes": size, "sha256_of_64MiB_piece_sha256s": inputs.file_digest(path),
-                                 "s": round(time.perf_counter() - t0, 2)}
-        del d_file
+        if side:
+            with gfs.Context(mode=gfs.MODE_ONDEMAND, **cfg) as ctx:
+                fid = ctx.open(path)
+                od = timed_scans(ctx, fid, args.steps, args.warmup)
+            extra["ondemand_gbps"] = round(size / (sum(od) / len(od)) / 1e9, 2)
+            extra["ondemand_steps"] = len(od)
+            d_file = torch.empty(size, dtype=torch.uint8, device=dev)
+            cpu_t = []
+            for i in range(3):
+                cpu_t.append(gfs.cpuio_scan(path, stride, stride, args.host_threads, 8 * MiB, d_file, out, stream))
+            extra["cpuio_gbps"] = round(size / min(cpu_t[1:]) / 1e9, 2)
+            extra["cpuio_threads"] = args.host_threads
+            one = gfs.cpuio_scan(path, stride, stride, 1, size, d_file, out, stream)
+            extra["cpuio_naive_1thread_gbps"] = round(size / one / 1e9, 2)
+            # context: the same checksums on the host alone, every core (pread + sums, no GPU)
+            ncpu = os.cpu_count() or 1
+            cs = min(gfs.cpu_scan(path, stride, stride, ncpu)[3] for _ in range(2))
+            extra["cpu_scan"] = {"gbps": round(size / cs / 1e9, 2), "threads": ncpu,
+                                 "kind": "host threads pread each stride and checksum it, no GPU (gfs_cpu_scan)"}
+            t0 = time.perf_counter()
+            extra["input_digest"] = {"file_bytes": size, "sha256_of_64MiB_piece_sha256s": inputs.file_digest(path),
+                                     "s": round(time.perf_counter() - t0, 2)}
+            del d_file
         h2d = gfs.probe_h2d(GiB, 16 * MiB, 3)
         h2d_page = gfs.probe_h2d(GiB, page, 3)
         prd = gfs.probe_pread(path, 16, 4 * MiB, 2)
@@ -1050,13 +1059,13 @@ def run_gfs(args):
             binding, binding_src = min(pull, prd), "min(GPU reads of host memory, 16-thread pread)"
         else:
             binding, binding_src = min(h2d, prd), "min(pinned H2D copy, 16-thread pread)"
-        if args.xfer == "mapped":
+        if side and args.xfer == "mapped":
             oc = mapped_open_close(path)
             e2e_mean = sum(e2e_t) / len(e2e_t)
             for v in oc.values():  # one open, one scan through the C ABI, one close
                 v["e2e_open_scan_close_gbps"] = round(size / (v["open_s"] + e2e_mean + v["close_s"]) / 1e9, 2)
             extra["mapped_open_close"] = oc
-        if not args.no_extras:
+        if side and not args.no_extras:
             for key, fn in (("readahead_vs_ondemand", lambda: ra_vs_od_legs(args, stream)),
                             ("host_merge", lambda: merge_legs(args, path, stream)),
                             ("cold", lambda: cold_legs(args, stream))):
@@ -1113,7 +1122,7 @@ def run_gfs(args):
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     line.update(extra)
     serving_results = {}
-    if rank == 0 and not args.quick and not args.no_serving:
+    if rank == 0 and not args.quick and not args.no_serving and side:
         xf = xfer_code(args.xfer)
         serv = {"workload": "64 scans, files 2^(24+8u) B (log-uniform 16 MiB-4 GiB), 6 GiB cache, 296 CTAs, "
                             "1 MiB units; Poisson 20/s and 200/s, and all 64 at once (saturating)"}
@@ -1124,7 +1133,7 @@ def run_gfs(args):
                                   ("ondemand_saturating", gfs.MODE_ONDEMAND, None)):
             serv[label], serving_results[label] = serving_bench(args, xf, mode, rate)
         line["serving"] = serv
-    if not args.quick and not args.no_cpu_baseline:
+    if not args.quick and not args.no_cpu_baseline and side:
         line["cpu_baseline"], line["parity"] = oracle_checks(path, stride, last, serving_results, args.cpu_seconds,
                                                              args.workload)
     print(json.dumps(line), flush=True)
