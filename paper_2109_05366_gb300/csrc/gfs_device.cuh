@@ -725,12 +725,16 @@ static __device__ int take_frame(const DevHandle& g, bool for_ra, unsigned long 
   return -kEAGAIN;
 }
 
-// Give a frame that lost an insert race back, keyless, to the returned-frame ring.
-static __device__ void frame_return(const DevHandle& g, int f, bool pinned, unsigned long long deadline) {  // one thread
+// Give a frame that lost an insert race back, keyless: to the returned-frame ring,
+// taken again before any consumed page is evicted, unless it sits in the
+// requesting block's own LRA queue (Section 5.1), which reuses it from there (a
+// ring entry too would let the queue's reuses push it again and again).
+static __device__ void frame_return(const DevHandle& g, int f, bool pinned, bool in_own_queue,
+                                    unsigned long long deadline) {  // one thread
   if (pinned) atomicSub(&g.fpins[f], 1u);
   st_rlx64(&g.fkey[f], KEY_NONE);
   st_rel(&g.fstate[f], FR_EMPTY);
-  ring_push(g, ret_ring(g), (uint32_t)f, deadline);  // taken again before any consumed page is evicted
+  if (!in_own_queue) ring_push(g, ret_ring(g), (uint32_t)f, deadline);
 }
 
 // ---------------------------------------------------------------- pull transfer (GFS_XFER_PULL)
@@ -1288,7 +1292,7 @@ static __device__ uint32_t install_run(const DevHandle& g, int stream, uint32_t 
     if (j <= L) {
       const uint32_t f = s_frames[j];
       ok = lane_tab_insert(g, make_key(fid, p + j), f, deadline) == (int)f;
-      if (!ok) frame_return(g, (int)f, false, deadline);  // never reachable: not in the table
+      if (!ok) frame_return(g, (int)f, false, own_queue(g, stream), deadline);  // never reachable: not in the table
       else {
         const unsigned long long q = p + j;
         if (fi.fetched) atomicOr(&fi.fetched[q >> 5], 1u << (q & 31));
@@ -1391,7 +1395,7 @@ static __device__ int request_range(const DevHandle& g, int stream, uint32_t fid
     __syncwarp();
     int r = tab_insert(g, key, (uint32_t)f, deadline);
     if (r != f) {
-      if (lane == 0) frame_return(g, f, pin, deadline);
+      if (lane == 0) frame_return(g, f, pin, own_queue(g, stream), deadline);
       __syncwarp();
       if (i == 0) return r < 0 ? r : -kEAGAIN;
       break;
