@@ -684,6 +684,26 @@ def test_readahead_per_block_lra_concurrent_exact(torch_cuda, gfs, datadir, xfer
             ctx.reset_cache()
 
 
+@pytest.mark.parametrize("xfer", [1, 2])
+def test_per_block_lra_overlapping_greads_many_scans(torch_cuda, gfs, datadir, xfer):
+    """Per-block LRA under overlapping greads (64 KiB every 16 KiB, four readers per page),
+    twenty scans without a reset through a cache smaller than the file: frames that lose
+    an install race stay in their block's queue and are reused from there, so lost races
+    never pile up anywhere (every scan exact, no wait runs out)."""
+    torch = torch_cuda
+    size = 6 * MiB + 777
+    path = _file(datadir, 37, size)
+    with gfs.Context(cache_bytes=4 * MiB, page_size=4 * KiB, mode=0, replacement=1, ra_cap_pages=15,
+                     max_rpc_pages=32, xfer=xfer, timeout_ns=2 * 10**9) as ctx:
+        fid = ctx.open(path)
+        for _ in range(20):
+            out = ctx.scan(fid, 16 * KiB, read_len=64 * KiB, blocks=64, threads=256)
+            torch.cuda.synchronize()
+            _check_scan(gfs, path, 16 * KiB, *out, read_len=64 * KiB)
+        st = ctx.stats()
+        assert st["timeouts"] == 0 and st["enomem"] == 0 and st["eio"] == 0
+
+
 # ------------------------------------------------ the paper's own design (Sections 4.1, 5.1)
 @pytest.mark.parametrize("xfer", [1, 2])
 @pytest.mark.parametrize("repl", [0, 1])
