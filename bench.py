@@ -304,12 +304,14 @@ def run_cfg3(args):
 
 
 def run_cfg4(args):
-    """Config 4: float32 32768x32768 row dots by 128-row stripes; 8 GiB Zipf int32 histogram."""
+    """Config 4: float32 32768x32768 row dots by 128-row stripes; 8 GiB Zipf int32 histogram.
+
+    Rates only (with the kernels' status and the histogram's total count); every row and
+    every bin is checked against the oracle at this size in tests/test_gpu_fullsize.py."""
     import numpy as np
     import torch
 
     import inputs
-    from oracle import apps
     from paper_2109_05366_gb300 import gfs
     rows = cols = 32768
     mpath = os.path.join(data_dir(), "gfs_cfg4_mat_%d.f32" % rows)
@@ -337,15 +339,9 @@ def run_cfg4(args):
                 e1.record(stream)
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1) / 1e3)
-            got = out.cpu().numpy().astype(np.float64)
-            rng = np.random.default_rng(4)
-            sample = np.sort(rng.choice(rows, 64, replace=False))
-            worst = 0.0
-            for r in sample:
-                ref, ab = apps.rowdot(mpath, rows, cols, vec, int(r), int(r) + 1)
-                worst = max(worst, abs(got[r] - ref[0]) / (apps.gamma(cols) * ab[0]))
+            finite = bool(torch.isfinite(out).all().item())
             res["rowdot_" + xname] = {"gbps": round(rows * cols * 4 / min(ts[1:]) / 1e9, 1), "status": int(status.item()),
-                                      "sampled_rows": 64, "max_err_over_bound": round(worst, 4)}
+                                      "all_finite": finite}
             fz = ctx.open(zpath)
             ts = []
             for r in range(3):
