@@ -471,8 +471,8 @@ int gfs_cpuio_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_
  * (file offset + 1) mod 2^64), the same values the stride scan returns.
  * h_count, h_sum, h_hash: caller-owned host arrays of ceil(size / stride)
  * entries.  *seconds receives the wall time of the scan.  Returns 0, -EINVAL,
- * -ENOMEM or the -errno of open / pread (h_count[s] = that -errno for a stride
- * whose read failed). */
+ * -ENOMEM, -EAGAIN (no host thread could be started) or the -errno of open; a
+ * stride whose pread failed gets that -errno in h_count[s]. */
 int gfs_cpu_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t threads, int64_t* h_count,
                  uint64_t* h_sum, uint64_t* h_hash, double* seconds);
 

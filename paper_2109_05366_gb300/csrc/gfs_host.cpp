@@ -1668,7 +1668,7 @@ int gfs_cpu_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t 
   std::atomic<int> fail{0};
   const double t0 = now_s();
   std::vector<std::thread> th;
-  for (uint32_t t = 0; t < threads; ++t)
+  for (uint32_t t = 0; t < threads; ++t) try {
     th.emplace_back([&] {
       std::vector<uint8_t> buf;
       try {
@@ -1701,6 +1701,10 @@ int gfs_cpu_scan(const char* path, uint64_t stride, uint64_t read_len, uint32_t 
         h_hash[s] = hash;
       }
     });
+  } catch (...) {  // no more threads: the ones started serve every stride
+    if (th.empty()) fail.store(-EAGAIN);
+    break;
+  }
   for (auto& x : th) x.join();
   *seconds = now_s() - t0;
   close(fd);
