@@ -116,6 +116,32 @@ def test_serialized_logs_match_oracle(torch_cuda, gfs, datadir, size, page, fram
     assert ev == sim.evict_log
 
 
+@pytest.mark.parametrize("xfer", XFERS)
+@pytest.mark.parametrize("size,frames,blocks,stride,ra_cap", [
+    (6 * MiB + 5, 1024, 3, MiB, 255),     # 256-page demand runs, file larger than the cache
+    (3 * MiB + 7, 2048, 2, 64 * KiB, 255),  # readahead windows growing to 256 pages, file fits
+])
+def test_serialized_logs_at_the_largest_request(torch_cuda, gfs, datadir, size, frames, blocks, stride, ra_cap, xfer):
+    """Requests of up to 256 pages (the largest a request holds): runs of frames taken,
+    evicted and installed in eight rounds of 32 lanes; the logs still equal the oracle's."""
+    page = 4 * KiB
+    path = _file(datadir, 2, size)
+    reserve = policy.default_reserve(blocks, stride, page)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=0, ra_cap_pages=ra_cap, trace_capacity=1 << 16,
+                     reserve_frames=reserve, max_rpc_pages=256, xfer=xfer) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, blocks=blocks, threads=256, serialize=True)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out)
+        rpc, ev, nr, ne = ctx.trace()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, mode="readahead", ra_cap=ra_cap, reserve=reserve,
+                               max_rpc_pages=256)
+    assert max(n for _, _, n, _ in sim.rpc_log) >= 200  # the shape reaches the largest requests
+    assert nr == len(sim.rpc_log) and ne == len(sim.evict_log)
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
 @pytest.mark.parametrize("xfer", [1, 2])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_serialized_least_recently_allocated_beyond_1024_frames(torch_cuda, gfs, datadir, mode, xfer):
