@@ -134,6 +134,36 @@ def test_init_rejects_bad_config_without_gpu():
     assert e.value.errno == 22
 
 
+@pytest.mark.parametrize("kw,err", [
+    # limits a configuration may reach: accepted, so the call goes on to find no device
+    (dict(page_size=4096, cache_bytes=((1 << 24) - 1) * 4096), 19),   # the most frames a key can name
+    (dict(max_rpc_pages=256, ra_cap_pages=255), 19),                   # the largest request
+    (dict(rpc_slots=2), 19),
+    (dict(page_size=64 << 20, cache_bytes=64 << 20), 19),              # the largest page, one frame
+    (dict(host_threads=256), 19),
+    # one step past them: refused before any device call
+    (dict(page_size=4096, cache_bytes=(1 << 24) * 4096), 22),
+    (dict(max_rpc_pages=257), 22),
+    (dict(max_rpc_pages=0), 22),
+    (dict(rpc_slots=1), 22),
+    (dict(page_size=128 << 20, cache_bytes=128 << 20), 22),
+    (dict(page_size=2048), 22),
+    (dict(page_size=1 << 20, cache_bytes=(1 << 20) - 1), 22),         # no whole frame
+    (dict(host_threads=0), 22),
+    (dict(host_threads=257), 22),
+    (dict(max_files=0), 22),
+    (dict(timeout_ns=0), 22),
+    (dict(mode=2, xfer=0), 95),                                        # the paper mode copies its own pages
+])
+def test_init_limits_without_gpu(kw, err):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host has a GPU")
+    with pytest.raises(gfs.GfsError) as e:
+        gfs.Context(**kw)
+    assert e.value.errno == err
+
+
 @pytest.mark.parametrize("page,frames,requests,max_pages,threads,slots,size", [
     (4096, 512, 2000, 16, 4, 32, (3 << 20) + 12345),
     (65536, 64, 400, 8, 8, 4, (5 << 20) + 1),
