@@ -70,3 +70,31 @@ def test_contexts_give_everything_back(torch_cuda, gfs, datadir):
     assert free1 >= free0 - 64 * MiB, (free0, free1)
     assert tasks1 <= tasks0 + 2, (tasks0, tasks1)  # 16 I/O threads per context would show
     assert fds1 <= fds0 + 2, (fds0, fds1)
+
+
+@pytest.mark.parametrize("xfers", [(2, 2), (2, 1), (1, 0)])
+def test_two_contexts_scan_at_once(torch_cuda, gfs, datadir, xfers):
+    """Two tenants: two contexts (each its own cache, ring and I/O threads) scan their own
+    files on two streams at the same time; both results equal the oracle's."""
+    torch = torch_cuda
+    paths = []
+    for k, size in enumerate((40 * MiB + 3, 56 * MiB + 4097)):
+        p = os.path.join(datadir, "two_%d_%d.bin" % (k, size))
+        inputs.ensure_file(p, 60 + k, size)
+        paths.append(p)
+    wants = [plain.scan_plain(p, MiB) for p in paths]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ctxs = [gfs.Context(cache_bytes=16 * MiB, page_size=256 * KiB, xfer=x, max_rpc_pages=16) for x in xfers]
+    try:
+        fids = [c.open(p) for c, p in zip(ctxs, paths)]
+        outs = [c.scan(f, MiB, blocks=48, stream=s) for c, f, s in zip(ctxs, fids, streams)]
+        torch.cuda.synchronize()
+        for out, want, c in zip(outs, wants, ctxs):
+            assert out[0].cpu().numpy()[:len(want[0])].tolist() == want[0]
+            assert np.array_equal(gfs.u64_view(out[1])[:len(want[1])], np.array(want[1], dtype=np.uint64))
+            assert np.array_equal(gfs.u64_view(out[2])[:len(want[2])], np.array(want[2], dtype=np.uint64))
+            st = c.stats()
+            assert st["timeouts"] == 0 and st["eio"] == 0 and st["enomem"] == 0
+    finally:
+        for c in ctxs:
+            c.shutdown()
