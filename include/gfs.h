@@ -24,6 +24,8 @@
  *     the caller; h_* pointers are host memory owned by the caller.
  *   - A gfs_ctx is owned by the library from gfs_init to gfs_shutdown; it is
  *     not safe to call gfs_* on one context from several host threads at once.
+ *     Contexts are independent of one another (each its own cache, ring and I/O
+ *     threads): several may run at once on one device, on their own streams.
  */
 #ifndef GFS_H_
 #define GFS_H_
