@@ -45,7 +45,7 @@ def _check_scan(gfs, path, stride, cnt, sm, hs, read_len=None):
     assert cnt.cpu().numpy().tolist() == c
     assert np.array_equal(gfs.u64_view(sm)[:len(s)], np.array(s, dtype=np.uint64))
     assert np.array_equal(gfs.u64_view(hs)[:len(h)], np.array(h, dtype=np.uint64))
-
+# ------------------------------------------------ 64 MiB file, 128 MiB cache (fits), 256 KiB pages, 64 blocks
 
 # ------------------------------------------------ config 1: 64 MiB, fits the cache
 XFERS = [0, 1, 2]  # GFS_XFER_DMA, GFS_XFER_PULL, GFS_XFER_MAPPED
