@@ -1079,7 +1079,8 @@ def run_gfs(args):
     kt = sum(times) / len(times)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(1e3 * kt, 3), "step_ms": [round(1e3 * t, 2) for t in times],
+        "warmup": args.warmup, "ms_per_step": round(1e3 * kt, 3),
+        "median_ms_per_step": round(1e3 * statistics.median(times), 3), "step_ms": [round(1e3 * t, 2) for t in times],
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded xorshift64 file, warm host page cache)",
