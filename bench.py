@@ -956,6 +956,7 @@ def run_gfs(args):
     # weak scaling: every rank scans its own file (seed + rank), no data-path collective
     path = os.path.join(data_dir(), "gfs_bench_s%d_%d.bin" % (rank_seed(seed, rank), size))
     gen_s = ensure_input(path, rank_seed(seed, rank), size)
+    resident = round(_resident_fraction(path), 4)  # warm run: the file sits in the host page cache (mincore)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     nstr = (size + stride - 1) // stride
@@ -1089,6 +1090,7 @@ def run_gfs(args):
                    "host_threads": args.host_threads, "rpc_slots": args.rpc_slots, "fused": bool(args.fused),
                    "xfer": args.xfer, "mapped": mapped, "max_rpc_pages": args.max_rpc_pages,
                    "l2": "inputs larger than L2 (%d MiB file); no flush" % (size // MiB),
+                   "host_page_cache_resident": resident,
                    "parallelism": "replicas" if world > 1 else "1gpu"},
         "clocks": clocks,
         "e2e": {"value": round(size / (sum(e2e_t) / len(e2e_t)) / 1e9, 3), "unit": "GB/s",
