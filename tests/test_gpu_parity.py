@@ -142,6 +142,30 @@ def test_serialized_logs_at_the_largest_request(torch_cuda, gfs, datadir, size, 
     assert ev == sim.evict_log
 
 
+@pytest.mark.parametrize("xfer", XFERS)
+@pytest.mark.parametrize("size,page,frames,blocks,stride,read_len,ra_cap,fused", [
+    (72 * MiB + 7, 2 * MiB, 16, 4, 4 * MiB, 4 * MiB, 4, False),    # 2 MiB pages, file 2.3x the cache
+    (72 * MiB + 7, 2 * MiB, 16, 4, 4 * MiB, 4 * MiB, 4, True),     # the same with the fused consumer
+    (160 * MiB + 5, 64 << 20, 4, 2, 16 * MiB, 16 * MiB, 2, False),  # the largest page: four reads per page
+])
+def test_serialized_logs_at_the_largest_pages(torch_cuda, gfs, datadir, size, page, frames, blocks, stride, read_len,
+                                             ra_cap, fused, xfer):
+    path = _file(datadir, 2, size)
+    reserve = policy.default_reserve(blocks, read_len, page)
+    with gfs.Context(cache_bytes=frames * page, page_size=page, mode=0, ra_cap_pages=ra_cap, trace_capacity=1 << 16,
+                     reserve_frames=reserve, max_rpc_pages=16, xfer=xfer) as ctx:
+        fid = ctx.open(path)
+        out = ctx.scan(fid, stride, read_len=read_len, blocks=blocks, threads=256, serialize=True, fused=fused)
+        torch_cuda.cuda.synchronize()
+        _check_scan(gfs, path, stride, *out, read_len=read_len)
+        rpc, ev, nr, ne = ctx.trace()
+    sim, res = policy.run_scan(path, page, frames, stride, blocks, read_len=read_len, mode="readahead", ra_cap=ra_cap,
+                               reserve=reserve, max_rpc_pages=16)
+    assert nr == len(sim.rpc_log) and ne == len(sim.evict_log)
+    assert rpc == sim.rpc_log
+    assert ev == sim.evict_log
+
+
 @pytest.mark.parametrize("xfer", [1, 2])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_serialized_least_recently_allocated_beyond_1024_frames(torch_cuda, gfs, datadir, mode, xfer):
